@@ -1,0 +1,436 @@
+#!/usr/bin/env python
+"""Throughput of the differentiable 3DGS rasterizer with pose gradients.
+
+One step = project + bin/sort + render forward + L1 loss + raster backward +
+projection backward + pose-gradient reduction over one batch of views, i.e.
+forward and backward to every Gaussian parameter and every view's pose.
+
+Default workload: 1,000,000 clustered SH-degree-3 Gaussians, one 1237x822
+view (fx=fy=1000), synthetic and seeded; the step is captured once into a
+CUDA graph and replayed. Metric: pixels per second (Mpix/s) of fwd+bwd incl.
+pose gradients; ``value`` is the whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the path has no exchange step on one GPU per process): weak
+scaling, max-over-ranks time. ``--impl reference`` times the FP64 CPU oracle
+on the host cores (rank 0 only) on bounded pixel samples of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpix/s incl. pose grads at 1M Gaussians"
+UNIT = "Mpix/s"
+
+# FP32 operations per pixel-Gaussian pair, counted from the kernels'
+# arithmetic (gs_render.cu): every pair that passes the pixel gate evaluates
+# the exponent (dx, dy, 3 mul + 2 fma, o*G, clamp/threshold: 10 ops + 1 ex2);
+# a composited pair adds 9 in the forward (1-alpha, T update, weight,
+# 3 fma) and 50 in the backward (colour/alpha/conic/mean gradients and the
+# recomputed accumulation).
+FWD_OPS_EVAL, FWD_OPS_COMP = 10, 9
+BWD_OPS_EVAL, BWD_OPS_COMP = 10, 50
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-fraction", type=float, default=1.0 / 16.0,
+                    help="pixel fraction of each reference-arm step")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_2509_25191_gb300 import synth
+    sc, vw = synth.single_view_1m(0, n)
+    return sc, vw
+
+
+def algorithmic_bytes(n, sh_degree, slots, instances, pixels, n_tiles):
+    """Bytes the method must move per step: raw records read twice and
+    gradients written once (3 N R_in), projected records written and read
+    (64 + 48 B per slot for records and 2D gradients, both ways 132 B),
+    tile instances (key + id written, read sorted, gathered in forward and
+    backward: 108 B), images (colour, target, upstream, image re-read: 36 B
+    per pixel), tile ranges."""
+    r_in = 4 * (3 + 3 + 4 + 1 + 3 * (sh_degree + 1) ** 2)
+    return 3 * n * r_in + 132 * slots + 108 * instances + 36 * pixels + 8 * n_tiles
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 100 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+
+def run_native(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_25191_gb300 import _lib, build
+    from paper_2509_25191_gb300.autograd import Rasterizer
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    tile = tuple(int(x) for x in args.tile.split("x"))
+    sc, vw = workload(args.n)
+    g = _lib.Gaussians.from_scene(sc, dev)
+    views = _lib.Views.from_synth(vw, dev)
+    P = views.pixels
+    rng = np.random.default_rng(1234)
+    target = torch.as_tensor(rng.uniform(0, 1, views.num_image_floats()).astype(np.float32), device=dev)
+
+    rast = Rasterizer(tile=tile)
+    # eager step to size the instance capacity (the one host readback)
+    image, proj = rast.forward(g, views)
+    torch.cuda.synchronize()
+    n_inst = rast.last_instances
+    rast.reserve(views, int(n_inst * 1.25) + 4096, dev)
+    proj = torch.empty_like(proj)
+    image = torch.empty(views.num_image_floats(), device=dev)
+    dimg = torch.empty_like(image)
+    loss = torch.empty(1, device=dev)
+    grads = rast.grads_buffers(g, views)
+    dvm = torch.empty(views.n, 12, device=dev)
+    dtw = torch.empty(views.n, 6, device=dev)
+    cfg, bins, status = rast.cfg, rast.bins, rast.status
+
+    def step(events=None):
+        rec = (lambda: events.append(torch.cuda.Event(enable_timing=True)) or events[-1].record()) \
+            if events is not None else (lambda: None)
+        rec()
+        _lib.gs_project(g, views, cfg, proj, status)
+        rec()
+        _lib.gs_bin_sort(views, cfg, proj, bins, status)
+        rec()
+        _lib.gs_render_fwd(views, cfg, proj, bins, image, status)
+        rec()
+        _lib.gs_l1_loss(image, target, loss, dimg)
+        rec()
+        _lib.gs_rasterize_bwd(views, cfg, proj, bins, image, dimg, grads.grad2d, status)
+        rec()
+        _lib.gs_project_bwd(g, views, cfg, proj, grads, True, status)
+        rec()
+        _lib.gs_pose_grad(views, grads.pose_partials, grads.n_blocks, dvm, dtw)
+        rec()
+
+    kernels_per_step = 1 + 5 + 1 + 1 + 1 + 1 + 1   # project, bin(5), fwd, l1, rbwd, pbwd, pose
+    step()
+    torch.cuda.synchronize()
+    rast.check_status()
+
+    # per-stage durations (CUDA events on the launching stream, eager calls)
+    names = ["gs_project", "gs_bin_sort", "gs_render_fwd", "gs_l1_loss", "gs_rasterize_bwd", "gs_project_bwd",
+             "gs_pose_grad"]
+    acc = np.zeros(len(names))
+    reps = 10
+    for _ in range(reps):
+        ev = []
+        step(ev)
+        torch.cuda.synchronize()
+        acc += [ev[i].elapsed_time(ev[i + 1]) for i in range(len(names))]
+    stage_ms = acc / reps
+    pairs = _lib.pair_counts(bins)
+    n_inst = int(bins.counters[0].item())
+
+    # capture the whole step in a CUDA graph
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        step()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            step()
+    torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        graph.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        cur = torch.cuda.current_stream()
+        t0.record(cur)
+        for _ in range(args.steps):
+            graph.replay()
+        t1.record(cur)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms = t0.elapsed_time(t1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    clocks = clk.summary()
+    rast.check_status()
+    value = world * P / (ms * 1e-3) / 1e6
+
+    # end to end through the public API: pinned host inputs copied in, result out
+    e2e = None
+    if not args.no_e2e:
+        host = [t.cpu().pin_memory() for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.sh,
+                                               views.viewmats)]
+        dev_t = [g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, views.viewmats]
+        out_img = torch.empty(image.shape, dtype=torch.float32).pin_memory()
+        out_pose = torch.empty(dvm.shape, dtype=torch.float32).pin_memory()
+        out_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+        h2d = sum(t.numel() * 4 for t in host)
+        d2h = (out_img.numel() + out_pose.numel() + 1) * 4
+        k_e2e = max(3, min(args.steps, 50))
+
+        def e2e_step():
+            for h, d in zip(host, dev_t):
+                d.copy_(h, non_blocking=True)
+            graph.replay()
+            out_img.copy_(image, non_blocking=True)
+            out_pose.copy_(dvm, non_blocking=True)
+            out_loss.copy_(loss, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(k_e2e):
+            e2e_step()
+        b.record()
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(b) / k_e2e
+        if world > 1:
+            tt = torch.tensor([ems], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt.item())
+        e2e = {"value": round(world * P / (ems * 1e-3) / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ems, 4), "steps": k_e2e}
+
+    # roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    top = int(np.argmax(stage_ms))
+    t_top = stage_ms[top] * 1e-3
+    if names[top] in ("gs_render_fwd", "gs_rasterize_bwd"):
+        ev_, co_ = (pairs[0], pairs[1]) if names[top] == "gs_render_fwd" else (pairs[2], pairs[3])
+        ops = (FWD_OPS_EVAL * ev_ + FWD_OPS_COMP * co_) if names[top] == "gs_render_fwd" else \
+            (BWD_OPS_EVAL * ev_ + BWD_OPS_COMP * co_)
+        peak = sms * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = ops / t_top / 1e12
+        roof = {"kernel": names[top], "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz"
+                               f" ({peak_src} max clock)",
+                "units": {"pairs_evaluated": ev_, "pairs_composited": co_, "fp32_ops": int(ops)}}
+    else:
+        hbm = peaks["hbm_gbs"]
+        roof = {"kernel": names[top], "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None}
+    step_bytes = algorithmic_bytes(g.n, g.sh_degree, views.num_slots(), n_inst, P, views.num_tiles(cfg))
+    hbm_frac_step = step_bytes / (ms * 1e-3) / (peaks["hbm_gbs"] * 1e9)
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"single view 1237x822, {g.n} clustered SH3 Gaussians (seed 0), fwd+L1+bwd+pose",
+                   "gaussians": g.n, "views": views.n, "pixels_per_step": P, "tile": list(tile),
+                   "instances": n_inst, "l2": "inputs larger than L2 (236 MB raw records + 64 MB projected)",
+                   "graph": "one CUDA graph per step", "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "step_hbm_roofline": {"algorithmic_bytes": int(step_bytes), "frac": round(hbm_frac_step, 4),
+                              "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src},
+        "stages_ms": {n: round(float(t), 4) for n, t in zip(names, stage_ms)},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": kernels_per_step * args.steps,
+    }
+    return out, sc, vw
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_step(sc, vw, fraction, seed):
+    """One oracle fwd+bwd+pose pass over a random pixel sample (all pixels if
+    fraction >= 1). Returns the number of pixels computed."""
+    from oracle import oracle as O
+    W, H = int(vw.width[0]), int(vw.height[0])
+    rng = np.random.default_rng(seed)
+    mask = None if fraction >= 1 else rng.random((H, W)) < fraction
+    up = rng.standard_normal((3, H, W))
+    if mask is not None:
+        up[:, ~mask] = 0.0
+    f = O.forward(sc, vw, masks=None if mask is None else [mask])
+    O.backward(sc, vw, f, [up])
+    return W * H if mask is None else int(mask.sum())
+
+
+def cpu_baseline(sc, vw):
+    t = time.perf_counter()
+    npx = oracle_step(sc, vw, 1.0, 7)
+    dt = time.perf_counter() - t
+    return {"value": round(npx / dt / 1e6, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full step: all {npx} pixels of the same workload, FP64 C oracle, single thread",
+            "seconds": round(dt, 2)}
+
+
+_WORKER = {}
+
+
+def _ref_worker_init(n):
+    _WORKER["scene"] = workload(n)
+
+
+def _ref_worker_step(job):
+    fraction, seed = job
+    sc, vw = _WORKER["scene"]
+    return oracle_step(sc, vw, fraction, seed)
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands (single-threaded FP64 C), one step per worker
+    process; steps run concurrently on the host cores (spawned pool)."""
+    if rank != 0:
+        return None
+    import multiprocessing as mp
+    from oracle import oracle as O
+    O.build()
+    cores = max(1, min(os.cpu_count() or 1, args.steps))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_ref_worker_init, initargs=(args.n,)) as pool:
+        pool.map(_ref_worker_step, [(args.ref_fraction, 10_000 + w) for w in range(max(args.warmup, cores))])
+        t = time.perf_counter()
+        px = sum(pool.map(_ref_worker_step, [(args.ref_fraction, k) for k in range(args.steps)], chunksize=1))
+        dt = time.perf_counter() - t
+    val = px / dt / 1e6
+    sample = (f"each step: full projection, binning and projection backward of all {args.n} Gaussians, render "
+              f"forward+backward on a random {args.ref_fraction:.4f} of the 1237x822 pixels; FP64 C oracle, "
+              f"single-threaded per step, {cores} steps at a time on {cores} host cores")
+    return {"metric": METRIC, "value": round(val, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"single view 1237x822, {args.n} clustered SH3 Gaussians (seed 0), fwd+bwd+pose"},
+            "cpu_baseline": {"value": round(val, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(val, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    out, sc, vw = run_native(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(sc, vw)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

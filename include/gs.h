@@ -1,0 +1,214 @@
+/*
+ * gs.h -- C ABI of libgsplat_gb300.so: a differentiable tile-based 3D Gaussian
+ * Splatting rasterizer with camera-pose gradients for NVIDIA GB300 (sm_103a).
+ *
+ * Paper anchors (arXiv 2509.25191, "VGGT-X"):
+ *   Section 3.1 -- Gaussians with mean, covariance R S S^T R^T, opacity and
+ *                  degree-3 SH colour; pixel colours by alpha blending;
+ *                  training by photometric loss.
+ *   Section 3.4 -- joint optimisation of per-view residual poses (translation
+ *                  and 6D rotation) with the Gaussians, which needs the
+ *                  gradient of the rendered images w.r.t. each camera pose.
+ *   The rasterizer itself is cited, not specified, by the paper; the EWA
+ *   projection Sigma' = J W Sigma W^T J^T + 0.3 I, the alpha clamp 0.99, the
+ *   1/255 cutoff and the stop before T < 1e-4 are the readings this library
+ *   implements (defaults of gs_config).
+ *
+ * Conventions for every entry point
+ *   - All functions return int: GS_OK (0) or a gs_status code. No exception
+ *     or abort crosses the ABI. gs_error_string() names a code.
+ *   - Buffers marked DEVICE are device pointers owned by the caller; the
+ *     library never allocates, frees or synchronises. Buffers marked HOST are
+ *     read during the call only.
+ *   - Work is enqueued on the caller's stream (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream). Given the same host arguments,
+ *     the enqueued work is the same on every call, so a call sequence can be
+ *     captured into a CUDA graph and replayed with new DEVICE contents.
+ *   - Host-side argument errors return GS_ERR_ARG before anything is
+ *     enqueued; a failed launch returns GS_ERR_CUDA. Conditions found on the
+ *     device (instance capacity exceeded) are written to the caller's DEVICE
+ *     status word int32[4] = {code, detail_lo, detail_hi, 0}; the caller reads
+ *     it at a point of its choosing. Kernels never trap and never spin.
+ *   - float32 everywhere. Quaternions are (w,x,y,z). Cameras are
+ *     world->camera rigid transforms with OpenCV axes (x right, y down,
+ *     z forward); a pixel (u,v) has its centre at (u+0.5, v+0.5).
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_MAX_VIEWS 64        /* views per call */
+#define GS_RECORD_FLOATS 16    /* floats per projected record */
+#define GS_GRAD2D_FLOATS 12    /* floats per 2D-gradient record */
+#define GS_POSE_FLOATS 12      /* dL/dR (row-major) then dL/dt */
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_ARG = 1,          /* invalid argument (host check) */
+    GS_ERR_CUDA = 2,         /* a CUDA call or launch failed */
+    GS_ERR_CAPACITY = 3,     /* device: instance capacity too small; detail = instances needed */
+    GS_ERR_UNSUPPORTED = 4,  /* configuration not compiled in (tile shape, SH degree) */
+    GS_ERR_OVERFLOW = 5      /* device: more than 2^31-1 tile instances */
+} gs_status;
+
+/* Rasterizer settings. gs_config_default() fills the defaults in brackets. */
+typedef struct gs_config {
+    int tile_w, tile_h;   /* tile in pixels [16,16]; supported: 16x16, 8x8, 16x8, 32x8, 32x16 */
+    int pixel_gate;       /* [1] evaluate a Gaussian at a pixel only if |dx|,|dy| <= radius */
+    float near_z;         /* [0.2] cull if camera-space z <= near_z */
+    float dilation;       /* [0.3] added to the 2D covariance diagonal (pixels^2) */
+    float alpha_min;      /* [1/255] skip contributions with alpha below this */
+    float alpha_max;      /* [0.99] clamp alpha to this */
+    float t_min;          /* [1e-4] stop before transmittance would fall below this */
+    float fov_clamp;      /* [1.3] clamp x/z, y/z to +-fov_clamp*tan(half fov) inside J */
+    float bg[3];          /* [0,0,0] background colour */
+} gs_config;
+
+/* Gaussians (all DEVICE, float32, contiguous). Several scenes may be
+ * concatenated; each view names the range it sees (gs_views). */
+typedef struct gs_gaussians {
+    int64_t n;                   /* total Gaussians */
+    int sh_degree;               /* 0..3; K = (sh_degree+1)^2 */
+    const float *means;          /* [n,3] */
+    const float *log_scales;     /* [n,3]; scale = exp */
+    const float *quats;          /* [n,4] (w,x,y,z), need not be unit */
+    const float *opacity_logits; /* [n]; opacity = sigmoid */
+    const float *sh;             /* [n,K,3], coefficient l*l+l+m, channel last */
+} gs_gaussians;
+
+/* Views rendered by one call. Views that see the same Gaussian range must be
+ * contiguous; ranges of different groups must not overlap. */
+typedef struct gs_views {
+    int n_views;                 /* V, 1..GS_MAX_VIEWS */
+    const float *viewmats;       /* DEVICE [V,12]: R row-major (9) then t (3), world->camera */
+    const float *intrinsics;     /* DEVICE [V,4]: fx, fy, cx, cy (pixels) */
+    const int32_t *width;        /* HOST [V] */
+    const int32_t *height;       /* HOST [V] */
+    const int64_t *gauss_begin;  /* HOST [V] first Gaussian the view sees */
+    const int64_t *gauss_count;  /* HOST [V] number of Gaussians the view sees */
+} gs_views;
+
+/* Tile lists produced by gs_bin_sort (all DEVICE, caller-allocated with the
+ * sizes from the layout queries below). */
+typedef struct gs_bins {
+    int64_t capacity;     /* instance capacity of keys/ids/keys_tmp */
+    int32_t *tile_ranges; /* [T,2] start,end of each tile's instances; tiles of view v
+                             start at gs_tile_base(v), tile (tx,ty) at +ty*Gx+tx */
+    uint64_t *keys;       /* [capacity] (float32 depth bits << 32) | slot, ascending per tile */
+    uint32_t *ids;        /* [capacity] slot of each instance, same order as keys */
+    uint64_t *keys_tmp;   /* [capacity] scratch for tiles too large for on-chip sorting */
+    int32_t *tile_order;  /* [T] work order: tiles by decreasing instance count */
+    int32_t *tile_scratch;/* [T] scratch (per-tile counters) */
+    int32_t *counters;    /* [GS_NUM_COUNTERS] scratch; counters[0] = instances after the call;
+                             int64 at counters+8: pixel-Gaussian pairs evaluated by gs_render_fwd,
+                             +10: composited by it, +12/+14: the same for gs_rasterize_bwd */
+} gs_bins;
+#define GS_NUM_COUNTERS 16
+
+/* Gradient outputs of gs_render_bwd (all DEVICE). The parameter gradients are
+ * OVERWRITTEN (not accumulated). grad2d and pose_partials are caller-owned
+ * scratch that also remain readable after the call. */
+typedef struct gs_grads {
+    float *means;          /* [n,3] */
+    float *log_scales;     /* [n,3] */
+    float *quats;          /* [n,4] */
+    float *opacity_logits; /* [n] */
+    float *sh;             /* [n,K,3] */
+    float *grad2d;         /* [P,12] per slot: dL/d(x,y,A,B | C,o,r,g | b,-,-,-) */
+    float *pose_partials;  /* [V, gs_pose_blocks(n), 12] */
+} gs_grads;
+
+/* ---------------- layout queries (host, pure) ---------------- */
+
+void gs_config_default(gs_config *cfg);
+/* P: number of projected records (slots). Slot of Gaussian i in view v is
+ * gs_slot_base(v) + (i - gauss_begin[v]). */
+int64_t gs_num_slots(const gs_views *views);
+int64_t gs_slot_base(const gs_views *views, int v);
+/* T: total tiles over all views; ceil(W/tile_w)*ceil(H/tile_h) per view. */
+int64_t gs_num_tiles(const gs_views *views, const gs_config *cfg);
+int64_t gs_tile_base(const gs_views *views, const gs_config *cfg, int v);
+/* Image floats: sum_v 3*H_v*W_v; view v is [3,H_v,W_v] at float offset
+ * gs_pixel_base(v) (= 3 * sum_{u<v} H_u*W_u). */
+int64_t gs_num_image_floats(const gs_views *views);
+int64_t gs_pixel_base(const gs_views *views, int v);
+/* Blocks of the projection-backward grid for n Gaussians (pose partials). */
+int gs_pose_blocks(int64_t n);
+
+/* ---------------- the rasterizer ---------------- */
+
+/* Project every Gaussian into every view that sees it (Section 3.1
+ * primitive; EWA splatting). Per slot p, proj[16p..16p+15] =
+ *   {x, y, x_lo, y_lo}  mean in pixels as an unevaluated float pair x+x_lo,
+ *   {A, B, C, o}        conic (inverse dilated 2D covariance, B off-diagonal)
+ *                       and opacity,
+ *   {r, g, b, radius}   colour (SH evaluated, +0.5, clamped at 0) and the
+ *                       integer radius ceil(3 sqrt(lambda_max)) (0 = culled),
+ *   {depth, clamp_bits, 0, 0}  camera z; bit c set if channel c was clamped.
+ * proj: DEVICE [P,16]. status: DEVICE int32[4] (unused here, may be NULL). */
+int gs_project(const gs_gaussians *g, const gs_views *views, const gs_config *cfg,
+               float *proj, int32_t *status, void *stream);
+
+/* Bin the projected records into tiles and sort each tile by (depth, slot).
+ * A record touches the tiles [floor((x-r)/tw), floor((x+r)/tw)] x (same in
+ * y), clipped to the view's grid, computed in float32. If the instance count
+ * exceeds bins->capacity, status = {GS_ERR_CAPACITY, needed} and the lists
+ * are left unsorted; counters[0] holds the count either way (a call with
+ * capacity 0 is a pure count). */
+int gs_bin_sort(const gs_views *views, const gs_config *cfg, const float *proj,
+                const gs_bins *bins, int32_t *status, void *stream);
+
+/* Composite every pixel front to back (Section 3.1 alpha blending) and
+ * write image: DEVICE [sum_v 3 H_v W_v] (view layout as gs_pixel_base). If a
+ * capacity error is pending in counters, images are filled with zeros. */
+int gs_render_fwd(const gs_views *views, const gs_config *cfg, const float *proj,
+                  const gs_bins *bins, float *image, int32_t *status, void *stream);
+
+/* Backward of gs_project + gs_render_fwd for the upstream gradient
+ * dL_dimage (same layout as image). image must be the forward's output for
+ * the same inputs (transmittance is recomputed from it, not stored).
+ * Writes grads->grad2d (zeroed by the call), the raw-parameter gradients
+ * (unless want_gaussian_grads == 0) and grads->pose_partials. */
+int gs_render_bwd(const gs_gaussians *g, const gs_views *views, const gs_config *cfg,
+                  const float *proj, const gs_bins *bins, const float *image,
+                  const float *dL_dimage, const gs_grads *grads, int want_gaussian_grads,
+                  int32_t *status, void *stream);
+
+/* The two stages of gs_render_bwd, callable separately (same arguments and
+ * semantics as there). gs_rasterize_bwd zeroes grad2d [P,12] and adds the
+ * per-slot 2D gradients dL/d(x,y,A,B | C,o,r,g | b); gs_project_bwd chains
+ * grad2d to the raw parameters and the pose partials. */
+int gs_rasterize_bwd(const gs_views *views, const gs_config *cfg, const float *proj, const gs_bins *bins,
+                     const float *image, const float *dL_dimage, float *grad2d, int32_t *status, void *stream);
+int gs_project_bwd(const gs_gaussians *g, const gs_views *views, const gs_config *cfg, const float *proj,
+                   const float *grad2d, const gs_grads *grads, int want_gaussian_grads, int32_t *status,
+                   void *stream);
+
+/* Reduce pose partials (Section 3.4 pose residuals): dL_dviewmat DEVICE
+ * [V,12] = dL/dR (row-major) then dL/dt; dL_dtwist DEVICE [V,6] (may be NULL)
+ * = gradient w.r.t. a left twist (rho, phi), T <- exp(xi^) T:
+ * M = dL/dR R^T + dL/dt t^T (3x3, 1-based indices below),
+ * dL/dphi = (M32 - M23, M13 - M31, M21 - M12), dL/drho = dL/dt.
+ * Summation order is fixed (deterministic). */
+int gs_pose_grad(const gs_views *views, const float *pose_partials, int n_blocks,
+                 float *dL_dviewmat, float *dL_dtwist, void *stream);
+
+/* Mean L1 photometric loss (Section 3.1 photometric supervision) and its
+ * gradient: loss DEVICE [1] = mean |image - target| (overwritten),
+ * dL_dimage DEVICE [count] = sign(image - target) / count. */
+int gs_l1_loss(const float *image, const float *target, int64_t count, float *loss,
+               float *dL_dimage, void *stream);
+
+const char *gs_error_string(int code);
+int gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

@@ -495,15 +495,18 @@ static int composite_pixel(int px, int py, int64_t s, int64_t e, const int32_t *
 /* Render one view. Tile lists (ranges over tiles ty*Gx+tx, ids) come from
  * or_bin_fill (possibly built with enlarged radii so that every Gaussian a
  * float32 computation might list is present; the gate below uses radius).
- * img is [3,H,W]; T_final, n_contrib and flags are [H,W]. */
+ * img is [3,H,W]; T_final, n_contrib and flags are [H,W]. If mask is not
+ * NULL, only pixels with mask[py*W+px] != 0 are computed. */
 void or_render(const double *xy, const double *conic, const double *opac, const double *rgb,
                const int32_t *radius, const double *r_real, const double *depth,
                int W, int H, int TW, int TH, const int64_t *ranges, const int32_t *ids,
-               const or_params *P, double *img, double *T_final, int32_t *n_contrib, int32_t *flags)
+               const or_params *P, const uint8_t *mask, double *img, double *T_final, int32_t *n_contrib,
+               int32_t *flags)
 {
     int Gx = (W + TW - 1) / TW;
     for (int py = 0; py < H; ++py)
         for (int px = 0; px < W; ++px) {
+            if (mask && !mask[(int64_t)py * W + px]) continue;
             int64_t t = (int64_t)(py / TH) * Gx + px / TW;
             double C[3], T;
             int fl;

@@ -199,7 +199,8 @@ def bins_for_render(proj, W, H, TW, TH, params: Params = None):
     return bin_view(proj["xy"][:, 0], proj["xy"][:, 1], r, proj["depth"], W, H, TW, TH)
 
 
-def render_view(proj, W, H, TW=16, TH=16, params: Params = None, bins=None):
+def render_view(proj, W, H, TW=16, TH=16, params: Params = None, bins=None, mask=None):
+    """mask: optional [H,W] bool; only those pixels are computed (others 0)."""
     params = params or Params()
     if bins is None:
         bins = bins_for_render(proj, W, H, TW, TH, params)
@@ -209,10 +210,11 @@ def render_view(proj, W, H, TW=16, TH=16, params: Params = None, bins=None):
     nc = np.zeros((H, W), np.int32)
     fl = np.zeros((H, W), np.int32)
     prm = params.c()
+    m = None if mask is None else np.ascontiguousarray(mask, np.uint8)
     lib().or_render(_p(proj["xy"]), _p(proj["conic"]), _p(proj["opac"]), _p(proj["rgb"]),
                     _p(proj["radius"]), _p(proj["r_real"]), _p(proj["depth"]), W, H, TW, TH,
                     _p(np.ascontiguousarray(ranges)), _p(np.ascontiguousarray(ids)), ctypes.byref(prm),
-                    _p(img), _p(T), _p(nc), _p(fl))
+                    None if m is None else _p(m), _p(img), _p(T), _p(nc), _p(fl))
     return dict(image=img, T=T, n_contrib=nc, flags=fl)
 
 
@@ -264,16 +266,17 @@ def pose_twist(viewmat, gR, gt):
 # whole-path helpers
 # ---------------------------------------------------------------------------
 
-def forward(scene, views, TW=16, TH=16, params: Params = None):
+def forward(scene, views, TW=16, TH=16, params: Params = None, masks=None):
     """Per view: projection, tile lists and rendering. Returns a list of dicts
-    with keys proj, bins, image [3,H,W], T, n_contrib, flags."""
+    with keys proj, bins, image [3,H,W], T, n_contrib, flags. masks: optional
+    per-view [H,W] bool arrays restricting the rendered pixels."""
     params = params or Params()
     out = []
     for v in range(views.n):
         W, H = int(views.width[v]), int(views.height[v])
         proj = project_view(scene, views, v, params)
         bins = bins_for_render(proj, W, H, TW, TH, params)
-        r = render_view(proj, W, H, TW, TH, params, bins)
+        r = render_view(proj, W, H, TW, TH, params, bins, None if masks is None else masks[v])
         r.update(proj=proj, bins=bins)
         out.append(r)
     return out

@@ -1,0 +1,297 @@
+"""ctypes binding of libgsplat_gb300.so (include/gs.h), same names as the C ABI.
+
+Argument marshalling only: every step of the rasterizer runs in the CUDA
+library. torch provides device memory and the current stream. There is no
+fallback: if the library is missing or the device is not CUDA, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsplat_gb300.so")
+
+GS_OK, GS_ERR_ARG, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_UNSUPPORTED, GS_ERR_OVERFLOW = range(6)
+GS_MAX_VIEWS = 64
+GS_RECORD_FLOATS = 16
+GS_GRAD2D_FLOATS = 12
+GS_NUM_COUNTERS = 16
+
+EXPORTED = ["gs_config_default", "gs_num_slots", "gs_slot_base", "gs_num_tiles", "gs_tile_base",
+            "gs_num_image_floats", "gs_pixel_base", "gs_pose_blocks", "gs_project", "gs_bin_sort",
+            "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version"]
+
+
+class GsError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {error_string(code)} (code {code})")
+        self.code = code
+
+
+class gs_config(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("pixel_gate", ctypes.c_int),
+                ("near_z", ctypes.c_float), ("dilation", ctypes.c_float), ("alpha_min", ctypes.c_float),
+                ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float), ("fov_clamp", ctypes.c_float),
+                ("bg", ctypes.c_float * 3)]
+
+
+class gs_gaussians(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int), ("means", ctypes.c_void_p),
+                ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+class gs_views(ctypes.Structure):
+    _fields_ = [("n_views", ctypes.c_int), ("viewmats", ctypes.c_void_p), ("intrinsics", ctypes.c_void_p),
+                ("width", ctypes.c_void_p), ("height", ctypes.c_void_p), ("gauss_begin", ctypes.c_void_p),
+                ("gauss_count", ctypes.c_void_p)]
+
+
+class gs_bins(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("tile_ranges", ctypes.c_void_p), ("keys", ctypes.c_void_p),
+                ("ids", ctypes.c_void_p), ("keys_tmp", ctypes.c_void_p), ("tile_order", ctypes.c_void_p),
+                ("tile_scratch", ctypes.c_void_p), ("counters", ctypes.c_void_p)]
+
+
+class gs_grads(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("grad2d", ctypes.c_void_p),
+                ("pose_partials", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load():
+    """Load the library (built by ``__graft_entry__.build()`` or
+    ``paper_2509_25191_gb300.build``). Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libgsplat_gb300.so not built ({LIB_PATH} missing); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name in ["gs_num_slots", "gs_slot_base", "gs_num_tiles", "gs_tile_base", "gs_num_image_floats",
+                 "gs_pixel_base"]:
+        getattr(lib, name).restype = ctypes.c_int64
+    lib.gs_error_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def error_string(code: int) -> str:
+    try:
+        return load().gs_error_string(int(code)).decode()
+    except RuntimeError:
+        return f"status {code}"
+
+
+def _check(rc, where):
+    if rc != GS_OK:
+        raise GsError(rc, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# argument structures
+# ---------------------------------------------------------------------------
+
+def config(tile=(16, 16), pixel_gate=True, bg=(0.0, 0.0, 0.0), near=0.2, dilation=0.3,
+           alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, fov_clamp=1.3) -> gs_config:
+    c = gs_config()
+    load().gs_config_default(ctypes.byref(c))
+    c.tile_w, c.tile_h = int(tile[0]), int(tile[1])
+    c.pixel_gate = int(bool(pixel_gate))
+    c.near_z, c.dilation, c.alpha_min, c.alpha_max, c.t_min, c.fov_clamp = \
+        near, dilation, alpha_min, alpha_max, t_min, fov_clamp
+    c.bg = (ctypes.c_float * 3)(*bg)
+    return c
+
+
+class Gaussians:
+    """Device tensors of the Gaussians (float32, contiguous, on one CUDA device)."""
+
+    def __init__(self, means, log_scales, quats, opacity_logits, sh):
+        self.means, self.log_scales, self.quats = means, log_scales, quats
+        self.opacity_logits, self.sh = opacity_logits, sh
+        K = sh.shape[1]
+        self.sh_degree = int(round(K ** 0.5)) - 1
+        assert (self.sh_degree + 1) ** 2 == K and sh.shape[2] == 3
+        self.n = int(means.shape[0])
+        for t in (means, log_scales, quats, opacity_logits, sh):
+            assert t.dtype == torch.float32 and t.is_cuda and t.is_contiguous()
+
+    def c(self) -> gs_gaussians:
+        return gs_gaussians(self.n, self.sh_degree, _ptr(self.means), _ptr(self.log_scales), _ptr(self.quats),
+                            _ptr(self.opacity_logits), _ptr(self.sh))
+
+    @staticmethod
+    def from_scene(scene, device="cuda"):
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32)).to(device)
+        return Gaussians(f(scene.means), f(scene.log_scales), f(scene.quats), f(scene.opacity_logits), f(scene.sh))
+
+
+class Views:
+    """Views of one call: device pose/intrinsics tensors plus host layout."""
+
+    def __init__(self, viewmats, intrinsics, width, height, gauss_begin, gauss_count):
+        self.viewmats, self.intrinsics = viewmats, intrinsics
+        self.width = np.ascontiguousarray(width, np.int32)
+        self.height = np.ascontiguousarray(height, np.int32)
+        self.gauss_begin = np.ascontiguousarray(gauss_begin, np.int64)
+        self.gauss_count = np.ascontiguousarray(gauss_count, np.int64)
+        self.n = int(self.width.shape[0])
+        assert 1 <= self.n <= GS_MAX_VIEWS
+
+    def c(self) -> gs_views:
+        return gs_views(self.n, _ptr(self.viewmats), _ptr(self.intrinsics),
+                        self.width.ctypes.data_as(ctypes.c_void_p), self.height.ctypes.data_as(ctypes.c_void_p),
+                        self.gauss_begin.ctypes.data_as(ctypes.c_void_p),
+                        self.gauss_count.ctypes.data_as(ctypes.c_void_p))
+
+    @staticmethod
+    def from_synth(views, device="cuda", viewmats=None):
+        vm = viewmats if viewmats is not None else torch.as_tensor(views.viewmats, dtype=torch.float32).to(device)
+        return Views(vm.contiguous(), torch.as_tensor(views.intrinsics, dtype=torch.float32).to(device),
+                     views.width, views.height, views.gauss_begin, views.gauss_count)
+
+    # layout
+    def num_slots(self):
+        return int(self.gauss_count.sum())
+
+    def slot_base(self, v):
+        return int(self.gauss_count[:v].sum())
+
+    def num_tiles(self, cfg):
+        return int(load().gs_num_tiles(ctypes.byref(self.c()), ctypes.byref(cfg)))
+
+    def tile_base(self, cfg, v):
+        return int(load().gs_tile_base(ctypes.byref(self.c()), ctypes.byref(cfg), v))
+
+    def num_image_floats(self):
+        return int(3 * (self.width.astype(np.int64) * self.height).sum())
+
+    def pixel_base(self, v):
+        return int(3 * (self.width[:v].astype(np.int64) * self.height[:v]).sum())
+
+    @property
+    def pixels(self):
+        return int((self.width.astype(np.int64) * self.height).sum())
+
+
+class Bins:
+    """Caller-owned tile-list buffers (device)."""
+
+    def __init__(self, n_tiles, capacity, device="cuda"):
+        self.n_tiles, self.capacity = int(n_tiles), int(capacity)
+        i32 = dict(dtype=torch.int32, device=device)
+        self.tile_ranges = torch.empty(max(1, self.n_tiles) * 2, **i32)
+        self.tile_order = torch.empty(max(1, self.n_tiles), **i32)
+        self.tile_scratch = torch.empty(max(1, self.n_tiles), **i32)
+        self.counters = torch.zeros(GS_NUM_COUNTERS, **i32)
+        cap = max(1, self.capacity)
+        self.keys = torch.empty(cap, dtype=torch.int64, device=device)
+        self.keys_tmp = torch.empty(cap, dtype=torch.int64, device=device)
+        self.ids = torch.empty(cap, dtype=torch.int32, device=device)
+
+    def c(self) -> gs_bins:
+        return gs_bins(self.capacity, _ptr(self.tile_ranges), _ptr(self.keys), _ptr(self.ids), _ptr(self.keys_tmp),
+                       _ptr(self.tile_order), _ptr(self.tile_scratch), _ptr(self.counters))
+
+
+class Grads:
+    """Gradient outputs and backward scratch (device)."""
+
+    def __init__(self, n, sh_degree, n_slots, n_views, device="cuda", want_gaussian_grads=True):
+        K = (sh_degree + 1) ** 2
+        f = dict(dtype=torch.float32, device=device)
+        nn = max(1, n) if want_gaussian_grads else 1
+        self.means = torch.empty(nn, 3, **f)
+        self.log_scales = torch.empty(nn, 3, **f)
+        self.quats = torch.empty(nn, 4, **f)
+        self.opacity_logits = torch.empty(nn, **f)
+        self.sh = torch.empty(nn, K, 3, **f)
+        self.grad2d = torch.empty(max(1, n_slots), GS_GRAD2D_FLOATS, **f)
+        self.n_blocks = int(load().gs_pose_blocks(ctypes.c_int64(n)))
+        self.pose_partials = torch.empty(n_views * self.n_blocks * 12, **f)
+
+    def c(self) -> gs_grads:
+        return gs_grads(_ptr(self.means), _ptr(self.log_scales), _ptr(self.quats), _ptr(self.opacity_logits),
+                        _ptr(self.sh), _ptr(self.grad2d), _ptr(self.pose_partials))
+
+
+def new_status(device="cuda"):
+    return torch.zeros(4, dtype=torch.int32, device=device)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one wrapper per entry point
+# ---------------------------------------------------------------------------
+
+def gs_project(g: Gaussians, views: Views, cfg: gs_config, proj, status=None, stream=None):
+    _check(load().gs_project(ctypes.byref(g.c()), ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj),
+                             _ptr(status), _stream(stream)), "gs_project")
+
+
+def gs_bin_sort(views: Views, cfg: gs_config, proj, bins: Bins, status=None, stream=None):
+    _check(load().gs_bin_sort(ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj), ctypes.byref(bins.c()),
+                              _ptr(status), _stream(stream)), "gs_bin_sort")
+
+
+def gs_render_fwd(views: Views, cfg: gs_config, proj, bins: Bins, image, status=None, stream=None):
+    _check(load().gs_render_fwd(ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj), ctypes.byref(bins.c()),
+                                _ptr(image), _ptr(status), _stream(stream)), "gs_render_fwd")
+
+
+def gs_render_bwd(g: Gaussians, views: Views, cfg: gs_config, proj, bins: Bins, image, dL_dimage, grads: Grads,
+                  want_gaussian_grads=True, status=None, stream=None):
+    _check(load().gs_render_bwd(ctypes.byref(g.c()), ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj),
+                                ctypes.byref(bins.c()), _ptr(image), _ptr(dL_dimage), ctypes.byref(grads.c()),
+                                int(bool(want_gaussian_grads)), _ptr(status), _stream(stream)), "gs_render_bwd")
+
+
+def gs_rasterize_bwd(views: Views, cfg: gs_config, proj, bins: Bins, image, dL_dimage, grad2d, status=None,
+                     stream=None):
+    _check(load().gs_rasterize_bwd(ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj), ctypes.byref(bins.c()),
+                                   _ptr(image), _ptr(dL_dimage), _ptr(grad2d), _ptr(status), _stream(stream)),
+           "gs_rasterize_bwd")
+
+
+def gs_project_bwd(g: Gaussians, views: Views, cfg: gs_config, proj, grads: Grads, want_gaussian_grads=True,
+                   status=None, stream=None):
+    _check(load().gs_project_bwd(ctypes.byref(g.c()), ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj),
+                                 _ptr(grads.grad2d), ctypes.byref(grads.c()), int(bool(want_gaussian_grads)),
+                                 _ptr(status), _stream(stream)), "gs_project_bwd")
+
+
+def pair_counts(bins: Bins):
+    """(fwd evaluated, fwd composited, bwd evaluated, bwd composited) pixel-
+    Gaussian pairs of the last render calls (reads the device counters)."""
+    c = bins.counters.cpu().numpy().view(np.int64)
+    return int(c[4]), int(c[5]), int(c[6]), int(c[7])
+
+
+def gs_pose_grad(views: Views, pose_partials, n_blocks, dL_dviewmat, dL_dtwist=None, stream=None):
+    _check(load().gs_pose_grad(ctypes.byref(views.c()), _ptr(pose_partials), int(n_blocks), _ptr(dL_dviewmat),
+                               _ptr(dL_dtwist), _stream(stream)), "gs_pose_grad")
+
+
+def gs_l1_loss(image, target, loss, dL_dimage, stream=None):
+    _check(load().gs_l1_loss(_ptr(image), _ptr(target), ctypes.c_int64(image.numel()), _ptr(loss),
+                             _ptr(dL_dimage), _stream(stream)), "gs_l1_loss")

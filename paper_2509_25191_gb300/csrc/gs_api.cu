@@ -1,0 +1,303 @@
+// extern "C" entry points of libgsplat_gb300.so (declared in include/gs.h):
+// host-side argument checks, the per-call launch description, and dispatch
+// to the kernels. No allocation, no synchronisation.
+#include <string.h>
+
+#include "gs_common.cuh"
+
+namespace gsk {
+
+int launch_project(const Launch &L, int deg, const gs_gaussians *g, const float *viewmats, const float *intr,
+                   float *proj, cudaStream_t st);
+int launch_bin_sort(const Launch &L, const float *proj, const gs_bins *b, int32_t *status, cudaStream_t st);
+int launch_render_fwd(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st);
+int launch_render_bwd(const Launch &L, const float *proj, const gs_bins *b, const float *image,
+                      const float *dL_dimage, float *grad2d, cudaStream_t st);
+int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const float *viewmats, const float *intr,
+                       const float *proj, const float *grad2d, const gs_grads *out, int want_gauss, int nblk,
+                       cudaStream_t st);
+int launch_pose_reduce(int n_views, const float *partials, int nblk, const float *viewmats, float *out_rt,
+                       float *out_twist, cudaStream_t st);
+int launch_l1(const float *image, const float *target, long long n, float *loss, float *grad, cudaStream_t st);
+int pose_blocks(long long n);
+
+int num_sms() {
+    static int cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
+static bool tile_supported(int tw, int th) {
+    return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 16 && th == 8) || (tw == 32 && th == 8) ||
+           (tw == 32 && th == 16);
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Validate views/config and fill the launch description.
+static int build_launch(const gs_views *vw, const gs_config *cfg, Launch &L) {
+    if (!vw || !cfg) return GS_ERR_ARG;
+    const int V = vw->n_views;
+    if (V < 1 || V > GS_MAX_VIEWS) return GS_ERR_ARG;
+    if (!vw->width || !vw->height || !vw->gauss_begin || !vw->gauss_count) return GS_ERR_ARG;
+    if (!tile_supported(cfg->tile_w, cfg->tile_h)) return GS_ERR_UNSUPPORTED;
+    memset(&L, 0, sizeof L);
+    L.n_views = V;
+    L.tw = cfg->tile_w;
+    L.th = cfg->tile_h;
+    L.pixel_gate = cfg->pixel_gate ? 1 : 0;
+    L.near_z = cfg->near_z;
+    L.dilation = cfg->dilation;
+    L.alpha_min = cfg->alpha_min;
+    L.alpha_max = cfg->alpha_max;
+    L.t_min = cfg->t_min;
+    L.fov_clamp = cfg->fov_clamp;
+    L.bg[0] = cfg->bg[0]; L.bg[1] = cfg->bg[1]; L.bg[2] = cfg->bg[2];
+    if (!(L.alpha_max > 0.f && L.alpha_max < 1.f) || !(L.t_min > 0.f)) return GS_ERR_ARG;
+    long long slot = 0, pix = 0, tiles = 0;
+    for (int v = 0; v < V; ++v) {
+        const int W = vw->width[v], H = vw->height[v];
+        const long long gb = vw->gauss_begin[v], gc = vw->gauss_count[v];
+        if (W < 1 || H < 1 || W > 65536 || H > 65536 || gb < 0 || gc < 0 || gc > 0x7fffffffLL) return GS_ERR_ARG;
+        ViewDesc &d = L.v[v];
+        d.W = W; d.H = H;
+        d.Gx = (W + L.tw - 1) / L.tw;
+        d.Gy = (H + L.th - 1) / L.th;
+        d.tile_base = (int)tiles;
+        d.g_count = (int)gc;
+        d.g_begin = gb;
+        d.slot_base = slot;
+        d.pix_base = pix;
+        slot += gc;
+        pix += 3LL * W * H;
+        tiles += (long long)d.Gx * d.Gy;
+        if (tiles > 0x7fffffffLL) return GS_ERR_ARG;
+        // scene groups: runs of views with the same Gaussian range
+        if (v > 0 && gb == vw->gauss_begin[v - 1] && gc == vw->gauss_count[v - 1]) {
+            L.s[L.n_scenes - 1].v_end = v + 1;
+        } else {
+            SceneDesc &s = L.s[L.n_scenes++];
+            s.g_begin = gb; s.g_count = (int)gc; s.v_begin = v; s.v_end = v + 1;
+        }
+    }
+    if (slot > 0xffffffffLL) return GS_ERR_ARG;   // slots are 32-bit in the sort keys
+    // scene groups must not overlap (each Gaussian is handled by one thread)
+    for (int a = 0; a < L.n_scenes; ++a)
+        for (int b = a + 1; b < L.n_scenes; ++b) {
+            const SceneDesc &x = L.s[a], &y = L.s[b];
+            if (x.g_begin < y.g_begin + y.g_count && y.g_begin < x.g_begin + x.g_count) return GS_ERR_ARG;
+        }
+    long long thr = 0;
+    for (int a = 0; a < L.n_scenes; ++a) {
+        L.s[a].thread_base = thr;
+        thr += L.s[a].g_count;
+    }
+    L.n_threads = thr;
+    L.n_slots = slot;
+    L.n_tiles = (int)tiles;
+    return GS_OK;
+}
+
+static int check_gaussians(const gs_gaussians *g, const gs_views *vw) {
+    if (!g || g->n < 0 || g->sh_degree < 0 || g->sh_degree > 3) return g && (g->sh_degree > 3) ? GS_ERR_UNSUPPORTED : GS_ERR_ARG;
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh)) return GS_ERR_ARG;
+    if (g->n > 0 && !aligned16(g->quats)) return GS_ERR_ARG;
+    if (g->n > 0 && (g->sh_degree == 1 || g->sh_degree == 3) && !aligned16(g->sh)) return GS_ERR_ARG;
+    for (int v = 0; v < vw->n_views; ++v)
+        if (vw->gauss_begin[v] + vw->gauss_count[v] > g->n) return GS_ERR_ARG;
+    return GS_OK;
+}
+
+}  // namespace gsk
+
+using namespace gsk;
+
+extern "C" {
+
+void gs_config_default(gs_config *cfg) {
+    if (!cfg) return;
+    cfg->tile_w = 16;
+    cfg->tile_h = 16;
+    cfg->pixel_gate = 1;
+    cfg->near_z = 0.2f;
+    cfg->dilation = 0.3f;
+    cfg->alpha_min = 1.0f / 255.0f;
+    cfg->alpha_max = 0.99f;
+    cfg->t_min = 1e-4f;
+    cfg->fov_clamp = 1.3f;
+    cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.0f;
+}
+
+int64_t gs_num_slots(const gs_views *vw) {
+    if (!vw || vw->n_views < 1) return 0;
+    int64_t s = 0;
+    for (int v = 0; v < vw->n_views; ++v) s += vw->gauss_count[v];
+    return s;
+}
+
+int64_t gs_slot_base(const gs_views *vw, int v) {
+    int64_t s = 0;
+    for (int u = 0; u < v; ++u) s += vw->gauss_count[u];
+    return s;
+}
+
+int64_t gs_num_tiles(const gs_views *vw, const gs_config *cfg) {
+    if (!vw || !cfg || cfg->tile_w < 1 || cfg->tile_h < 1) return 0;
+    int64_t t = 0;
+    for (int v = 0; v < vw->n_views; ++v)
+        t += (int64_t)((vw->width[v] + cfg->tile_w - 1) / cfg->tile_w) * ((vw->height[v] + cfg->tile_h - 1) / cfg->tile_h);
+    return t;
+}
+
+int64_t gs_tile_base(const gs_views *vw, const gs_config *cfg, int v) {
+    int64_t t = 0;
+    for (int u = 0; u < v; ++u)
+        t += (int64_t)((vw->width[u] + cfg->tile_w - 1) / cfg->tile_w) * ((vw->height[u] + cfg->tile_h - 1) / cfg->tile_h);
+    return t;
+}
+
+int64_t gs_num_image_floats(const gs_views *vw) {
+    if (!vw) return 0;
+    int64_t p = 0;
+    for (int v = 0; v < vw->n_views; ++v) p += 3LL * vw->width[v] * vw->height[v];
+    return p;
+}
+
+int64_t gs_pixel_base(const gs_views *vw, int v) {
+    int64_t p = 0;
+    for (int u = 0; u < v; ++u) p += 3LL * vw->width[u] * vw->height[u];
+    return p;
+}
+
+int gs_pose_blocks(int64_t n) { return pose_blocks(n); }
+
+int gs_project(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, float *proj, int32_t *status,
+               void *stream) {
+    (void)status;
+    Launch L;
+    int rc = build_launch(vw, cfg, L);
+    if (rc) return rc;
+    if ((rc = check_gaussians(g, vw))) return rc;
+    if (!vw->viewmats || !vw->intrinsics || (L.n_slots > 0 && !proj)) return GS_ERR_ARG;
+    if (!aligned16(proj)) return GS_ERR_ARG;
+    return launch_project(L, g->sh_degree, g, vw->viewmats, vw->intrinsics, proj, (cudaStream_t)stream);
+}
+
+int gs_bin_sort(const gs_views *vw, const gs_config *cfg, const float *proj, const gs_bins *b, int32_t *status,
+                void *stream) {
+    Launch L;
+    int rc = build_launch(vw, cfg, L);
+    if (rc) return rc;
+    if (!b || !proj || !b->tile_ranges || !b->tile_order || !b->tile_scratch || !b->counters) return GS_ERR_ARG;
+    if (b->capacity < 0) return GS_ERR_ARG;
+    if (b->capacity > 0 && (!b->keys || !b->ids || !b->keys_tmp)) return GS_ERR_ARG;
+    if (!aligned16(proj) || !aligned16(b->tile_ranges)) return GS_ERR_ARG;
+    return launch_bin_sort(L, proj, b, status, (cudaStream_t)stream);
+}
+
+int gs_render_fwd(const gs_views *vw, const gs_config *cfg, const float *proj, const gs_bins *b, float *image,
+                  int32_t *status, void *stream) {
+    (void)status;
+    Launch L;
+    int rc = build_launch(vw, cfg, L);
+    if (rc) return rc;
+    if (!b || !proj || !image || !b->tile_ranges || !b->tile_order || !b->counters || !b->ids) return GS_ERR_ARG;
+    return launch_render_fwd(L, proj, b, image, (cudaStream_t)stream);
+}
+
+int gs_rasterize_bwd(const gs_views *vw, const gs_config *cfg, const float *proj, const gs_bins *b,
+                     const float *image, const float *dL_dimage, float *grad2d, int32_t *status, void *stream) {
+    (void)status;
+    Launch L;
+    int rc = build_launch(vw, cfg, L);
+    if (rc) return rc;
+    if (!b || !proj || !image || !dL_dimage || !grad2d || !b->tile_ranges || !b->tile_order || !b->counters ||
+        !b->ids)
+        return GS_ERR_ARG;
+    if (!aligned16(grad2d)) return GS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_FLOATS * (size_t)L.n_slots, st) != cudaSuccess)
+        return GS_ERR_CUDA;
+    return launch_render_bwd(L, proj, b, image, dL_dimage, grad2d, st);
+}
+
+int gs_project_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, const float *proj,
+                   const float *grad2d, const gs_grads *out, int want_gaussian_grads, int32_t *status,
+                   void *stream) {
+    (void)status;
+    Launch L;
+    int rc = build_launch(vw, cfg, L);
+    if (rc) return rc;
+    if ((rc = check_gaussians(g, vw))) return rc;
+    if (!proj || !grad2d || !out || !out->pose_partials || !vw->viewmats || !vw->intrinsics) return GS_ERR_ARG;
+    if (want_gaussian_grads && g->n > 0 &&
+        (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->sh))
+        return GS_ERR_ARG;
+    if (!aligned16(grad2d) || (want_gaussian_grads && g->n > 0 && !aligned16(out->quats))) return GS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (want_gaussian_grads) {
+        // Gaussians outside every view's range still get (zero) gradients
+        long long covered = 0;
+        for (int a = 0; a < L.n_scenes; ++a) covered += L.s[a].g_count;
+        if (covered != g->n && g->n > 0) {
+            const int K = (g->sh_degree + 1) * (g->sh_degree + 1);
+            const size_t n = (size_t)g->n;
+            if (cudaMemsetAsync(out->means, 0, sizeof(float) * 3 * n, st) ||
+                cudaMemsetAsync(out->log_scales, 0, sizeof(float) * 3 * n, st) ||
+                cudaMemsetAsync(out->quats, 0, sizeof(float) * 4 * n, st) ||
+                cudaMemsetAsync(out->opacity_logits, 0, sizeof(float) * n, st) ||
+                cudaMemsetAsync(out->sh, 0, sizeof(float) * 3 * K * n, st))
+                return GS_ERR_CUDA;
+        }
+    }
+    return launch_project_bwd(L, g->sh_degree, g, vw->viewmats, vw->intrinsics, proj, grad2d, out,
+                              want_gaussian_grads, pose_blocks(g->n), st);
+}
+
+int gs_render_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, const float *proj,
+                  const gs_bins *b, const float *image, const float *dL_dimage, const gs_grads *out,
+                  int want_gaussian_grads, int32_t *status, void *stream) {
+    if (!out) return GS_ERR_ARG;
+    int rc = check_gaussians(g, vw);
+    if (rc) return rc;
+    rc = gs_rasterize_bwd(vw, cfg, proj, b, image, dL_dimage, out->grad2d, status, stream);
+    if (rc) return rc;
+    return gs_project_bwd(g, vw, cfg, proj, out->grad2d, out, want_gaussian_grads, status, stream);
+}
+
+int gs_pose_grad(const gs_views *vw, const float *pose_partials, int n_blocks, float *dL_dviewmat,
+                 float *dL_dtwist, void *stream) {
+    if (!vw || vw->n_views < 1 || vw->n_views > GS_MAX_VIEWS || !pose_partials || !dL_dviewmat || n_blocks < 1 ||
+        !vw->viewmats)
+        return GS_ERR_ARG;
+    return launch_pose_reduce(vw->n_views, pose_partials, n_blocks, vw->viewmats, dL_dviewmat, dL_dtwist,
+                              (cudaStream_t)stream);
+}
+
+int gs_l1_loss(const float *image, const float *target, int64_t count, float *loss, float *dL_dimage,
+               void *stream) {
+    if (count < 0 || !loss || (count > 0 && (!image || !target || !dL_dimage))) return GS_ERR_ARG;
+    return launch_l1(image, target, count, loss, dL_dimage, (cudaStream_t)stream);
+}
+
+const char *gs_error_string(int code) {
+    switch (code) {
+    case GS_OK: return "ok";
+    case GS_ERR_ARG: return "invalid argument";
+    case GS_ERR_CUDA: return "CUDA error";
+    case GS_ERR_CAPACITY: return "instance capacity exceeded";
+    case GS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case GS_ERR_OVERFLOW: return "more than 2^31-1 tile instances";
+    default: return "unknown status";
+    }
+}
+
+int gs_version(void) { return 1; }
+
+}  // extern "C"

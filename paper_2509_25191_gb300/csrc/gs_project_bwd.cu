@@ -1,0 +1,440 @@
+// Backward of the projection: per-slot 2D gradients -> raw Gaussian
+// parameters and camera poses.
+//
+// One thread per Gaussian (fixed grid, grid-stride), looping over the views of
+// its scene: the Gaussian's parameters are read once, its gradients are summed
+// over views in registers and written once (overwrite). Each view's pose
+// gradient (dL/dR, dL/dt; Section 3.4 needs it for the pose residuals) is
+// summed over a warp with shuffles, kept per warp in shared memory, and
+// written as one partial per block; k_pose_reduce then sums the partials in a
+// fixed order, so the pose gradient is deterministic given grad2d.
+//
+// Chain (FP32, exact derivative of the forward in gs_project.cu):
+//   conic -> dilated 2D covariance (inverse), Sigma' = T Sigma T^T with
+//   T = J R_v, J with the tangent clamp (zero derivative through a clamped
+//   tangent), mean2D = f x / z + c, m = R_v mu + t_v, Sigma = M M^T with
+//   M = R(q) diag(exp l), q normalised, o = sigmoid, colour = max(0,
+//   sum f_k Y_k(d) + 0.5), d = normalise(mu - C_v), C_v = -R_v^T t_v.
+#include "gs_common.cuh"
+
+namespace gsk {
+
+constexpr int PB_THREADS = 256;
+constexpr int PB_WARPS = PB_THREADS / 32;
+
+template <int DEG, bool GAUSS>
+__global__ void __launch_bounds__(PB_THREADS) k_project_bwd(
+    const Launch L, const float *__restrict__ means, const float *__restrict__ log_scales,
+    const float *__restrict__ quats, const float *__restrict__ logits, const float *__restrict__ sh,
+    const float *__restrict__ viewmats, const float *__restrict__ intr, const float4 *__restrict__ proj,
+    const float4 *__restrict__ grad2d, float *__restrict__ g_means, float *__restrict__ g_log_scales,
+    float *__restrict__ g_quats, float *__restrict__ g_logits, float *__restrict__ g_sh,
+    float *__restrict__ pose_partials) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    __shared__ float s_pose[PB_WARPS][GS_MAX_VIEWS][12];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < PB_WARPS * GS_MAX_VIEWS * 12; i += PB_THREADS) (&s_pose[0][0][0])[i] = 0.f;
+    __syncthreads();
+
+    const long long stride = (long long)gridDim.x * PB_THREADS;
+    for (long long base = (long long)blockIdx.x * PB_THREADS; base < L.n_threads; base += stride) {
+        const long long gid = base + threadIdx.x;
+        const bool valid = gid < L.n_threads;
+        const int s = valid ? scene_of_thread(L, gid) : 0;
+        const long long li = valid ? gid - L.s[s].thread_base : 0;
+        const long long i = L.s[s].g_begin + li;
+        const int vb = valid ? L.s[s].v_begin : 0x7fffffff, ve = valid ? L.s[s].v_end : 0;
+        const int wvb = __reduce_min_sync(0xffffffffu, vb), wve = __reduce_max_sync(0xffffffffu, ve);
+
+        float mx = 0.f, my = 0.f, mz = 0.f, sc[3] = {0.f, 0.f, 0.f}, qn[4] = {1.f, 0.f, 0.f, 0.f}, qlen = 1.f;
+        float Rq[9], M[9], S00 = 0, S01 = 0, S02 = 0, S11 = 0, S12 = 0, S22 = 0, opac = 0.f;
+        float f[3 * K];
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) f[k] = 0.f;
+        if (valid) {
+            mx = means[3 * i]; my = means[3 * i + 1]; mz = means[3 * i + 2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sc[a] = expf(log_scales[3 * i + a]);
+            const float4 q = reinterpret_cast<const float4 *>(quats)[i];
+            qlen = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+            const float iq = 1.f / qlen;
+            qn[0] = q.x * iq; qn[1] = q.y * iq; qn[2] = q.z * iq; qn[3] = q.w * iq;
+            opac = 1.f / (1.f + expf(-logits[i]));
+#pragma unroll
+            for (int k = 0; k < 3 * K; ++k) f[k] = sh[(long long)3 * K * i + k];
+        }
+        quat_rot(qn[0], qn[1], qn[2], qn[3], Rq);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) M[3 * a + b] = Rq[3 * a + b] * sc[b];
+        S00 = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+        S01 = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+        S02 = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+        S11 = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+        S12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+        S22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+
+        // accumulators over views
+        float gm[3] = {0.f, 0.f, 0.f}, go = 0.f;
+        float GS00 = 0, GS01 = 0, GS02 = 0, GS11 = 0, GS12 = 0, GS22 = 0;   // full-matrix entries, symmetric
+        float gf[3 * K];
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) gf[k] = 0.f;
+
+        for (int v = wvb; v < wve; ++v) {
+            float pg[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) pg[c] = 0.f;
+            bool contrib = false;
+            if (v >= vb && v < ve) {
+                const long long slot = L.v[v].slot_base + li;
+                const float4 ga4 = grad2d[3 * slot], gb4 = grad2d[3 * slot + 1], gc4 = grad2d[3 * slot + 2];
+                contrib = ga4.x != 0.f || ga4.y != 0.f || ga4.z != 0.f || ga4.w != 0.f || gb4.x != 0.f ||
+                          gb4.y != 0.f || gb4.z != 0.f || gb4.w != 0.f || gc4.x != 0.f;
+                if (contrib) {
+                    const float gx = ga4.x, gy = ga4.y, gA = ga4.z, gB = ga4.w, gC = gb4.x, gop = gb4.y;
+                    const float grgb[3] = {gb4.z, gb4.w, gc4.x};
+                    const int clamp_bits = __float_as_int(proj[4 * slot + 3].y);
+                    const ViewDesc &vd = L.v[v];
+                    const float *vm = viewmats + 12 * v;
+                    float R[9], t[3];
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) R[a] = __ldg(vm + a);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) t[a] = __ldg(vm + 9 + a);
+                    const float fx = __ldg(intr + 4 * v), fy = __ldg(intr + 4 * v + 1);
+                    const float x = R[0] * mx + R[1] * my + R[2] * mz + t[0];
+                    const float y = R[3] * mx + R[4] * my + R[5] * mz + t[1];
+                    const float z = R[6] * mx + R[7] * my + R[8] * mz + t[2];
+                    const float limx = L.fov_clamp * 0.5f * (float)vd.W / fx;
+                    const float limy = L.fov_clamp * 0.5f * (float)vd.H / fy;
+                    const float iz = 1.f / z, iz2 = iz * iz;
+                    const float ur = x * iz, wr = y * iz;
+                    const bool u_in = ur >= -limx && ur <= limx, w_in = wr >= -limy && wr <= limy;
+                    const float u = fminf(fmaxf(ur, -limx), limx), w = fminf(fmaxf(wr, -limy), limy);
+                    const float J00 = fx * iz, J02 = -fx * u * iz, J11 = fy * iz, J12 = -fy * w * iz;
+                    float T[6];
+                    T[0] = J00 * R[0] + J02 * R[6]; T[1] = J00 * R[1] + J02 * R[7]; T[2] = J00 * R[2] + J02 * R[8];
+                    T[3] = J11 * R[3] + J12 * R[6]; T[4] = J11 * R[4] + J12 * R[7]; T[5] = J11 * R[5] + J12 * R[8];
+                    float TS[6];   // T Sigma
+                    TS[0] = T[0] * S00 + T[1] * S01 + T[2] * S02;
+                    TS[1] = T[0] * S01 + T[1] * S11 + T[2] * S12;
+                    TS[2] = T[0] * S02 + T[1] * S12 + T[2] * S22;
+                    TS[3] = T[3] * S00 + T[4] * S01 + T[5] * S02;
+                    TS[4] = T[3] * S01 + T[4] * S11 + T[5] * S12;
+                    TS[5] = T[3] * S02 + T[4] * S12 + T[5] * S22;
+                    const float a = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + L.dilation;
+                    const float b = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
+                    const float c = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + L.dilation;
+                    const float det = a * c - b * b;
+                    const float id2 = 1.f / (det * det);
+
+                    go += gop;
+
+                    // colour -> SH and view direction
+                    const float Cx = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
+                    const float Cy = -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]);
+                    const float Cz = -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]);
+                    const float dxv = mx - Cx, dyv = my - Cy, dzv = mz - Cz;
+                    const float idl = rsqrtf(dxv * dxv + dyv * dyv + dzv * dzv);
+                    const float d0 = dxv * idl, d1 = dyv * idl, d2 = dzv * idl;
+                    float graw[3];
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) graw[ch] = (clamp_bits >> ch) & 1 ? 0.f : grgb[ch];
+                    float gC3[3] = {0.f, 0.f, 0.f};
+                    if (DEG > 0 || GAUSS) {
+                        float Yb[16];
+                        sh_basis<DEG>(d0, d1, d2, Yb);
+                        float gY[16];
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            gY[k] = f[3 * k] * graw[0] + f[3 * k + 1] * graw[1] + f[3 * k + 2] * graw[2];
+                            if (GAUSS) {
+                                gf[3 * k] += Yb[k] * graw[0];
+                                gf[3 * k + 1] += Yb[k] * graw[1];
+                                gf[3 * k + 2] += Yb[k] * graw[2];
+                            }
+                        }
+                        if (DEG > 0) {
+                            float gdx, gdy, gdz;
+                            sh_basis_vjp<DEG>(d0, d1, d2, gY, gdx, gdy, gdz);
+                            const float dg = d0 * gdx + d1 * gdy + d2 * gdz;
+                            const float gdir0 = (gdx - d0 * dg) * idl, gdir1 = (gdy - d1 * dg) * idl,
+                                        gdir2 = (gdz - d2 * dg) * idl;
+                            gm[0] += gdir0; gm[1] += gdir1; gm[2] += gdir2;
+                            gC3[0] = -gdir0; gC3[1] = -gdir1; gC3[2] = -gdir2;
+                        }
+                    }
+                    // C = -R^T t: dL/dR[a][b] += -t_a gC_b, dL/dt_a += -sum_b R[a][b] gC_b
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa) {
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb) pg[3 * aa + bb] += -t[aa] * gC3[bb];
+                        pg[9 + aa] += -(R[3 * aa] * gC3[0] + R[3 * aa + 1] * gC3[1] + R[3 * aa + 2] * gC3[2]);
+                    }
+
+                    // conic (A,B,C) -> dilated covariance (a,b,c)
+                    const float ga = (-c * c * gA + b * c * gB - b * b * gC) * id2;
+                    const float gb = (2.f * b * c * gA - (a * c + b * b) * gB + 2.f * a * b * gC) * id2;
+                    const float gc = (-b * b * gA + a * b * gB - a * a * gC) * id2;
+                    const float P00 = ga, P01 = 0.5f * gb, P11 = gc;   // symmetric full-matrix gradient
+                    // dL/dT = 2 P T Sigma
+                    float GT[6];
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) {
+                        GT[cc] = 2.f * (P00 * TS[cc] + P01 * TS[3 + cc]);
+                        GT[3 + cc] = 2.f * (P01 * TS[cc] + P11 * TS[3 + cc]);
+                    }
+                    if (GAUSS) {
+                        // dL/dSigma = T^T P T
+                        float PT[6];
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) {
+                            PT[cc] = P00 * T[cc] + P01 * T[3 + cc];
+                            PT[3 + cc] = P01 * T[cc] + P11 * T[3 + cc];
+                        }
+                        GS00 += T[0] * PT[0] + T[3] * PT[3];
+                        GS01 += T[0] * PT[1] + T[3] * PT[4];
+                        GS02 += T[0] * PT[2] + T[3] * PT[5];
+                        GS11 += T[1] * PT[1] + T[4] * PT[4];
+                        GS12 += T[1] * PT[2] + T[4] * PT[5];
+                        GS22 += T[2] * PT[2] + T[5] * PT[5];
+                    }
+                    // T = J R: dL/dJ = GT R^T, dL/dR += J^T GT
+                    const float GJ00 = GT[0] * R[0] + GT[1] * R[1] + GT[2] * R[2];
+                    const float GJ02 = GT[0] * R[6] + GT[1] * R[7] + GT[2] * R[8];
+                    const float GJ11 = GT[3] * R[3] + GT[4] * R[4] + GT[5] * R[5];
+                    const float GJ12 = GT[3] * R[6] + GT[4] * R[7] + GT[5] * R[8];
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) {
+                        pg[cc] += J00 * GT[cc];
+                        pg[3 + cc] += J11 * GT[3 + cc];
+                        pg[6 + cc] += J02 * GT[cc] + J12 * GT[3 + cc];
+                    }
+                    float gmc0 = 0.f, gmc1 = 0.f, gmc2 = 0.f;
+                    gmc2 += GJ00 * (-fx * iz2) + GJ02 * (fx * u * iz2) + GJ11 * (-fy * iz2) + GJ12 * (fy * w * iz2);
+                    const float gu = GJ02 * (-fx * iz), gw = GJ12 * (-fy * iz);
+                    if (u_in) { gmc0 += gu * iz; gmc2 += -gu * x * iz2; }
+                    if (w_in) { gmc1 += gw * iz; gmc2 += -gw * y * iz2; }
+                    gmc0 += gx * fx * iz;
+                    gmc2 += -gx * fx * x * iz2;
+                    gmc1 += gy * fy * iz;
+                    gmc2 += -gy * fy * y * iz2;
+                    // m = R mu + t
+                    gm[0] += R[0] * gmc0 + R[3] * gmc1 + R[6] * gmc2;
+                    gm[1] += R[1] * gmc0 + R[4] * gmc1 + R[7] * gmc2;
+                    gm[2] += R[2] * gmc0 + R[5] * gmc1 + R[8] * gmc2;
+                    const float gmc[3] = {gmc0, gmc1, gmc2};
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa) {
+                        pg[3 * aa] += gmc[aa] * mx;
+                        pg[3 * aa + 1] += gmc[aa] * my;
+                        pg[3 * aa + 2] += gmc[aa] * mz;
+                        pg[9 + aa] += gmc[aa];
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                for (int cc = 0; cc < 12; ++cc) {
+                    float val = pg[cc];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                    pg[cc] = val;
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int cc = 0; cc < 12; ++cc) s_pose[wid][v][cc] += pg[cc];
+                }
+            }
+        }
+
+        if (valid && GAUSS) {
+            // Sigma = M M^T: dL/dM = 2 GS M (GS symmetric)
+            const float GSf[9] = {GS00, GS01, GS02, GS01, GS11, GS12, GS02, GS12, GS22};
+            float gs[3] = {0.f, 0.f, 0.f}, GRq[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    const float GM = 2.f * (GSf[3 * r] * M[cc] + GSf[3 * r + 1] * M[3 + cc] + GSf[3 * r + 2] * M[6 + cc]);
+                    gs[cc] += GM * Rq[3 * r + cc];
+                    GRq[3 * r + cc] = GM * sc[cc];
+                }
+            g_log_scales[3 * i] = gs[0] * sc[0];
+            g_log_scales[3 * i + 1] = gs[1] * sc[1];
+            g_log_scales[3 * i + 2] = gs[2] * sc[2];
+            // rotation of (w,x,y,z) -> quaternion gradient
+            const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+            const float gw = 2.f * (-z * GRq[1] + y * GRq[2] + z * GRq[3] - x * GRq[5] - y * GRq[6] + x * GRq[7]);
+            const float gxq = 2.f * (y * GRq[1] + z * GRq[2] + y * GRq[3] - 2.f * x * GRq[4] - w * GRq[5] +
+                                     z * GRq[6] + w * GRq[7] - 2.f * x * GRq[8]);
+            const float gyq = 2.f * (-2.f * y * GRq[0] + x * GRq[1] + w * GRq[2] + x * GRq[3] + z * GRq[5] -
+                                     w * GRq[6] + z * GRq[7] - 2.f * y * GRq[8]);
+            const float gzq = 2.f * (-2.f * z * GRq[0] - w * GRq[1] + x * GRq[2] + w * GRq[3] - 2.f * z * GRq[4] +
+                                     y * GRq[5] + x * GRq[6] + y * GRq[7]);
+            const float dq = gw * w + gxq * x + gyq * y + gzq * z;
+            const float iq = 1.f / qlen;
+            reinterpret_cast<float4 *>(g_quats)[i] =
+                make_float4((gw - w * dq) * iq, (gxq - x * dq) * iq, (gyq - y * dq) * iq, (gzq - z * dq) * iq);
+            g_means[3 * i] = gm[0];
+            g_means[3 * i + 1] = gm[1];
+            g_means[3 * i + 2] = gm[2];
+            g_logits[i] = go * opac * (1.f - opac);
+#pragma unroll
+            for (int k = 0; k < 3 * K; ++k) g_sh[(long long)3 * K * i + k] = gf[k];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < L.n_views * 12; e += PB_THREADS) {
+        const int v = e / 12, cc = e % 12;
+        float acc = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < PB_WARPS; ++ww) acc += s_pose[ww][v][cc];
+        pose_partials[((long long)v * gridDim.x + blockIdx.x) * 12 + cc] = acc;
+    }
+}
+
+int pose_blocks(long long n) {
+    long long b = (n + PB_THREADS - 1) / PB_THREADS;
+    const long long cap = 4LL * num_sms();
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const float *viewmats, const float *intr,
+                       const float *proj, const float *grad2d, const gs_grads *out, int want_gauss, int nblk,
+                       cudaStream_t st) {
+    const float4 *p = reinterpret_cast<const float4 *>(proj);
+    const float4 *g2 = reinterpret_cast<const float4 *>(grad2d);
+#define GS_PB(D, G)                                                                                              \
+    k_project_bwd<D, G><<<nblk, PB_THREADS, 0, st>>>(L, g->means, g->log_scales, g->quats, g->opacity_logits,  \
+                                                     g->sh, viewmats, intr, p, g2, out->means, out->log_scales, \
+                                                     out->quats, out->opacity_logits, out->sh, out->pose_partials)
+    if (want_gauss) {
+        switch (deg) {
+        case 0: GS_PB(0, true); break;
+        case 1: GS_PB(1, true); break;
+        case 2: GS_PB(2, true); break;
+        case 3: GS_PB(3, true); break;
+        default: return GS_ERR_UNSUPPORTED;
+        }
+    } else {
+        switch (deg) {
+        case 0: GS_PB(0, false); break;
+        case 1: GS_PB(1, false); break;
+        case 2: GS_PB(2, false); break;
+        case 3: GS_PB(3, false); break;
+        default: return GS_ERR_UNSUPPORTED;
+        }
+    }
+#undef GS_PB
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// pose partials -> dL/d(R,t) and the left-twist gradient, fixed order
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_pose_reduce(const float *__restrict__ partials, int nblk,
+                                                     const float *__restrict__ viewmats, float *__restrict__ out_rt,
+                                                     float *__restrict__ out_twist) {
+    __shared__ float s[12][256];
+    const int v = blockIdx.x;
+    float acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = 0.f;
+    for (int b = threadIdx.x; b < nblk; b += 256)
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] += partials[((long long)v * nblk + b) * 12 + c];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) s[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+#pragma unroll
+            for (int c = 0; c < 12; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        float g[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            g[c] = s[c][0];
+            out_rt[12 * v + c] = g[c];
+        }
+        if (out_twist) {
+            const float *R = viewmats + 12 * v, *t = viewmats + 12 * v + 9;
+            // M = dL/dR R^T + dL/dt t^T
+            float Mm[9];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+                    Mm[3 * a + b] = g[3 * a] * R[3 * b] + g[3 * a + 1] * R[3 * b + 1] + g[3 * a + 2] * R[3 * b + 2] +
+                                    g[9 + a] * t[b];
+            out_twist[6 * v + 0] = g[9];
+            out_twist[6 * v + 1] = g[10];
+            out_twist[6 * v + 2] = g[11];
+            out_twist[6 * v + 3] = Mm[7] - Mm[5];
+            out_twist[6 * v + 4] = Mm[2] - Mm[6];
+            out_twist[6 * v + 5] = Mm[3] - Mm[1];
+        }
+    }
+}
+
+int launch_pose_reduce(int n_views, const float *partials, int nblk, const float *viewmats, float *out_rt,
+                       float *out_twist, cudaStream_t st) {
+    k_pose_reduce<<<n_views, 256, 0, st>>>(partials, nblk, viewmats, out_rt, out_twist);
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// mean L1 loss and its gradient
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_l1(const float4 *__restrict__ img, const float4 *__restrict__ tgt,
+                                            long long n4, const float *__restrict__ img1,
+                                            const float *__restrict__ tgt1, long long n, float inv_n,
+                                            float4 *__restrict__ grad4, float *__restrict__ grad1,
+                                            float *__restrict__ loss) {
+    __shared__ float s_w[8];
+    float acc = 0.f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 a = img[i], b = tgt[i];
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+        acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+        grad4[i] = make_float4(d0 > 0.f ? inv_n : (d0 < 0.f ? -inv_n : 0.f), d1 > 0.f ? inv_n : (d1 < 0.f ? -inv_n : 0.f),
+                               d2 > 0.f ? inv_n : (d2 < 0.f ? -inv_n : 0.f), d3 > 0.f ? inv_n : (d3 < 0.f ? -inv_n : 0.f));
+    }
+    for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float d = img1[i] - tgt1[i];
+        acc += fabsf(d);
+        grad1[i] = d > 0.f ? inv_n : (d < 0.f ? -inv_n : 0.f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w) t += s_w[w];
+        atomicAdd(loss, t * inv_n);
+    }
+}
+
+int launch_l1(const float *image, const float *target, long long n, float *loss, float *grad, cudaStream_t st) {
+    if (cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess) return GS_ERR_CUDA;
+    if (n == 0) return GS_OK;
+    const bool al = ((uintptr_t)image % 16 == 0) && ((uintptr_t)target % 16 == 0) && ((uintptr_t)grad % 16 == 0);
+    const long long n4 = al ? n / 4 : 0;
+    long long blocks = (n + 1023) / 1024;
+    if (blocks > 8LL * num_sms()) blocks = 8LL * num_sms();
+    k_l1<<<(int)blocks, 256, 0, st>>>(reinterpret_cast<const float4 *>(image), reinterpret_cast<const float4 *>(target),
+                                      n4, image, target, n, 1.f / (float)n, reinterpret_cast<float4 *>(grad), grad,
+                                      loss);
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+}  // namespace gsk

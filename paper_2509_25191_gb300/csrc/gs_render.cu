@@ -1,0 +1,349 @@
+// Front-to-back alpha compositing (forward) and its recompute-T backward.
+//
+// Section 3.1: a pixel's colour is the alpha blend of the depth-sorted
+// Gaussians covering it, c_p = sum_i c_i alpha_i T_i + T_final bg with
+// T_i = prod_{j<i} (1 - alpha_j). Per Gaussian and pixel:
+//   alpha = min(alpha_max, o exp(-1/2 d^T conic d)), skipped if the exponent
+//   is > 0 or alpha < alpha_min, and (pixel gate) if |dx| or |dy| > radius;
+//   the Gaussian that would bring T (1 - alpha) below t_min is not composited
+//   and the pixel stops.
+//
+// Both kernels are persistent: blocks pull tiles from an atomic queue over
+// tile_order (largest tiles first), one thread per pixel, and stage each
+// tile's instances through shared memory in batches of one per thread.
+//
+// The backward does not store or replay transmittance: it walks the same list
+// front to back with bit-identical arithmetic (explicit-rounding intrinsics,
+// so forward and backward take the same decisions), and gets the colour of
+// everything behind Gaussian i from the forward image,
+//   S_i = sum_{j>i} c_j alpha_j T_j + T_final bg = image - sum_{j<=i} c_j alpha_j T_j,
+// so that dL/dalpha_i = T_i (c_i . g) - (S_i . g) / (1 - alpha_i).
+// Per-Gaussian gradients (mean2D, conic, opacity, colour) are summed over a
+// warp with shuffles, over the block in shared memory, and added to the
+// per-slot grad2d record with one vector atomic per float4.
+#include "gs_common.cuh"
+
+namespace gsk {
+
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float LN2 = 0.69314718055994531f;
+
+__device__ __forceinline__ void stage(const float4 *__restrict__ proj, unsigned int slot, float ox, float oy,
+                                      float4 &xy, float4 &con, float4 &rgb) {
+    const float4 r0 = proj[4ull * slot];
+    const float4 r1 = proj[4ull * slot + 1];
+    const float4 r2 = proj[4ull * slot + 2];
+    xy = make_float4(__fadd_rn(__fsub_rn(r0.x, ox), r0.z), __fadd_rn(__fsub_rn(r0.y, oy), r0.w), r2.w, r1.w);
+    con = make_float4(__fmul_rn(r1.x, -0.5f * LOG2E), __fmul_rn(r1.y, -LOG2E), __fmul_rn(r1.z, -0.5f * LOG2E),
+                      __uint_as_float(slot));
+    rgb = make_float4(r2.x, r2.y, r2.z, 0.f);
+}
+
+// alpha of a staged Gaussian at pixel centre (pcx, pcy), block-relative.
+// Returns false if the Gaussian is skipped at this pixel.
+__device__ __forceinline__ bool eval_alpha(const float4 &xy, const float4 &con, float pcx, float pcy, int gate,
+                                           float alpha_min, float alpha_max, float &alpha, float &G, float &dx,
+                                           float &dy, bool &clamped) {
+    dx = __fsub_rn(pcx, xy.x);
+    dy = __fsub_rn(pcy, xy.y);
+    if (gate && (fabsf(dx) > xy.z || fabsf(dy) > xy.z)) return false;
+    const float p2 = __fmaf_rn(con.x, __fmul_rn(dx, dx),
+                               __fmaf_rn(con.z, __fmul_rn(dy, dy), __fmul_rn(con.y, __fmul_rn(dx, dy))));
+    if (p2 > 0.f) return false;
+    G = ex2_approx(p2);
+    const float oG = __fmul_rn(xy.w, G);
+    clamped = oG > alpha_max;
+    alpha = clamped ? alpha_max : oG;
+    return alpha >= alpha_min;
+}
+
+// Positions are staged relative to the origin of the enclosing 32x32-pixel
+// block (every supported tile nests in one), so a pixel's arithmetic is the
+// same for every tile shape and the image is bit-identical across shapes.
+struct TileInfo {
+    int view, px, py;
+    float ox, oy;     // block origin in pixels
+    float pcx, pcy;   // this thread's pixel centre relative to the block origin
+    bool inside;
+};
+
+template <int TW, int TH>
+__device__ __forceinline__ TileInfo tile_info(const Launch &L, int tile) {
+    TileInfo ti;
+    ti.view = view_of_tile(L, tile);
+    const ViewDesc &vd = L.v[ti.view];
+    const int lt = tile - vd.tile_base;
+    const int tx = lt % vd.Gx, ty = lt / vd.Gx;
+    ti.px = tx * TW + (int)(threadIdx.x % TW);
+    ti.py = ty * TH + (int)(threadIdx.x / TW);
+    const int bx = (tx * TW) & ~31, by = (ty * TH) & ~31;
+    ti.ox = (float)bx;
+    ti.oy = (float)by;
+    ti.pcx = (float)(ti.px - bx) + 0.5f;
+    ti.pcy = (float)(ti.py - by) + 0.5f;
+    ti.inside = ti.px < vd.W && ti.py < vd.H;
+    return ti;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// add a thread's pair counts to the 64-bit counters at c[0], c[1] (one atomic per warp)
+__device__ __forceinline__ void count_pairs(int *counters, int at, unsigned int n_eval, unsigned int n_comp) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
+        n_comp += __shfl_xor_sync(0xffffffffu, n_comp, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        unsigned long long *c = reinterpret_cast<unsigned long long *>(counters + at);
+        atomicAdd(c, (unsigned long long)n_eval);
+        atomicAdd(c + 1, (unsigned long long)n_comp);
+    }
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) k_render_fwd(const Launch L, const float4 *__restrict__ proj,
+                                                        const int2 *__restrict__ ranges,
+                                                        const unsigned int *__restrict__ ids,
+                                                        const int *__restrict__ order, int *__restrict__ counters,
+                                                        float *__restrict__ image) {
+    constexpr int BS = TW * TH;
+    __shared__ float4 s_xy[BS], s_con[BS], s_rgb[BS];
+    __shared__ int s_item;
+    const bool abort = counters[CNT_ABORT] != 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counters + CNT_Q_FWD, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= L.n_tiles) break;
+        const int tile = order[item];
+        const TileInfo ti = tile_info<TW, TH>(L, tile);
+        const int2 r = abort ? make_int2(0, 0) : ranges[tile];
+        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        bool done = !ti.inside;
+        unsigned int n_eval = 0, n_comp = 0;
+        for (int b0 = r.x; b0 < r.y; b0 += BS) {
+            if (__syncthreads_count(done) == BS) break;
+            const int j = b0 + threadIdx.x;
+            if (j < r.y) stage(proj, ids[j], ti.ox, ti.oy, s_xy[threadIdx.x], s_con[threadIdx.x], s_rgb[threadIdx.x]);
+            __syncthreads();
+            const int nb = min(BS, r.y - b0);
+            for (int k = 0; k < nb && !done; ++k) {
+                float alpha, G = 0.f, dx, dy;
+                bool clamped;
+                const bool use = eval_alpha(s_xy[k], s_con[k], ti.pcx, ti.pcy, L.pixel_gate, L.alpha_min,
+                                            L.alpha_max, alpha, G, dx, dy, clamped);
+                n_eval += G > 0.f || use;
+                if (!use) continue;
+                const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                if (Tn < L.t_min) { done = true; break; }
+                ++n_comp;
+                const float w = __fmul_rn(alpha, T);
+                const float4 c = s_rgb[k];
+                C0 = __fmaf_rn(c.x, w, C0);
+                C1 = __fmaf_rn(c.y, w, C1);
+                C2 = __fmaf_rn(c.z, w, C2);
+                T = Tn;
+            }
+        }
+        count_pairs(counters, 8, n_eval, n_comp);
+        if (ti.inside) {
+            const ViewDesc &vd = L.v[ti.view];
+            const long long hw = (long long)vd.W * vd.H;
+            float *img = image + vd.pix_base + (long long)ti.py * vd.W + ti.px;
+            if (abort) {
+                img[0] = 0.f; img[hw] = 0.f; img[2 * hw] = 0.f;
+            } else {
+                img[0] = __fmaf_rn(T, L.bg[0], C0);
+                img[hw] = __fmaf_rn(T, L.bg[1], C1);
+                img[2 * hw] = __fmaf_rn(T, L.bg[2], C2);
+            }
+        }
+    }
+}
+
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) k_render_bwd(const Launch L, const float4 *__restrict__ proj,
+                                                        const int2 *__restrict__ ranges,
+                                                        const unsigned int *__restrict__ ids,
+                                                        const int *__restrict__ order, int *__restrict__ counters,
+                                                        const float *__restrict__ image,
+                                                        const float *__restrict__ dL_dimage,
+                                                        float4 *__restrict__ grad2d) {
+    constexpr int BS = TW * TH;
+    __shared__ float4 s_xy[BS], s_con[BS], s_rgb[BS];
+    __shared__ float s_g[9][BS];
+    __shared__ int s_item;
+    if (counters[CNT_ABORT]) return;
+    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < BS; k += BS)
+        for (int c = 0; c < 9; ++c) s_g[c][k] = 0.f;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counters + CNT_Q_BWD, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= L.n_tiles) break;
+        const int tile = order[item];
+        const TileInfo ti = tile_info<TW, TH>(L, tile);
+        const int2 r = ranges[tile];
+        float img0 = 0.f, img1 = 0.f, img2 = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        if (ti.inside) {
+            const ViewDesc &vd = L.v[ti.view];
+            const long long hw = (long long)vd.W * vd.H;
+            const long long o = vd.pix_base + (long long)ti.py * vd.W + ti.px;
+            img0 = image[o]; img1 = image[o + hw]; img2 = image[o + 2 * hw];
+            g0 = dL_dimage[o]; g1 = dL_dimage[o + hw]; g2 = dL_dimage[o + 2 * hw];
+        }
+        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        bool done = !ti.inside || (g0 == 0.f && g1 == 0.f && g2 == 0.f);
+        unsigned int n_eval = 0, n_comp = 0;
+        for (int b0 = r.x; b0 < r.y; b0 += BS) {
+            if (__syncthreads_count(done) == BS) break;
+            const int j = b0 + threadIdx.x;
+            if (j < r.y) stage(proj, ids[j], ti.ox, ti.oy, s_xy[threadIdx.x], s_con[threadIdx.x], s_rgb[threadIdx.x]);
+            __syncthreads();
+            const int nb = min(BS, r.y - b0);
+            for (int k = 0; k < nb; ++k) {
+                // gradient of this pixel w.r.t. (x, y, A, B, C, o, r, g, b) of Gaussian k
+                float gv[9];
+#pragma unroll
+                for (int c = 0; c < 9; ++c) gv[c] = 0.f;
+                bool hit = false;
+                if (!done) {
+                    float alpha, G, dx, dy;
+                    bool clamped;
+                    const float4 xy = s_xy[k], con = s_con[k];
+                    G = 0.f;
+                    const bool use = eval_alpha(xy, con, ti.pcx, ti.pcy, L.pixel_gate, L.alpha_min, L.alpha_max,
+                                                alpha, G, dx, dy, clamped);
+                    n_eval += G > 0.f || use;
+                    if (use) {
+                        const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                        if (Tn < L.t_min) {
+                            done = true;
+                        } else {
+                            hit = true;
+                            ++n_comp;
+                            const float w = __fmul_rn(alpha, T);
+                            const float4 c = s_rgb[k];
+                            C0 = __fmaf_rn(c.x, w, C0);
+                            C1 = __fmaf_rn(c.y, w, C1);
+                            C2 = __fmaf_rn(c.z, w, C2);
+                            gv[6] = w * g0;
+                            gv[7] = w * g1;
+                            gv[8] = w * g2;
+                            const float S0 = img0 - C0, S1 = img1 - C1, S2 = img2 - C2;
+                            const float dL_dalpha =
+                                T * (c.x * g0 + c.y * g1 + c.z * g2) - (S0 * g0 + S1 * g1 + S2 * g2) / (1.f - alpha);
+                            if (!clamped) {
+                                // alpha = o G, G = exp(power), power = -1/2 (A dx^2 + 2B dx dy + C dy^2),
+                                // dx = pixel - mean: d power / d mean = (A dx + B dy, B dx + C dy)
+                                gv[5] = dL_dalpha * G;
+                                const float dp = dL_dalpha * alpha;
+                                const float A = con.x * (-2.f * LN2), B = con.y * (-LN2), Cc = con.z * (-2.f * LN2);
+                                gv[0] = dp * (A * dx + B * dy);
+                                gv[1] = dp * (B * dx + Cc * dy);
+                                gv[2] = -0.5f * dp * dx * dx;
+                                gv[3] = -dp * dx * dy;
+                                gv[4] = -0.5f * dp * dy * dy;
+                            }
+                            T = Tn;
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, hit)) {
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) gv[c] = warp_sum(gv[c]);
+                    if (lane == 0) {
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) atomicAdd(&s_g[c][k], gv[c]);
+                    }
+                }
+            }
+            __syncthreads();
+            // flush this batch's per-Gaussian sums
+            const int k = threadIdx.x;
+            if (k < nb) {
+                const float a0 = s_g[0][k], a1 = s_g[1][k], a2 = s_g[2][k], a3 = s_g[3][k], a4 = s_g[4][k];
+                const float a5 = s_g[5][k], a6 = s_g[6][k], a7 = s_g[7][k], a8 = s_g[8][k];
+                if (a0 != 0.f || a1 != 0.f || a2 != 0.f || a3 != 0.f || a4 != 0.f || a5 != 0.f || a6 != 0.f ||
+                    a7 != 0.f || a8 != 0.f) {
+                    const unsigned int slot = __float_as_uint(s_con[k].w);
+                    float4 *dst = grad2d + 3ull * slot;
+                    atomicAdd(dst, make_float4(a0, a1, a2, a3));
+                    atomicAdd(dst + 1, make_float4(a4, a5, a6, a7));
+                    atomicAdd(dst + 2, make_float4(a8, 0.f, 0.f, 0.f));
+                }
+#pragma unroll
+                for (int c = 0; c < 9; ++c) s_g[c][k] = 0.f;
+            }
+        }
+    }
+}
+
+template <int TW, int TH>
+static int launch_fwd_t(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st) {
+    static int blocks_per_sm = 0;
+    if (!blocks_per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_fwd<TW, TH>, TW * TH, 0) !=
+                cudaSuccess || blocks_per_sm < 1)
+            blocks_per_sm = 1;
+    }
+    const int grid = min(num_sms() * blocks_per_sm, max(1, L.n_tiles));
+    // every call walks all tiles again: reset this kernel's work-queue head
+    if (cudaMemsetAsync(b->counters + CNT_Q_FWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
+    k_render_fwd<TW, TH><<<grid, TW * TH, 0, st>>>(L, reinterpret_cast<const float4 *>(proj),
+                                                   reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
+                                                   b->tile_order, b->counters, image);
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+template <int TW, int TH>
+static int launch_bwd_t(const Launch &L, const float *proj, const gs_bins *b, const float *image,
+                        const float *dL_dimage, float *grad2d, cudaStream_t st) {
+    static int blocks_per_sm = 0;
+    if (!blocks_per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_bwd<TW, TH>, TW * TH, 0) !=
+                cudaSuccess || blocks_per_sm < 1)
+            blocks_per_sm = 1;
+    }
+    const int grid = min(num_sms() * blocks_per_sm, max(1, L.n_tiles));
+    if (cudaMemsetAsync(b->counters + CNT_Q_BWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
+    k_render_bwd<TW, TH><<<grid, TW * TH, 0, st>>>(L, reinterpret_cast<const float4 *>(proj),
+                                                   reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
+                                                   b->tile_order, b->counters, image, dL_dimage,
+                                                   reinterpret_cast<float4 *>(grad2d));
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+int launch_render_fwd(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st) {
+#define GS_CALL_FWD(TW, TH) launch_fwd_t<TW, TH>(L, proj, b, image, st)
+    if (L.tw == 16 && L.th == 16) return GS_CALL_FWD(16, 16);
+    if (L.tw == 8 && L.th == 8) return GS_CALL_FWD(8, 8);
+    if (L.tw == 16 && L.th == 8) return GS_CALL_FWD(16, 8);
+    if (L.tw == 32 && L.th == 8) return GS_CALL_FWD(32, 8);
+    if (L.tw == 32 && L.th == 16) return GS_CALL_FWD(32, 16);
+    return GS_ERR_UNSUPPORTED;
+#undef GS_CALL_FWD
+}
+
+int launch_render_bwd(const Launch &L, const float *proj, const gs_bins *b, const float *image,
+                      const float *dL_dimage, float *grad2d, cudaStream_t st) {
+#define GS_CALL_BWD(TW, TH) launch_bwd_t<TW, TH>(L, proj, b, image, dL_dimage, grad2d, st)
+    if (L.tw == 16 && L.th == 16) return GS_CALL_BWD(16, 16);
+    if (L.tw == 8 && L.th == 8) return GS_CALL_BWD(8, 8);
+    if (L.tw == 16 && L.th == 8) return GS_CALL_BWD(16, 8);
+    if (L.tw == 32 && L.th == 8) return GS_CALL_BWD(32, 8);
+    if (L.tw == 32 && L.th == 16) return GS_CALL_BWD(32, 16);
+    return GS_ERR_UNSUPPORTED;
+#undef GS_CALL_BWD
+}
+
+}  // namespace gsk

@@ -1,0 +1,386 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2509_25191_gb300 import _lib, synth
+from paper_2509_25191_gb300.autograd import Rasterizer
+from tests.gpu_util import (check_grad, gpu_forward, image_errors, oracle_forward, split, upstream)
+
+pytestmark = pytest.mark.gpu
+
+
+def _eye_view(n, W, H, f, cx=None, cy=None):
+    return synth._views(np.concatenate([np.eye(3).reshape(-1), np.zeros(3)]), f, W, H, 0, n) if cx is None else \
+        synth.Views(np.concatenate([np.eye(3).reshape(-1), np.zeros(3)]).reshape(1, 12).astype(np.float32),
+                    np.array([[f, f, cx, cy]], np.float32), np.array([W], np.int32), np.array([H], np.int32),
+                    np.array([0]), np.array([n]))
+
+
+def _reduced_c2(n=30000, W=333, H=221, seed=0):
+    """The 1M-Gaussian clustered SH3 workload scaled down: same distributions,
+    fewer Gaussians, lower resolution (ragged tiles on both axes)."""
+    sc = synth.cluster_scene(seed, n)
+    vw = synth._views(synth.look_at((0.0, 0.0, -6.0)), 1000.0 * W / 1237.0, W, H, 0, n)
+    return sc, vw
+
+
+CASES = {
+    "small_2k": lambda: synth.single_view_small(),
+    "clustered_sh3": lambda: _reduced_c2(),
+    "orbit_4views": lambda: synth.orbit_views(0, 20000, 4, 200, 112, 1000.0 * 200 / 979.0),
+    "uneven_3scenes": lambda: synth.uneven_scenes(seeds=(1, 2, 3), sizes=(3000, 6000, 9000), views_per_scene=2,
+                                                  resolutions=((96, 64), (150, 90), (77, 131)), focal=150.0),
+}
+
+
+# ---------------------------------------------------------------------------
+# library / ABI
+# ---------------------------------------------------------------------------
+
+def test_invalid_arguments_rejected_on_host():
+    sc, vw = synth.single_view_small(n=50)
+    g = _lib.Gaussians.from_scene(sc)
+    views = _lib.Views.from_synth(vw)
+    proj = torch.empty(50, 16, device="cuda")
+    with pytest.raises(_lib.GsError) as e:
+        _lib.gs_project(g, views, _lib.config(tile=(12, 16)), proj)
+    assert e.value.code == _lib.GS_ERR_UNSUPPORTED
+    bad = _lib.Views(views.viewmats, views.intrinsics, [128], [128], [0], [51])   # range past n
+    with pytest.raises(_lib.GsError) as e:
+        _lib.gs_project(g, bad, _lib.config(), proj)
+    assert e.value.code == _lib.GS_ERR_ARG
+    buf = torch.empty(50 * 16 + 4, device="cuda")
+    with pytest.raises(_lib.GsError) as e:
+        _lib.gs_project(g, views, _lib.config(), buf[1:1 + 50 * 16])   # 4-byte offset: not 16-byte aligned
+    assert e.value.code == _lib.GS_ERR_ARG
+    sc4 = synth.uniform_box_scene(0, 50, sh_degree=3)
+    sc4.sh = np.zeros((50, 25, 3), np.float32)                           # degree 4 is not supported
+    g4 = _lib.Gaussians.__new__(_lib.Gaussians)
+    g4.__dict__.update(g.__dict__)
+    g4.sh_degree = 4
+    with pytest.raises(_lib.GsError) as e:
+        _lib.gs_project(g4, views, _lib.config(), proj)
+    assert e.value.code == _lib.GS_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+
+
+def test_capacity_overflow_reports_needed_count():
+    sc, vw = synth.single_view_small()
+    g = _lib.Gaussians.from_scene(sc)
+    views = _lib.Views.from_synth(vw)
+    rast = Rasterizer()
+    proj = rast.project(g, views)
+    cfg = rast.cfg
+    small = _lib.Bins(views.num_tiles(cfg), 10)
+    status = _lib.new_status()
+    _lib.gs_bin_sort(views, cfg, proj, small, status)
+    img = torch.empty(views.num_image_floats(), device="cuda")
+    _lib.gs_render_fwd(views, cfg, proj, small, img, status)
+    torch.cuda.synchronize()
+    st = status.cpu().numpy()
+    need = int(small.counters[0].item())
+    assert st[0] == _lib.GS_ERR_CAPACITY and st[1] == need and need > 10
+    assert float(img.abs().max()) == 0.0
+    # a big enough capacity works afterwards in the same context
+    image, _ = rast.forward(g, views)
+    torch.cuda.synchronize()
+    rast.check_status()
+    assert rast.last_instances == need
+
+
+# ---------------------------------------------------------------------------
+# projection
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["small_2k", "clustered_sh3", "orbit_4views"])
+def test_projection_parity(case):
+    sc, vw = CASES[case]()
+    _, _, views, _, proj = gpu_forward(sc, vw)
+    P = proj.cpu().numpy()
+    for v in range(vw.n):
+        ref = O.project_view(sc, vw, v)
+        rec = P[views.slot_base(v): views.slot_base(v) + int(vw.gauss_count[v])]
+        rad = rec[:, 11]
+        both = (rad > 0) & (ref["radius"] > 0)
+        # validity agrees except where the radius itself is ambiguous
+        frac = ref["r_real"] - np.floor(ref["r_real"])
+        amb = (frac < 1e-4) | (frac > 1 - 1e-4)
+        disagree = ((rad > 0) != (ref["radius"] > 0)) & ~amb
+        assert disagree.sum() <= max(2, 1e-4 * len(rad)), disagree.sum()
+        x = rec[:, 0].astype(np.float64) + rec[:, 2]
+        y = rec[:, 1].astype(np.float64) + rec[:, 3]
+        assert np.abs(x - ref["xy"][:, 0])[both].max() < 2e-5 * max(1.0, np.abs(ref["xy"][both]).max())
+        assert np.abs(y - ref["xy"][:, 1])[both].max() < 2e-5 * max(1.0, np.abs(ref["xy"][both]).max())
+        con = rec[:, 4:7][both]
+        rc = ref["conic"][both]
+        scale = np.abs(rc).max(axis=1, keepdims=True)
+        assert (np.abs(con - rc) / scale).max() < 1e-4
+        assert np.abs(rec[:, 7][both] - ref["opac"][both]).max() < 1e-6
+        assert np.abs(rec[:, 8:11][both] - ref["rgb"][both]).max() < 1e-5
+        ok_r = both & ~amb
+        assert np.array_equal(rad[ok_r], ref["radius"][ok_r].astype(np.float32))
+        assert np.abs(rec[:, 12][both] / ref["depth"][both] - 1).max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# binning: bit-exact when fed the oracle's float32 records
+# ---------------------------------------------------------------------------
+
+def _records_from_oracle(sc, vw):
+    recs = []
+    for v in range(vw.n):
+        ref = O.project_view(sc, vw, v)
+        r = np.zeros((int(vw.gauss_count[v]), 16), np.float32)
+        r[:, 0] = ref["xy"][:, 0].astype(np.float32)
+        r[:, 1] = ref["xy"][:, 1].astype(np.float32)
+        r[:, 11] = ref["radius"].astype(np.float32)
+        r[:, 12] = ref["depth"].astype(np.float32)
+        recs.append((ref, r))
+    return recs
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+@pytest.mark.parametrize("case", ["small_2k", "orbit_4views", "uneven_3scenes"])
+def test_binning_bit_exact(case, tile):
+    sc, vw = CASES[case]()
+    recs = _records_from_oracle(sc, vw)
+    proj = torch.as_tensor(np.concatenate([r for _, r in recs])).cuda()
+    views = _lib.Views.from_synth(vw)
+    cfg = _lib.config(tile=tile)
+    n_inst = 0
+    refs = []
+    for v, (ref, r) in enumerate(recs):
+        W, H = int(vw.width[v]), int(vw.height[v])
+        refs.append(O.bin_view(r[:, 0], r[:, 1], ref["radius"], r[:, 12], W, H, *tile))
+        n_inst += len(refs[-1][2])
+    bins = _lib.Bins(views.num_tiles(cfg), n_inst)
+    status = _lib.new_status()
+    _lib.gs_bin_sort(views, cfg, proj, bins, status)
+    torch.cuda.synchronize()
+    assert status[0].item() == 0 and bins.counters[0].item() == n_inst
+    ranges = bins.tile_ranges.cpu().numpy().reshape(-1, 2)
+    keys = bins.keys.cpu().numpy().view(np.uint64)
+    ids = bins.ids.cpu().numpy().view(np.uint32)
+    inst_base = 0
+    for v, (rr, kk, ii) in enumerate(refs):
+        tb = views.tile_base(cfg, v)
+        sb = views.slot_base(v)
+        G = rr.shape[0]
+        got = ranges[tb:tb + G].astype(np.int64) - inst_base
+        assert np.array_equal(got, rr)
+        sl = slice(inst_base, inst_base + len(ii))
+        assert np.array_equal(ids[sl].astype(np.int64) - sb, ii.astype(np.int64))
+        exp_keys = (kk & np.uint64(0xffffffff00000000)) | (kk & np.uint64(0xffffffff)) + np.uint64(sb)
+        assert np.array_equal(keys[sl], exp_keys)
+        inst_base += len(ii)
+
+
+def test_binning_large_tiles_bit_exact():
+    """Tiles of > 2047 and > 16384 instances take the large-tile sort and
+    the merge path; the result must still equal the oracle's."""
+    rng = np.random.default_rng(11)
+    n, W, H = 60000, 64, 48
+    r = np.zeros((n, 16), np.float32)
+    r[:, 0] = rng.uniform(0, 64, n)
+    r[:, 1] = rng.uniform(0, 48, n)
+    r[:, 11] = rng.integers(1, 3, n)
+    r[:, 12] = rng.uniform(1.0, 9.0, n).astype(np.float32)
+    r[:40000, 0] = rng.uniform(17, 30, 40000)   # one very crowded tile column
+    r[:40000, 1] = rng.uniform(17, 30, 40000)
+    vw = synth.Views(np.zeros((1, 12), np.float32), np.ones((1, 4), np.float32), np.array([W], np.int32),
+                     np.array([H], np.int32), np.array([0]), np.array([n]))
+    views = _lib.Views.from_synth(vw)
+    cfg = _lib.config(tile=(16, 16))
+    rr, kk, ii = O.bin_view(r[:, 0], r[:, 1], r[:, 11].astype(np.int32), r[:, 12], W, H, 16, 16)
+    assert (rr[:, 1] - rr[:, 0]).max() > 16384
+    bins = _lib.Bins(views.num_tiles(cfg), len(ii))
+    _lib.gs_bin_sort(views, cfg, torch.as_tensor(r).cuda(), bins, _lib.new_status())
+    torch.cuda.synchronize()
+    assert np.array_equal(bins.tile_ranges.cpu().numpy().reshape(-1, 2), rr)
+    assert np.array_equal(bins.keys.cpu().numpy().view(np.uint64), kk)
+    assert np.array_equal(bins.ids.cpu().numpy().view(np.uint32).astype(np.int64), ii)
+
+
+# ---------------------------------------------------------------------------
+# rendering
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_render_parity(case):
+    sc, vw = CASES[case]()
+    bg = (0.1, 0.2, 0.3)
+    _, _, _, image, _ = gpu_forward(sc, vw, bg=bg)
+    ref = oracle_forward(sc, vw, bg=bg)
+    err, flagged = image_errors(split(image, vw), ref)
+    assert err <= 1e-4, (err, flagged)
+    assert flagged <= 0.01 * vw.pixels
+
+
+def test_render_edge_cases():
+    # nothing visible: every Gaussian behind the camera -> background only
+    sc = synth.uniform_box_scene(0, 100, lo=(-1, -1, -3), hi=(1, 1, -1))
+    vw = _eye_view(100, 37, 23, 40.0)
+    _, _, _, image, _ = gpu_forward(sc, vw, bg=(0.25, 0.5, 0.75))
+    img = split(image, vw)[0]
+    assert np.array_equal(img, np.broadcast_to(np.array([0.25, 0.5, 0.75], np.float32)[:, None, None], img.shape))
+    # a 1x1 image and a non-finite Gaussian
+    sc = synth.uniform_box_scene(1, 30, lo=(-0.1, -0.1, 2), hi=(0.1, 0.1, 3))
+    sc.means[3, 1] = np.inf
+    vw = _eye_view(30, 1, 1, 20.0)
+    _, _, _, image, proj = gpu_forward(sc, vw)
+    ref = oracle_forward(sc, vw)
+    err, _ = image_errors(split(image, vw), ref)
+    assert err <= 1e-4
+    assert proj[3, 11].item() == 0.0
+
+
+def test_batched_views_bit_equal_single_views():
+    sc, vw = CASES["orbit_4views"]()
+    _, _, _, image, _ = gpu_forward(sc, vw)
+    imgs = split(image, vw)
+    for v in range(vw.n):
+        one = vw.select([v])
+        _, _, _, im1, _ = gpu_forward(sc, one)
+        assert np.array_equal(split(im1, one)[0], imgs[v])
+
+
+def test_permutation_invariance_bit_exact():
+    sc, vw = _reduced_c2(n=8000, W=160, H=100)
+    # keep Gaussians of distinct float32 camera depth (camera at z=-6, R=I)
+    cz = (sc.means[:, 2].astype(np.float64) + 6.0).astype(np.float32)
+    _, first = np.unique(cz, return_index=True)
+    sc = sc.subset(np.sort(first))
+    vw = synth._views(synth.look_at((0.0, 0.0, -6.0)), 1000.0 * 160 / 1237.0, 160, 100, 0, sc.n)
+    _, _, _, a, _ = gpu_forward(sc, vw)
+    perm = np.random.default_rng(3).permutation(sc.n)
+    _, _, _, b, _ = gpu_forward(sc.permuted(perm), vw)
+    assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+
+
+def test_tile_size_invariance_bit_exact():
+    sc, vw = _reduced_c2(n=8000, W=170, H=90)
+    imgs = [gpu_forward(sc, vw, tile=t)[3].cpu().numpy() for t in [(16, 16), (8, 8), (16, 8), (32, 8), (32, 16)]]
+    for im in imgs[1:]:
+        assert np.array_equal(imgs[0], im)
+
+
+# ---------------------------------------------------------------------------
+# backward
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_backward_parity(case):
+    sc, vw = CASES[case]()
+    bg = (0.3, 0.1, 0.2)
+    rast, g, views, image, proj = gpu_forward(sc, vw, bg=bg)
+    ref = oracle_forward(sc, vw, bg=bg)
+    ups = upstream(vw, ref)
+    up = torch.as_tensor(np.concatenate([u.reshape(-1) for u in ups])).cuda()
+    grads, dvm, dtw = rast.backward(g, views, proj, image, up)
+    torch.cuda.synchronize()
+    rg, dRt, tw, g2ds = O.backward(sc, vw, ref, [u.astype(np.float64) for u in ups], params=O.Params(bg=bg))
+    # per-slot 2D gradients first (most diagnostic)
+    G2 = grads.grad2d.cpu().numpy()
+    for v in range(vw.n):
+        sb = views.slot_base(v)
+        got = G2[sb: sb + int(vw.gauss_count[v])][:, :9]
+        check_grad(got, g2ds[v], f"grad2d view {v}")
+    for name in ["means", "log_scales", "quats", "opacity_logits", "sh"]:
+        check_grad(getattr(grads, name).cpu().numpy(), rg[name], name)
+    check_grad(dvm.cpu().numpy(), dRt, "dL/d(R,t)")
+    check_grad(dtw.cpu().numpy(), tw, "twist")
+
+
+def test_pose_only_backward_matches_full():
+    sc, vw = CASES["orbit_4views"]()
+    rast, g, views, image, proj = gpu_forward(sc, vw)
+    up = torch.randn(views.num_image_floats(), device="cuda")
+    _, dvm_full, _ = rast.backward(g, views, proj, image, up, want_gaussian_grads=True)
+    dvm_full = dvm_full.clone()
+    _, dvm_pose, _ = rast.backward(g, views, proj, image, up, want_gaussian_grads=False)
+    torch.cuda.synchronize()
+    check_grad(dvm_pose.cpu().numpy(), dvm_full.cpu().numpy(), "pose-only", rel_norm=1e-5, rel_elem=1e-5,
+               abs_frac=1e-6)
+
+
+def test_autograd_and_pose_residual_chain():
+    """images -> L = <w, images>; gradients of the 6D/translation pose
+    residuals through torch match the oracle's dL/d(R,t) chained in FP64."""
+    from paper_2509_25191_gb300 import pose
+    from paper_2509_25191_gb300.autograd import RasterizeViews
+    sc, vw = CASES["orbit_4views"]()
+    ref = oracle_forward(sc, vw)
+    ups = upstream(vw, ref, seed=5)
+    w = torch.as_tensor(np.concatenate([u.reshape(-1) for u in ups])).cuda()
+    base = torch.as_tensor(vw.viewmats).cuda()
+    dr = pose.identity_6d(vw.n, device="cuda").requires_grad_(True)
+    dt = torch.zeros(vw.n, 3, device="cuda", requires_grad=True)
+    g = _lib.Gaussians.from_scene(sc)
+    params = [t.clone().requires_grad_(True) for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.sh)]
+    vm = pose.apply_residual(base, dr, dt)
+    layout = (vw.width, vw.height, vw.gauss_begin, vw.gauss_count)
+    img = RasterizeViews.apply(*params, vm, torch.as_tensor(vw.intrinsics).cuda(), layout, Rasterizer())
+    (img * w).sum().backward()
+    # oracle chain: dL/dR' from the oracle, then the same residual map in FP64 on CPU
+    _, dRt, _, _ = O.backward(sc, vw, ref, [u.astype(np.float64) for u in ups])
+    dr64 = pose.identity_6d(vw.n, dtype=torch.float64).requires_grad_(True)
+    dt64 = torch.zeros(vw.n, 3, dtype=torch.float64, requires_grad=True)
+    vm64 = pose.apply_residual(torch.as_tensor(vw.viewmats, dtype=torch.float64), dr64, dt64)
+    (vm64 * torch.as_tensor(dRt)).sum().backward()
+    check_grad(dr.grad.cpu().numpy(), dr64.grad.numpy(), "d(6D residual)")
+    check_grad(dt.grad.cpu().numpy(), dt64.grad.numpy(), "d(translation residual)")
+    rg, _, _, _ = O.backward(sc, vw, ref, [u.astype(np.float64) for u in ups])
+    check_grad(params[0].grad.cpu().numpy(), rg["means"], "means via autograd")
+
+
+def test_l1_loss_kernel():
+    a = torch.rand(3 * 37 * 41 + 3, device="cuda")
+    b = torch.rand_like(a)
+    b[5] = a[5]
+    loss = torch.empty(1, device="cuda")
+    grad = torch.empty_like(a)
+    _lib.gs_l1_loss(a, b, loss, grad)
+    torch.cuda.synchronize()
+    d = (a - b).double().cpu().numpy()
+    assert abs(loss.item() - np.abs(d).mean()) < 1e-6
+    assert np.array_equal(grad.cpu().numpy(), (np.sign(d) / d.size).astype(np.float32))
+
+
+# ---------------------------------------------------------------------------
+# CUDA graph capture of a whole step
+# ---------------------------------------------------------------------------
+
+def test_graph_capture_replays_step():
+    sc, vw = CASES["orbit_4views"]()
+    g = _lib.Gaussians.from_scene(sc)
+    views = _lib.Views.from_synth(vw)
+    rast = Rasterizer()
+    image0, proj0 = rast.forward(g, views)
+    up = torch.randn(views.num_image_floats(), device="cuda")
+    grads0, dvm0, _ = rast.backward(g, views, proj0, image0, up)
+    ref_img, ref_gm, ref_dvm = image0.clone(), grads0.means.clone(), dvm0.clone()
+    torch.cuda.synchronize()
+    rast.reserve(views, int(rast.last_instances * 1.5) + 1024)
+    proj = torch.empty_like(proj0)
+    image = torch.empty_like(image0)
+    grads = rast.grads_buffers(g, views)
+    dvm = torch.empty(vw.n, 12, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            rast.project(g, views, proj)
+            bins = rast.bin_sort(views, proj)
+            rast.render(views, proj, bins, image)
+            _lib.gs_render_bwd(g, views, rast.cfg, proj, bins, image, up, grads, True, rast.status)
+            _lib.gs_pose_grad(views, grads.pose_partials, grads.n_blocks, dvm)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    rast.check_status()
+    assert torch.equal(image, ref_img)
+    check_grad(grads.means.cpu().numpy(), ref_gm.cpu().numpy(), "graph means", 1e-5, 1e-4, 1e-6)
+    check_grad(dvm.cpu().numpy(), ref_dvm.cpu().numpy(), "graph pose", 1e-5, 1e-4, 1e-6)
