@@ -60,7 +60,8 @@ typedef enum gs_status {
 /* Rasterizer settings. gs_config_default() fills the defaults in brackets. */
 typedef struct gs_config {
     int tile_w, tile_h;   /* tile in pixels [16,16]; supported: 16x16, 8x8, 16x8, 32x8, 32x16 */
-    int pixel_gate;       /* [1] evaluate a Gaussian at a pixel only if |dx|,|dy| <= radius */
+    int pixel_gate;       /* [1] evaluate a Gaussian at a pixel only if |dx|,|dy| <= radius
+                             (the only supported value: it makes images tile-size invariant) */
     float near_z;         /* [0.2] cull if camera-space z <= near_z */
     float dilation;       /* [0.3] added to the 2D covariance diagonal (pixels^2) */
     float alpha_min;      /* [1/255] skip contributions with alpha below this */
@@ -120,7 +121,9 @@ typedef struct gs_grads {
     float *quats;          /* [n,4] */
     float *opacity_logits; /* [n] */
     float *sh;             /* [n,K,3] */
-    float *grad2d;         /* [P,12] per slot: dL/d(x,y,A,B | C,o,r,g | b,-,-,-) */
+    float *grad2d;         /* [P,12] per slot: dL/d(x, y, a, b | c, o, r, g | b_col, -, -, -): mean,
+                              dilated 2D covariance (a, b, c; b the off-diagonal value), opacity,
+                              colour */
     float *pose_partials;  /* [V, gs_pose_blocks(n), 12] */
 } gs_grads;
 
@@ -146,18 +149,23 @@ int gs_pose_blocks(int64_t n);
 /* Project every Gaussian into every view that sees it (Section 3.1
  * primitive; EWA splatting). Per slot p, proj[16p..16p+15] =
  *   {x, y, x_lo, y_lo}  mean in pixels as an unevaluated float pair x+x_lo,
- *   {A, B, C, o}        conic (inverse dilated 2D covariance, B off-diagonal)
- *                       and opacity,
+ *   {a, b, c, o}        dilated 2D covariance Sigma' (b off-diagonal; its
+ *                       inverse is the conic) and opacity,
  *   {r, g, b, radius}   colour (SH evaluated, +0.5, clamped at 0) and the
  *                       integer radius ceil(3 sqrt(lambda_max)) (0 = culled),
- *   {depth, clamp_bits, 0, 0}  camera z; bit c set if channel c was clamped.
+ *   {depth, clamp_bits, ext_x, ext_y}  camera z; bit c set if channel c was
+ *                       clamped; half-extents of the pixels the Gaussian can
+ *                       reach: min(radius, sqrt(k Sigma'_xx)) (and yy) with
+ *                       k = 2 ln(o / alpha_min), i.e. the bounding box of the
+ *                       ellipse where alpha >= alpha_min (culled if k <= 0).
  * proj: DEVICE [P,16]. status: DEVICE int32[4] (unused here, may be NULL). */
 int gs_project(const gs_gaussians *g, const gs_views *views, const gs_config *cfg,
                float *proj, int32_t *status, void *stream);
 
 /* Bin the projected records into tiles and sort each tile by (depth, slot).
- * A record touches the tiles [floor((x-r)/tw), floor((x+r)/tw)] x (same in
- * y), clipped to the view's grid, computed in float32. If the instance count
+ * A record with radius > 0 touches the tiles [floor((x-ext_x)/tw),
+ * floor((x+ext_x)/tw)] x [floor((y-ext_y)/th), floor((y+ext_y)/th)], clipped
+ * to the view's grid, computed in float32. If the instance count
  * exceeds bins->capacity, status = {GS_ERR_CAPACITY, needed} and the lists
  * are left unsorted; counters[0] holds the count either way (a call with
  * capacity 0 is a pure count). */
@@ -172,7 +180,8 @@ int gs_render_fwd(const gs_views *views, const gs_config *cfg, const float *proj
 
 /* Backward of gs_project + gs_render_fwd for the upstream gradient
  * dL_dimage (same layout as image). image must be the forward's output for
- * the same inputs (transmittance is recomputed from it, not stored).
+ * the same inputs (transmittance is recomputed, not stored; the colour
+ * behind each Gaussian is taken from the image).
  * Writes grads->grad2d (zeroed by the call), the raw-parameter gradients
  * (unless want_gaussian_grads == 0) and grads->pose_partials. */
 int gs_render_bwd(const gs_gaussians *g, const gs_views *views, const gs_config *cfg,
@@ -182,10 +191,11 @@ int gs_render_bwd(const gs_gaussians *g, const gs_views *views, const gs_config 
 
 /* The two stages of gs_render_bwd, callable separately (same arguments and
  * semantics as there). gs_rasterize_bwd zeroes grad2d [P,12] and adds the
- * per-slot 2D gradients dL/d(x,y,A,B | C,o,r,g | b); gs_project_bwd chains
+ * per-slot 2D gradients (layout as gs_grads.grad2d); gs_project_bwd chains
  * grad2d to the raw parameters and the pose partials. */
 int gs_rasterize_bwd(const gs_views *views, const gs_config *cfg, const float *proj, const gs_bins *bins,
-                     const float *image, const float *dL_dimage, float *grad2d, int32_t *status, void *stream);
+                     const float *image, const float *dL_dimage, float *grad2d, int32_t *status,
+                     void *stream);
 int gs_project_bwd(const gs_gaussians *g, const gs_views *views, const gs_config *cfg, const float *proj,
                    const float *grad2d, const gs_grads *grads, int want_gaussian_grads, int32_t *status,
                    void *stream);

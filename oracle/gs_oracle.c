@@ -25,8 +25,12 @@
  *     mean2D = (fx x/z + cx, fy y/z + cy); pixel (u,v) has centre (u+.5, v+.5).
  *     colour = max(0, sum_k f_k Y_k(dir) + 0.5), dir = normalise(mu - C_v),
  *     C_v = -R_v^T t_v, real SH with the Condon-Shortley phase.
- *   Binning is done in float32 (bit-exact contract with the GPU), sorting by
- *   (float32 depth, index). Compositing per pixel, front to back, over the
+ *   A Gaussian of opacity o can give alpha >= alpha_min only inside the
+ *   ellipse d^T conic d <= k, k = 2 ln(o / alpha_min) (culled if k <= 0);
+ *   the half-extents of that ellipse's bounding box, min(radius,
+ *   sqrt(k Sigma'_xx)) and min(radius, sqrt(k Sigma'_yy)), bound the tiles
+ *   it can touch. Binning is done in float32 (bit-exact contract with the
+ *   GPU) from those extents, sorting by (float32 depth, index). Compositing per pixel, front to back, over the
  *   Gaussians whose tile rectangle holds the pixel's tile and whose square
  *   |dx|,|dy| <= radius holds the pixel centre:
  *     alpha = min(alpha_max, o exp(-1/2 d^T conic d)); skipped if the
@@ -205,7 +209,7 @@ typedef struct {
     double px, py, depth;
     double s[3], qn[4], qlen, Rq[9], M[9], Sig[9];
     double u, w; int u_in, w_in;
-    double J[6], T[6], cov[3], det, conic[3], lam, r_real;
+    double J[6], T[6], cov[3], det, conic[3], lam, r_real, ext[2];
     int radius;
     double o;
     double dir[3], dlen, d[3], Y[16], dY[48];
@@ -298,6 +302,11 @@ static void project_one(const double *mean, const double *ls, const double *quat
     if (f->px + r < 0 || f->px - r > cam->W || f->py + r < 0 || f->py - r > cam->H) return;
 
     f->o = 1.0 / (1.0 + exp(-logit));
+    /* bounding box of the region where alpha can reach alpha_min */
+    double k = 2.0 * log(f->o / P->alpha_min);
+    if (!(k > 0)) return;
+    f->ext[0] = fmin(r, sqrt(k * f->cov[0]));
+    f->ext[1] = fmin(r, sqrt(k * f->cov[2]));
 
     /* view-dependent colour */
     double C[3];
@@ -320,11 +329,11 @@ static void project_one(const double *mean, const double *ls, const double *quat
 
 /* Project n Gaussians (FP64 inputs) into one view. Outputs per Gaussian:
  * xy[2], depth, conic[3], cov[3] (dilated), opacity, rgb[3], radius (0 =
- * culled), r_real = 3 sqrt(lambda_max), clamped[3]. */
+ * culled), r_real = 3 sqrt(lambda_max), clamped[3], ext[2] (tile extents). */
 void or_project(int64_t n, int deg, const double *means, const double *log_scales, const double *quats,
                 const double *logits, const double *sh, const or_cam *cam, const or_params *P,
                 double *xy, double *depth, double *conic, double *cov, double *opac, double *rgb,
-                int32_t *radius, double *r_real, int32_t *clamped)
+                int32_t *radius, double *r_real, int32_t *clamped, double *ext)
 {
     int K = (deg + 1) * (deg + 1);
     for (int64_t i = 0; i < n; ++i) {
@@ -338,6 +347,8 @@ void or_project(int64_t n, int deg, const double *means, const double *log_scale
             clamped[3 * i + a] = f.clamped[a];
         }
         opac[i] = f.o;
+        ext[2 * i] = f.valid ? f.ext[0] : 0.0;
+        ext[2 * i + 1] = f.valid ? f.ext[1] : 0.0;
         radius[i] = f.valid ? f.radius : 0;
         r_real[i] = f.valid ? f.r_real : 0.0;
     }
@@ -347,12 +358,12 @@ void or_project(int64_t n, int deg, const double *means, const double *log_scale
 /* binning in float32                                                       */
 /* ------------------------------------------------------------------------ */
 
-static void rect_f32(float x, float y, float r, int TW, int TH, int Gx, int Gy,
+static void rect_f32(float x, float y, float ex, float ey, int TW, int TH, int Gx, int Gy,
                      int *x0, int *x1, int *y0, int *y1)
 {
     float tw = (float)TW, th = (float)TH;
-    float a0 = floorf((x - r) / tw), a1 = floorf((x + r) / tw) + 1.0f;
-    float b0 = floorf((y - r) / th), b1 = floorf((y + r) / th) + 1.0f;
+    float a0 = floorf((x - ex) / tw), a1 = floorf((x + ex) / tw) + 1.0f;
+    float b0 = floorf((y - ey) / th), b1 = floorf((y + ey) / th) + 1.0f;
     a0 = a0 < 0.0f ? 0.0f : (a0 > (float)Gx ? (float)Gx : a0);
     a1 = a1 < 0.0f ? 0.0f : (a1 > (float)Gx ? (float)Gx : a1);
     b0 = b0 < 0.0f ? 0.0f : (b0 > (float)Gy ? (float)Gy : b0);
@@ -361,8 +372,9 @@ static void rect_f32(float x, float y, float r, int TW, int TH, int Gx, int Gy,
 }
 
 /* Count tile instances of n projected Gaussians of one view. r == 0 means
- * culled. Writes counts[Gx*Gy] (tile id ty*Gx + tx); returns the total. */
-int64_t or_bin_count(int64_t n, const float *x, const float *y, const int32_t *r, int W, int H,
+ * culled; ext[2i], ext[2i+1] are the half-extents of the tile rectangle.
+ * Writes counts[Gx*Gy] (tile id ty*Gx + tx); returns the total. */
+int64_t or_bin_count(int64_t n, const float *x, const float *y, const int32_t *r, const float *ext, int W, int H,
                      int TW, int TH, int32_t *counts)
 {
     int Gx = (W + TW - 1) / TW, Gy = (H + TH - 1) / TH;
@@ -371,7 +383,7 @@ int64_t or_bin_count(int64_t n, const float *x, const float *y, const int32_t *r
     for (int64_t i = 0; i < n; ++i) {
         if (r[i] <= 0) continue;
         int x0, x1, y0, y1;
-        rect_f32(x[i], y[i], (float)r[i], TW, TH, Gx, Gy, &x0, &x1, &y0, &y1);
+        rect_f32(x[i], y[i], ext[2 * i], ext[2 * i + 1], TW, TH, Gx, Gy, &x0, &x1, &y0, &y1);
         for (int ty = y0; ty < y1; ++ty)
             for (int tx = x0; tx < x1; ++tx) { counts[ty * Gx + tx]++; total++; }
     }
@@ -387,14 +399,14 @@ static int cmp_u64(const void *a, const void *b)
 /* Fill the per-tile lists: ranges[2*tile] = [start, end) in tile-id order,
  * keys[j] = (float32 bits of depth << 32) | index, ascending within a tile,
  * ids[j] = index. Arrays must hold the total from or_bin_count. */
-void or_bin_fill(int64_t n, const float *x, const float *y, const int32_t *r, const float *depth,
-                 int W, int H, int TW, int TH, int64_t *ranges, uint64_t *keys, int32_t *ids)
+void or_bin_fill(int64_t n, const float *x, const float *y, const int32_t *r, const float *ext,
+                 const float *depth, int W, int H, int TW, int TH, int64_t *ranges, uint64_t *keys, int32_t *ids)
 {
     int Gx = (W + TW - 1) / TW, Gy = (H + TH - 1) / TH;
     int64_t G = (int64_t)Gx * Gy;
     int32_t *counts = (int32_t *)calloc((size_t)G, sizeof(int32_t));
     int64_t *fill = (int64_t *)calloc((size_t)G, sizeof(int64_t));
-    or_bin_count(n, x, y, r, W, H, TW, TH, counts);
+    or_bin_count(n, x, y, r, ext, W, H, TW, TH, counts);
     int64_t acc = 0;
     for (int64_t t = 0; t < G; ++t) {
         ranges[2 * t] = acc;
@@ -405,7 +417,7 @@ void or_bin_fill(int64_t n, const float *x, const float *y, const int32_t *r, co
     for (int64_t i = 0; i < n; ++i) {
         if (r[i] <= 0) continue;
         int x0, x1, y0, y1;
-        rect_f32(x[i], y[i], (float)r[i], TW, TH, Gx, Gy, &x0, &x1, &y0, &y1);
+        rect_f32(x[i], y[i], ext[2 * i], ext[2 * i + 1], TW, TH, Gx, Gy, &x0, &x1, &y0, &y1);
         uint32_t bits;
         memcpy(&bits, &depth[i], 4);
         for (int ty = y0; ty < y1; ++ty)

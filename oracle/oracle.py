@@ -154,13 +154,13 @@ def project_view(scene, views, v, params: Params = None):
     n = c
     out = dict(xy=np.zeros((n, 2)), depth=np.zeros(n), conic=np.zeros((n, 3)), cov=np.zeros((n, 3)),
                opac=np.zeros(n), rgb=np.zeros((n, 3)), radius=np.zeros(n, np.int32),
-               r_real=np.zeros(n), clamped=np.zeros((n, 3), np.int32))
+               r_real=np.zeros(n), clamped=np.zeros((n, 3), np.int32), ext=np.zeros((n, 2)))
     cam = view_camera(views, v)
     prm = params.c()
     lib().or_project(ctypes.c_int64(n), ctypes.c_int(scene.sh_degree), _p(means), _p(ls), _p(q), _p(lg),
                      _p(sh), ctypes.byref(cam), ctypes.byref(prm),
                      _p(out["xy"]), _p(out["depth"]), _p(out["conic"]), _p(out["cov"]), _p(out["opac"]),
-                     _p(out["rgb"]), _p(out["radius"]), _p(out["r_real"]), _p(out["clamped"]))
+                     _p(out["rgb"]), _p(out["radius"]), _p(out["r_real"]), _p(out["clamped"]), _p(out["ext"]))
     return out
 
 
@@ -168,35 +168,42 @@ def tile_grid(W, H, TW, TH):
     return (W + TW - 1) // TW, (H + TH - 1) // TH
 
 
-def bin_view(x, y, r, depth, W, H, TW=16, TH=16):
+def bin_view(x, y, r, depth, W, H, TW=16, TH=16, ext=None):
     """Float32 binning: ranges [G,2] (tile id ty*Gx+tx), keys uint64
-    (depth bits << 32 | local index) ascending per tile, ids int32."""
+    (depth bits << 32 | local index) ascending per tile, ids int32. The tile
+    rectangle's half-extents are ext [n,2] (float32), or r if ext is None."""
     x = np.ascontiguousarray(x, np.float32)
     y = np.ascontiguousarray(y, np.float32)
     depth = np.ascontiguousarray(depth, np.float32)
     r = np.ascontiguousarray(r, np.int32)
+    if ext is None:
+        ext = np.stack([r, r], axis=1)
+    ext = np.ascontiguousarray(ext, np.float32)
     n = x.shape[0]
     Gx, Gy = tile_grid(W, H, TW, TH)
     counts = np.zeros(Gx * Gy, np.int32)
-    total = lib().or_bin_count(ctypes.c_int64(n), _p(x), _p(y), _p(r), W, H, TW, TH, _p(counts))
+    total = lib().or_bin_count(ctypes.c_int64(n), _p(x), _p(y), _p(r), _p(ext), W, H, TW, TH, _p(counts))
     ranges = np.zeros((Gx * Gy, 2), np.int64)
     keys = np.zeros(max(total, 1), np.uint64)
     ids = np.zeros(max(total, 1), np.int32)
-    lib().or_bin_fill(ctypes.c_int64(n), _p(x), _p(y), _p(r), _p(depth), W, H, TW, TH,
+    lib().or_bin_fill(ctypes.c_int64(n), _p(x), _p(y), _p(r), _p(ext), _p(depth), W, H, TW, TH,
                       _p(ranges), _p(keys), _p(ids))
     return ranges, keys[:total], ids[:total]
 
 
 def bins_for_render(proj, W, H, TW, TH, params: Params = None):
-    """Tile lists for rendering: float32-rounded means/depths, and radius + 1
-    where 3 sqrt(lambda) sits within the gate margin of an integer, so that
-    every Gaussian a float32 evaluation could list is present."""
+    """Tile lists for rendering: float32-rounded means/depths and extents
+    enlarged by a hair (and by one pixel where 3 sqrt(lambda) sits within the
+    gate margin of an integer), so that every Gaussian a float32 evaluation
+    could list is present. The lists only bound the search: compositing
+    applies the radius gate and the alpha rule itself."""
     params = params or Params()
     r = proj["radius"].copy()
     fr = proj["r_real"] - np.floor(proj["r_real"])
     amb = (r > 0) & ((fr < params.eps_gate) | (fr > 1 - params.eps_gate))
-    r[amb] += 1
-    return bin_view(proj["xy"][:, 0], proj["xy"][:, 1], r, proj["depth"], W, H, TW, TH)
+    ext = proj["ext"] * (1 + 1e-5) + 1e-4
+    ext[amb] += 1.0
+    return bin_view(proj["xy"][:, 0], proj["xy"][:, 1], r, proj["depth"], W, H, TW, TH, ext)
 
 
 def render_view(proj, W, H, TW=16, TH=16, params: Params = None, bins=None, mask=None):

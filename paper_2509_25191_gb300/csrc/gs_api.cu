@@ -46,7 +46,7 @@ static int build_launch(const gs_views *vw, const gs_config *cfg, Launch &L) {
     const int V = vw->n_views;
     if (V < 1 || V > GS_MAX_VIEWS) return GS_ERR_ARG;
     if (!vw->width || !vw->height || !vw->gauss_begin || !vw->gauss_count) return GS_ERR_ARG;
-    if (!tile_supported(cfg->tile_w, cfg->tile_h)) return GS_ERR_UNSUPPORTED;
+    if (!tile_supported(cfg->tile_w, cfg->tile_h) || !cfg->pixel_gate) return GS_ERR_UNSUPPORTED;
     memset(&L, 0, sizeof L);
     L.n_views = V;
     L.tw = cfg->tile_w;
@@ -212,7 +212,8 @@ int gs_render_fwd(const gs_views *vw, const gs_config *cfg, const float *proj, c
 }
 
 int gs_rasterize_bwd(const gs_views *vw, const gs_config *cfg, const float *proj, const gs_bins *b,
-                     const float *image, const float *dL_dimage, float *grad2d, int32_t *status, void *stream) {
+                     const float *image, const float *dL_dimage, float *grad2d, int32_t *status,
+                     void *stream) {
     (void)status;
     Launch L;
     int rc = build_launch(vw, cfg, L);

@@ -1,7 +1,7 @@
 // Tile binning and per-tile depth sort.
 //
 // Every projected record with radius > 0 touches the tiles of its float32
-// rectangle (tile_rect in gs_common.cuh). Instead of a global radix sort of
+// rectangle (tile_rect in gs_common.cuh), built from its reach extents. Instead of a global radix sort of
 // (tile, depth) keys over all instances, the instances are bucketed by tile
 // (count -> scan -> scatter with per-tile cursors) and each tile's bucket is
 // then sorted on chip by the 64-bit key (float32 depth bits << 32 | slot).
@@ -11,36 +11,78 @@
 // IEEE bits sort like the values.
 //
 // Kernels:
-//   k_bin_count    one thread per slot, atomic per-tile counts
+//   k_bin_count    per-tile counts, block-aggregated in shared memory
 //   k_bin_scan     one block: tile ranges, cursors, instance total, capacity
 //                  check, and a work order of tiles by decreasing count
-//   k_bin_scatter  one thread per slot, writes keys at per-tile cursors
-//   k_sort_small   persistent; tiles of <= 2047 instances, bitonic in smem
-//   k_sort_large   persistent; larger tiles: bitonic on 16384-key chunks in
-//                  smem, then merge-path merges through keys_tmp
+//   k_bin_scatter  writes keys: one global reservation per (block, tile),
+//                  placement inside it by shared-memory atomics
+//   k_sort_tiles   persistent, largest tiles first; radix sort on chip
+//                  (chunks + merge path for tiles above 4096 instances)
 #include "gs_common.cuh"
 
 namespace gsk {
 
-constexpr int SORT_SMALL_CAP = 2048;    // padded size (instances <= 2047)
-constexpr int SORT_SMALL_THREADS = 256;
-constexpr int SORT_LARGE_CAP = 16384;   // 128 KB of keys
-constexpr int SORT_LARGE_THREADS = 1024;
-constexpr int LARGE_BUCKET = 12;        // bucket of counts >= 2048
+constexpr int LARGE_BUCKET = 13;        // bucket of counts >= 4096 (chunked sort)
 
-__global__ void __launch_bounds__(256) k_bin_count(const Launch L, const float4 *__restrict__ proj,
-                                                   int *__restrict__ tile_count) {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= L.n_slots) return;
+// Slots are processed in chunks of BIN_CHUNK per block. Within a chunk, the
+// tile counts of each view segment are first gathered in a shared-memory
+// histogram and then added to global memory once per (block, tile), which
+// removes almost all same-address contention on the per-tile counters.
+// Views with more tiles than BIN_SMEM_TILES fall back to direct atomics.
+constexpr int BIN_THREADS = 512;
+constexpr int BIN_CHUNK = 4096;
+constexpr int BIN_SMEM_TILES = 12288;   // 48 KB of int counters
+
+__device__ __forceinline__ bool slot_rect(const Launch &L, const float4 *__restrict__ proj, long long p,
+                                          const ViewDesc &vd, int &x0, int &x1, int &y0, int &y1) {
     const float4 r2 = proj[4 * p + 2];
-    if (!(r2.w > 0.f)) return;
+    if (!(r2.w > 0.f)) return false;
     const float4 r0 = proj[4 * p];
-    const int v = view_of_slot(L, p);
-    const ViewDesc &vd = L.v[v];
-    int x0, x1, y0, y1;
-    tile_rect(r0.x, r0.y, r2.w, 1.f / (float)L.tw, 1.f / (float)L.th, vd.Gx, vd.Gy, x0, x1, y0, y1);
-    for (int ty = y0; ty < y1; ++ty)
-        for (int tx = x0; tx < x1; ++tx) atomicAdd(tile_count + vd.tile_base + ty * vd.Gx + tx, 1);
+    const float4 r3 = proj[4 * p + 3];
+    tile_rect(r0.x, r0.y, r3.z, r3.w, 1.f / (float)L.tw, 1.f / (float)L.th, vd.Gx, vd.Gy, x0, x1, y0, y1);
+    return true;
+}
+
+// next view segment [seg, seg_end) of a chunk that ends at c1
+__device__ __forceinline__ long long segment_end(const Launch &L, int v, long long c1) {
+    const long long e = (v + 1 < L.n_views) ? L.v[v + 1].slot_base : L.n_slots;
+    return e < c1 ? e : c1;
+}
+
+__global__ void __launch_bounds__(BIN_THREADS) k_bin_count(const Launch L, const float4 *__restrict__ proj,
+                                                           int *__restrict__ tile_count) {
+    __shared__ int s_cnt[BIN_SMEM_TILES];
+    const long long c0 = (long long)blockIdx.x * BIN_CHUNK;
+    const long long c1 = c0 + BIN_CHUNK < L.n_slots ? c0 + BIN_CHUNK : L.n_slots;
+    for (long long seg = c0; seg < c1;) {
+        const int v = view_of_slot(L, seg);
+        const long long seg_end = segment_end(L, v, c1);
+        const ViewDesc &vd = L.v[v];
+        const int Tv = vd.Gx * vd.Gy;
+        const bool on_chip = Tv <= BIN_SMEM_TILES;
+        if (on_chip) {
+            for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) s_cnt[t] = 0;
+            __syncthreads();
+        }
+        for (long long p = seg + threadIdx.x; p < seg_end; p += BIN_THREADS) {
+            int x0, x1, y0, y1;
+            if (!slot_rect(L, proj, p, vd, x0, x1, y0, y1)) continue;
+            for (int ty = y0; ty < y1; ++ty)
+                for (int tx = x0; tx < x1; ++tx) {
+                    if (on_chip) atomicAdd(s_cnt + ty * vd.Gx + tx, 1);
+                    else atomicAdd(tile_count + vd.tile_base + ty * vd.Gx + tx, 1);
+                }
+        }
+        if (on_chip) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) {
+                const int c = s_cnt[t];
+                if (c) atomicAdd(tile_count + vd.tile_base + t, c);
+            }
+            __syncthreads();
+        }
+        seg = seg_end;
+    }
 }
 
 __device__ __forceinline__ int count_bucket(int c) { return c <= 0 ? 0 : 32 - __clz(c); }
@@ -132,82 +174,197 @@ __global__ void __launch_bounds__(1024) k_bin_scan(const Launch L, long long cap
     }
 }
 
-__global__ void __launch_bounds__(256) k_bin_scatter(const Launch L, const float4 *__restrict__ proj,
-                                                     int *__restrict__ cursor,
-                                                     unsigned long long *__restrict__ keys,
-                                                     const int *__restrict__ counters) {
+// Same chunking as k_bin_count: each block reserves one contiguous range per
+// (block, tile) with a single global atomic, then places its instances inside
+// the range with shared-memory atomics.
+__global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, const float4 *__restrict__ proj,
+                                                             int *__restrict__ cursor,
+                                                             unsigned long long *__restrict__ keys,
+                                                             const int *__restrict__ counters) {
+    __shared__ int s_cnt[BIN_SMEM_TILES];
     if (counters[CNT_ABORT]) return;
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= L.n_slots) return;
-    const float4 r2 = proj[4 * p + 2];
-    if (!(r2.w > 0.f)) return;
-    const float4 r0 = proj[4 * p];
-    const float depth = proj[4 * p + 3].x;
-    const int v = view_of_slot(L, p);
-    const ViewDesc &vd = L.v[v];
-    int x0, x1, y0, y1;
-    tile_rect(r0.x, r0.y, r2.w, 1.f / (float)L.tw, 1.f / (float)L.th, vd.Gx, vd.Gy, x0, x1, y0, y1);
-    const unsigned long long key =
-        ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned long long)(unsigned int)p;
-    for (int ty = y0; ty < y1; ++ty)
-        for (int tx = x0; tx < x1; ++tx) {
-            int pos = atomicAdd(cursor + vd.tile_base + ty * vd.Gx + tx, 1);
-            keys[pos] = key;
-        }
-}
-
-// ascending bitonic sort of s[0..n2), n2 a power of two, by the whole block
-__device__ __forceinline__ void block_bitonic(unsigned long long *s, int n2) {
-    const int half = n2 >> 1;
-    for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < half; i += blockDim.x) {
-                const int a = ((i & ~(j - 1)) << 1) | (i & (j - 1));
-                const int b = a | j;
-                const unsigned long long ka = s[a], kb = s[b];
-                const bool up = (a & k) == 0;
-                if ((ka > kb) == up) { s[a] = kb; s[b] = ka; }
+    const long long c0 = (long long)blockIdx.x * BIN_CHUNK;
+    const long long c1 = c0 + BIN_CHUNK < L.n_slots ? c0 + BIN_CHUNK : L.n_slots;
+    for (long long seg = c0; seg < c1;) {
+        const int v = view_of_slot(L, seg);
+        const long long seg_end = segment_end(L, v, c1);
+        const ViewDesc &vd = L.v[v];
+        const int Tv = vd.Gx * vd.Gy;
+        const bool on_chip = Tv <= BIN_SMEM_TILES;
+        if (on_chip) {
+            for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) s_cnt[t] = 0;
+            __syncthreads();
+            for (long long p = seg + threadIdx.x; p < seg_end; p += BIN_THREADS) {
+                int x0, x1, y0, y1;
+                if (!slot_rect(L, proj, p, vd, x0, x1, y0, y1)) continue;
+                for (int ty = y0; ty < y1; ++ty)
+                    for (int tx = x0; tx < x1; ++tx) atomicAdd(s_cnt + ty * vd.Gx + tx, 1);
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) {
+                const int c = s_cnt[t];
+                if (c) s_cnt[t] = atomicAdd(cursor + vd.tile_base + t, c);
             }
             __syncthreads();
         }
+        for (long long p = seg + threadIdx.x; p < seg_end; p += BIN_THREADS) {
+            int x0, x1, y0, y1;
+            if (!slot_rect(L, proj, p, vd, x0, x1, y0, y1)) continue;
+            const float depth = proj[4 * p + 3].x;
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned long long)(unsigned int)p;
+            for (int ty = y0; ty < y1; ++ty)
+                for (int tx = x0; tx < x1; ++tx) {
+                    const int t = ty * vd.Gx + tx;
+                    const int pos = on_chip ? atomicAdd(s_cnt + t, 1) : atomicAdd(cursor + vd.tile_base + t, 1);
+                    keys[pos] = key;
+                }
+        }
+        if (on_chip) __syncthreads();
+        seg = seg_end;
     }
 }
 
-__device__ __forceinline__ int next_pow2(int n) { return n <= 1 ? 1 : 1 << (32 - __clz(n - 1)); }
+// ---------------------------------------------------------------------------
+// per-tile sort: stable block-wide LSD radix sort of the 32-bit depth bits
+// (8-bit digits; passes above the tile's highest differing bit are skipped),
+// carrying the slot, then a fix-up that orders runs of equal depth by slot.
+// The result is the unique (depth, slot) order. Tiles longer than SORT_CAP
+// are sorted in chunks and merged (merge path) through keys_tmp.
+// ---------------------------------------------------------------------------
+constexpr int SORT_THREADS = 512;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_CAP = 4096;
+constexpr int SORT_SEG_MIN = 128;   // at least this many keys per active warp
 
-__device__ __forceinline__ void sort_in_smem(unsigned long long *s, unsigned long long *keys, int st, int n) {
-    const int n2 = next_pow2(n);
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) s[i] = i < n ? keys[st + i] : ~0ull;
-    __syncthreads();
-    block_bitonic(s, n2);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) keys[st + i] = s[i];
-    __syncthreads();
-}
+struct SortSmem {
+    unsigned int key[2][SORT_CAP];
+    unsigned int val[2][SORT_CAP];
+    unsigned int hist[SORT_WARPS][256];   // digit counts, then running offsets
+    unsigned int part[SORT_THREADS];
+    unsigned int kmin, kmax;
+    int item;
+};
 
-__device__ __forceinline__ void write_ids(const unsigned long long *keys, unsigned int *ids, int st, int n) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) ids[st + i] = (unsigned int)(keys[st + i] & 0xffffffffu);
-}
-
-__global__ void __launch_bounds__(SORT_SMALL_THREADS) k_sort_small(const Launch L, const int2 *__restrict__ ranges,
-                                                                   const int *__restrict__ order,
-                                                                   unsigned long long *__restrict__ keys,
-                                                                   unsigned int *__restrict__ ids,
-                                                                   int *__restrict__ counters) {
-    __shared__ unsigned long long s[SORT_SMALL_CAP];
-    __shared__ int s_item;
-    if (counters[CNT_ABORT]) return;
-    const int first = counters[CNT_LARGE_TILES];
-    for (;;) {
-        if (threadIdx.x == 0) s_item = first + atomicAdd(counters + CNT_Q_SORT, 1);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
-        if (item >= L.n_tiles) break;
-        const int2 r = ranges[order[item]];
-        const int n = r.y - r.x;
-        if (n > 1) sort_in_smem(s, keys, r.x, n);
-        write_ids(keys, ids, r.x, n);
+// exclusive scan of the (digit, warp)-ordered counts hist[w][d], w < nwa
+__device__ __forceinline__ void scan_hist(SortSmem &S, int nwa) {
+    const int E = 256 * nwa;
+    const int per = (E + SORT_THREADS - 1) / SORT_THREADS;
+    const int e0 = min(E, (int)threadIdx.x * per), e1 = min(E, e0 + per);
+    unsigned int sum = 0;
+    for (int e = e0; e < e1; ++e) sum += S.hist[e % nwa][e / nwa];
+    // block exclusive scan of the per-thread sums
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
     }
+    if (lane == 31) S.part[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned int w = lane < SORT_WARPS ? S.part[lane] : 0, wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < SORT_WARPS) S.part[lane] = wi - w;
+    }
+    __syncthreads();
+    unsigned int run = S.part[wid] + incl - sum;
+    for (int e = e0; e < e1; ++e) {
+        unsigned int &h = S.hist[e % nwa][e / nwa];
+        const unsigned int c = h;
+        h = run;
+        run += c;
+    }
+    __syncthreads();
+}
+
+// sort keys[st .. st+n) (n <= SORT_CAP) in place by (depth, slot)
+__device__ void radix_sort_tile(SortSmem &S, unsigned long long *__restrict__ keys, unsigned int *__restrict__ ids,
+                                int st, int n, bool write_ids) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) { S.kmin = 0xffffffffu; S.kmax = 0u; }
+    __syncthreads();
+    unsigned int lmin = 0xffffffffu, lmax = 0u;
+    for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
+        const unsigned long long k = keys[st + i];
+        const unsigned int d = (unsigned int)(k >> 32);
+        S.key[0][i] = d;
+        S.val[0][i] = (unsigned int)(k & 0xffffffffu);
+        lmin = min(lmin, d);
+        lmax = max(lmax, d);
+    }
+    atomicMin(&S.kmin, lmin);
+    atomicMax(&S.kmax, lmax);
+    __syncthreads();
+    const unsigned int diff = S.kmin ^ S.kmax;
+    const int passes = diff ? (32 - __clz(diff) + 7) / 8 : 0;
+    const int nwa = max(1, min(SORT_WARPS, (n + SORT_SEG_MIN - 1) / SORT_SEG_MIN));
+    const int seg = ((n + nwa - 1) / nwa + 31) & ~31;
+    const int s0 = wid * seg, s1 = min(n, s0 + seg);
+    const unsigned int lt_mask = (1u << lane) - 1u;
+    int cur = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        for (int e = threadIdx.x; e < 256 * nwa; e += SORT_THREADS) S.hist[e / 256][e % 256] = 0;
+        __syncthreads();
+        if (wid < nwa) {
+            for (int b = s0; b < s1; b += 32) {
+                const int i = b + lane;
+                const bool act = i < s1;
+                const unsigned int d = act ? (S.key[cur][i] >> shift) & 255u : 256u + lane;
+                const unsigned int peers = __match_any_sync(0xffffffffu, d);
+                if (act && lane == __ffs(peers) - 1) S.hist[wid][d] += __popc(peers);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        scan_hist(S, nwa);
+        if (wid < nwa) {
+            for (int b = s0; b < s1; b += 32) {
+                const int i = b + lane;
+                const bool act = i < s1;
+                const unsigned int d = act ? (S.key[cur][i] >> shift) & 255u : 256u + lane;
+                const unsigned int peers = __match_any_sync(0xffffffffu, d);
+                unsigned int pos = 0;
+                if (act) pos = S.hist[wid][d] + __popc(peers & lt_mask);
+                __syncwarp();
+                if (act && lane == __ffs(peers) - 1) S.hist[wid][d] += __popc(peers);
+                if (act) {
+                    S.key[cur ^ 1][pos] = S.key[cur][i];
+                    S.val[cur ^ 1][pos] = S.val[cur][i];
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    // equal depths: order each run by slot (runs are rare and short)
+    for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
+        const unsigned int k = S.key[cur][i];
+        if ((i == 0 || S.key[cur][i - 1] != k) && i + 1 < n && S.key[cur][i + 1] == k) {
+            int e = i + 1;
+            while (e < n && S.key[cur][e] == k) ++e;
+            for (int a = i + 1; a < e; ++a) {
+                const unsigned int v = S.val[cur][a];
+                int b = a - 1;
+                while (b >= i && S.val[cur][b] > v) { S.val[cur][b + 1] = S.val[cur][b]; --b; }
+                S.val[cur][b + 1] = v;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
+        const unsigned int v = S.val[cur][i];
+        keys[st + i] = ((unsigned long long)S.key[cur][i] << 32) | v;
+        if (write_ids) ids[st + i] = v;
+    }
+    __syncthreads();
 }
 
 // merge sorted a[0..na) and b[0..nb) into out[0..na+nb) with the whole block
@@ -230,28 +387,35 @@ __device__ void block_merge(const unsigned long long *a, int na, const unsigned 
     }
 }
 
-__global__ void __launch_bounds__(SORT_LARGE_THREADS) k_sort_large(const Launch L, const int2 *__restrict__ ranges,
-                                                                   const int *__restrict__ order,
-                                                                   unsigned long long *__restrict__ keys,
-                                                                   unsigned long long *__restrict__ keys_tmp,
-                                                                   unsigned int *__restrict__ ids,
-                                                                   int *__restrict__ counters) {
-    extern __shared__ unsigned long long s_large[];
-    __shared__ int s_item;
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_tiles(const Launch L, const int2 *__restrict__ ranges,
+                                                             const int *__restrict__ order,
+                                                             unsigned long long *__restrict__ keys,
+                                                             unsigned long long *__restrict__ keys_tmp,
+                                                             unsigned int *__restrict__ ids,
+                                                             int *__restrict__ counters) {
+    extern __shared__ __align__(16) unsigned char sort_smem[];
+    SortSmem &S = *reinterpret_cast<SortSmem *>(sort_smem);
     if (counters[CNT_ABORT]) return;
-    const int n_large = counters[CNT_LARGE_TILES];
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counters + CNT_Q_SORT_L, 1);
+        if (threadIdx.x == 0) S.item = atomicAdd(counters + CNT_Q_SORT, 1);
         __syncthreads();
-        const int item = s_item;
+        const int item = S.item;
         __syncthreads();
-        if (item >= n_large) break;
+        if (item >= L.n_tiles) break;
         const int2 r = ranges[order[item]];
         const int n = r.y - r.x;
-        for (int c = 0; c < n; c += SORT_LARGE_CAP) sort_in_smem(s_large, keys, r.x + c, min(SORT_LARGE_CAP, n - c));
+        if (n <= 1) {
+            if (n == 1 && threadIdx.x == 0) ids[r.x] = (unsigned int)(keys[r.x] & 0xffffffffu);
+            continue;
+        }
+        if (n <= SORT_CAP) {
+            radix_sort_tile(S, keys, ids, r.x, n, true);
+            continue;
+        }
+        for (int c = 0; c < n; c += SORT_CAP) radix_sort_tile(S, keys, ids, r.x + c, min(SORT_CAP, n - c), false);
         // pairwise merges of sorted runs, ping-pong between keys and keys_tmp
         unsigned long long *src = keys + r.x, *dst = keys_tmp + r.x;
-        for (int w = SORT_LARGE_CAP; w < n; w <<= 1) {
+        for (int w = SORT_CAP; w < n; w <<= 1) {
             for (int m = 0; m < n; m += 2 * w) {
                 const int na = min(w, n - m), nb = max(0, min(w, n - m - w));
                 block_merge(src + m, na, src + m + na, nb, dst + m);
@@ -259,11 +423,11 @@ __global__ void __launch_bounds__(SORT_LARGE_THREADS) k_sort_large(const Launch 
             __syncthreads();
             unsigned long long *t = src; src = dst; dst = t;
         }
-        if (src != keys + r.x) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) keys[r.x + i] = src[i];
-            __syncthreads();
+        for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
+            const unsigned long long k = src[i];
+            if (src != keys + r.x) keys[r.x + i] = k;
+            ids[r.x + i] = (unsigned int)(k & 0xffffffffu);
         }
-        write_ids(keys, ids, r.x, n);
         __syncthreads();
     }
 }
@@ -272,29 +436,24 @@ int launch_bin_sort(const Launch &L, const float *proj, const gs_bins *b, int32_
     const float4 *p = reinterpret_cast<const float4 *>(proj);
     if (cudaMemsetAsync(b->tile_scratch, 0, sizeof(int) * (size_t)L.n_tiles, st) != cudaSuccess) return GS_ERR_CUDA;
     if (cudaMemsetAsync(b->counters, 0, sizeof(int) * GS_NUM_COUNTERS, st) != cudaSuccess) return GS_ERR_CUDA;
-    const int bs = 256;
-    const long long nb = (L.n_slots + bs - 1) / bs;
-    if (nb > 0) k_bin_count<<<nb, bs, 0, st>>>(L, p, b->tile_scratch);
+    const long long nb = (L.n_slots + BIN_CHUNK - 1) / BIN_CHUNK;
+    if (nb > 0) k_bin_count<<<nb, BIN_THREADS, 0, st>>>(L, p, b->tile_scratch);
     k_bin_scan<<<1, 1024, 0, st>>>(L, b->capacity, b->tile_scratch, reinterpret_cast<int2 *>(b->tile_ranges),
                                    b->tile_order, b->counters, status);
     if (nb > 0)
-        k_bin_scatter<<<nb, bs, 0, st>>>(L, p, b->tile_scratch, reinterpret_cast<unsigned long long *>(b->keys),
-                                         b->counters);
+        k_bin_scatter<<<nb, BIN_THREADS, 0, st>>>(L, p, b->tile_scratch,
+                                                  reinterpret_cast<unsigned long long *>(b->keys), b->counters);
     static int smem_set = 0;
-    const int large_smem = SORT_LARGE_CAP * (int)sizeof(unsigned long long);
+    const int smem = (int)sizeof(SortSmem);
     if (!smem_set) {
-        if (cudaFuncSetAttribute(k_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, large_smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
             return GS_ERR_CUDA;
         smem_set = 1;
     }
-    const int sms = num_sms();
-    k_sort_large<<<sms, SORT_LARGE_THREADS, large_smem, st>>>(
+    k_sort_tiles<<<2 * num_sms(), SORT_THREADS, smem, st>>>(
         L, reinterpret_cast<const int2 *>(b->tile_ranges), b->tile_order,
         reinterpret_cast<unsigned long long *>(b->keys), reinterpret_cast<unsigned long long *>(b->keys_tmp),
         b->ids, b->counters);
-    k_sort_small<<<sms * 8, SORT_SMALL_THREADS, 0, st>>>(L, reinterpret_cast<const int2 *>(b->tile_ranges),
-                                                         b->tile_order, reinterpret_cast<unsigned long long *>(b->keys),
-                                                         b->ids, b->counters);
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 

@@ -132,14 +132,15 @@ __device__ __forceinline__ ff project_coord(float f, float xh, float xl, float z
 }
 
 // Tile rectangle [x0,x1) x [y0,y1) of a record, in float32 exactly as the
-// bit-exact binning contract states: floor((x -+ r)/tile) (+1 for the end),
-// clamped to the grid. inv_tw = 1/tw is exact (tw a power of two).
-__device__ __forceinline__ void tile_rect(float x, float y, float r, float inv_tw, float inv_th,
+// bit-exact binning contract states: floor((x -+ ex)/tile) (+1 for the end),
+// same in y with ey, clamped to the grid. inv_tw = 1/tw is exact (tw a
+// power of two).
+__device__ __forceinline__ void tile_rect(float x, float y, float ex, float ey, float inv_tw, float inv_th,
                                           int Gx, int Gy, int &x0, int &x1, int &y0, int &y1) {
-    float a0 = floorf(__fmul_rn(__fsub_rn(x, r), inv_tw));
-    float a1 = __fadd_rn(floorf(__fmul_rn(__fadd_rn(x, r), inv_tw)), 1.0f);
-    float b0 = floorf(__fmul_rn(__fsub_rn(y, r), inv_th));
-    float b1 = __fadd_rn(floorf(__fmul_rn(__fadd_rn(y, r), inv_th)), 1.0f);
+    float a0 = floorf(__fmul_rn(__fsub_rn(x, ex), inv_tw));
+    float a1 = __fadd_rn(floorf(__fmul_rn(__fadd_rn(x, ex), inv_tw)), 1.0f);
+    float b0 = floorf(__fmul_rn(__fsub_rn(y, ey), inv_th));
+    float b1 = __fadd_rn(floorf(__fmul_rn(__fadd_rn(y, ey), inv_th)), 1.0f);
     x0 = (int)fminf(fmaxf(a0, 0.0f), (float)Gx);
     x1 = (int)fminf(fmaxf(a1, 0.0f), (float)Gx);
     y0 = (int)fminf(fmaxf(b0, 0.0f), (float)Gy);

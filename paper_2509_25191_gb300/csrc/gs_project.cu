@@ -3,12 +3,18 @@
 // One thread per Gaussian; the thread reads the Gaussian's raw record once
 // (mean, log-scale, quaternion, opacity logit, SH) and loops over the views
 // of its scene, writing one 64-byte record per (view, Gaussian) slot:
-//   {x, y, x_lo, y_lo} {A, B, C, o} {r, g, b, radius} {depth, clamp_bits, 0, 0}
+//   {x, y, x_lo, y_lo} {a, b, c, o} {r, g, b, radius} {depth, clamp_bits, ext_x, ext_y}
+// with (a, b, c) the dilated 2D covariance (its inverse is the conic).
 // Section 3.1: Sigma = R S S^T R^T, opacity, SH colour. EWA splatting:
 // Sigma' = J W Sigma W^T J^T + dilation I, conic = inverse, radius =
 // ceil(3 sqrt(lambda_max)). The camera-space mean and the pixel-space mean are
 // carried as float pairs so that 1000-pixel-wide images keep ~1e-5 px
 // accuracy (a plain float mean would be off by up to 1e-4 px there).
+// ext_x, ext_y bound the pixels the Gaussian can reach: alpha >= alpha_min
+// only inside the ellipse d^T conic d <= k, k = 2 ln(o / alpha_min), whose
+// bounding box has half-extents sqrt(k Sigma'_xx), sqrt(k Sigma'_yy); they are
+// clipped to the radius and enlarged by 2^-14 relative so that float32
+// rounding never shrinks the region. A Gaussian with k <= 0 is culled.
 #include "gs_common.cuh"
 
 namespace gsk {
@@ -64,9 +70,10 @@ __global__ void __launch_bounds__(128) k_project_fwd(const Launch L, const float
     const float S12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
     const float S22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
     const float opac = 1.f / (1.f + expf(-lg));
+    const float kext = 2.f * logf(opac / L.alpha_min);
     bool finite_in = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(S00) && isfinite(S11) &&
                      isfinite(S22) && isfinite(S01) && isfinite(S02) && isfinite(S12) && isfinite(opac) &&
-                     qn2 > 0.f;
+                     qn2 > 0.f && kext > 0.f;
 
     for (int v = L.s[s].v_begin; v < L.s[s].v_end; ++v) {
         const ViewDesc &vd = L.v[v];
@@ -135,14 +142,16 @@ __global__ void __launch_bounds__(128) k_project_fwd(const Launch L, const float
             if (acc < 0.f) { clamp_bits |= 1 << ch; acc = 0.f; }
             rgb[ch] = acc;
         }
-        const float A = cc * idet, B = -cb * idet, C = ca * idet;
-        ok = ok && isfinite(PX.hi) && isfinite(PY.hi) && isfinite(A) && isfinite(B) && isfinite(C) &&
-             isfinite(rgb[0]) && isfinite(rgb[1]) && isfinite(rgb[2]);
+        ok = ok && isfinite(PX.hi) && isfinite(PY.hi) && isfinite(idet) && isfinite(ca) && isfinite(cb) &&
+             isfinite(cc) && isfinite(rgb[0]) && isfinite(rgb[1]) && isfinite(rgb[2]);
         if (ok) {
+            const float grow = 1.f + 6.103515625e-05f;   // 1 + 2^-14
+            const float ex = fminf(radius, sqrtf(kext * ca) * grow);
+            const float ey = fminf(radius, sqrtf(kext * cc) * grow);
             out[0] = make_float4(PX.hi, PY.hi, PX.lo, PY.lo);
-            out[1] = make_float4(A, B, C, opac);
+            out[1] = make_float4(ca, cb, cc, opac);
             out[2] = make_float4(rgb[0], rgb[1], rgb[2], radius);
-            out[3] = make_float4(z, __int_as_float(clamp_bits), 0.f, 0.f);
+            out[3] = make_float4(z, __int_as_float(clamp_bits), ex, ey);
         } else {
             const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
             out[0] = zero; out[1] = zero; out[2] = zero; out[3] = zero;

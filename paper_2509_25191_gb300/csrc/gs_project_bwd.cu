@@ -10,7 +10,8 @@
 // fixed order, so the pose gradient is deterministic given grad2d.
 //
 // Chain (FP32, exact derivative of the forward in gs_project.cu):
-//   conic -> dilated 2D covariance (inverse), Sigma' = T Sigma T^T with
+//   dilated 2D covariance (its gradient comes from the raster backward),
+//   Sigma' = T Sigma T^T with
 //   T = J R_v, J with the tangent clamp (zero derivative through a clamped
 //   tangent), mean2D = f x / z + c, m = R_v mu + t_v, Sigma = M M^T with
 //   M = R(q) diag(exp l), q normalised, o = sigmoid, colour = max(0,
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(
                 contrib = ga4.x != 0.f || ga4.y != 0.f || ga4.z != 0.f || ga4.w != 0.f || gb4.x != 0.f ||
                           gb4.y != 0.f || gb4.z != 0.f || gb4.w != 0.f || gc4.x != 0.f;
                 if (contrib) {
-                    const float gx = ga4.x, gy = ga4.y, gA = ga4.z, gB = ga4.w, gC = gb4.x, gop = gb4.y;
+                    const float gx = ga4.x, gy = ga4.y, gsa = ga4.z, gsb = ga4.w, gsc = gb4.x, gop = gb4.y;
                     const float grgb[3] = {gb4.z, gb4.w, gc4.x};
                     const int clamp_bits = __float_as_int(proj[4 * slot + 3].y);
                     const ViewDesc &vd = L.v[v];
@@ -124,11 +125,6 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(
                     TS[3] = T[3] * S00 + T[4] * S01 + T[5] * S02;
                     TS[4] = T[3] * S01 + T[4] * S11 + T[5] * S12;
                     TS[5] = T[3] * S02 + T[4] * S12 + T[5] * S22;
-                    const float a = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + L.dilation;
-                    const float b = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
-                    const float c = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + L.dilation;
-                    const float det = a * c - b * b;
-                    const float id2 = 1.f / (det * det);
 
                     go += gop;
 
@@ -174,11 +170,8 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(
                         pg[9 + aa] += -(R[3 * aa] * gC3[0] + R[3 * aa + 1] * gC3[1] + R[3 * aa + 2] * gC3[2]);
                     }
 
-                    // conic (A,B,C) -> dilated covariance (a,b,c)
-                    const float ga = (-c * c * gA + b * c * gB - b * b * gC) * id2;
-                    const float gb = (2.f * b * c * gA - (a * c + b * b) * gB + 2.f * a * b * gC) * id2;
-                    const float gc = (-b * b * gA + a * b * gB - a * a * gC) * id2;
-                    const float P00 = ga, P01 = 0.5f * gb, P11 = gc;   // symmetric full-matrix gradient
+                    // grad2d carries dL/d(a, b, c) of the dilated covariance directly
+                    const float P00 = gsa, P01 = 0.5f * gsb, P11 = gsc;   // symmetric full-matrix gradient
                     // dL/dT = 2 P T Sigma
                     float GT[6];
 #pragma unroll

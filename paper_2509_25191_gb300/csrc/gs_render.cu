@@ -18,9 +18,9 @@
 // everything behind Gaussian i from the forward image,
 //   S_i = sum_{j>i} c_j alpha_j T_j + T_final bg = image - sum_{j<=i} c_j alpha_j T_j,
 // so that dL/dalpha_i = T_i (c_i . g) - (S_i . g) / (1 - alpha_i).
-// Per-Gaussian gradients (mean2D, conic, opacity, colour) are summed over a
-// warp with shuffles, over the block in shared memory, and added to the
-// per-slot grad2d record with one vector atomic per float4.
+// Per-Gaussian gradients (mean2D, 2D covariance, opacity, colour) are summed over a
+// warp with a shuffle reduce-scatter, over the block in shared memory, and
+// added to the per-slot grad2d record with one vector atomic per float4.
 #include "gs_common.cuh"
 
 namespace gsk {
@@ -28,44 +28,85 @@ namespace gsk {
 constexpr float LOG2E = 1.4426950408889634f;
 constexpr float LN2 = 0.69314718055994531f;
 
+// Staged instance: xy = mean relative to the block origin and the reach
+// half-extents (ext_x, ext_y <= radius, so the test |dx| <= ext_x, |dy| <=
+// ext_y implies the radius gate and rejects only pixels whose alpha is below
+// alpha_min anyway); con = quadratic-form coefficients and opacity; rgb =
+// colour and the slot.
+//
+// The exponent -1/2 d^T conic d is evaluated as the sum of two non-negative
+// terms, -1/2 [A u^2 + dy^2 / c] with u = dx - (b/c) dy and A = c / det (the
+// conditional x|y and marginal y parts of the 2D Gaussian with covariance
+// (a, b, c)). The expanded form A dx^2 + 2B dx dy + C dy^2 cancels badly for
+// elongated Gaussians far along their long axis (a factor ~100 in float32);
+// this one does not, at the same five operations per pixel.
 __device__ __forceinline__ void stage(const float4 *__restrict__ proj, unsigned int slot, float ox, float oy,
                                       float4 &xy, float4 &con, float4 &rgb) {
     const float4 r0 = proj[4ull * slot];
     const float4 r1 = proj[4ull * slot + 1];
     const float4 r2 = proj[4ull * slot + 2];
-    xy = make_float4(__fadd_rn(__fsub_rn(r0.x, ox), r0.z), __fadd_rn(__fsub_rn(r0.y, oy), r0.w), r2.w, r1.w);
-    con = make_float4(__fmul_rn(r1.x, -0.5f * LOG2E), __fmul_rn(r1.y, -LOG2E), __fmul_rn(r1.z, -0.5f * LOG2E),
-                      __uint_as_float(slot));
-    rgb = make_float4(r2.x, r2.y, r2.z, 0.f);
+    const float4 r3 = proj[4ull * slot + 3];
+    xy = make_float4(__fadd_rn(__fsub_rn(r0.x, ox), r0.z), __fadd_rn(__fsub_rn(r0.y, oy), r0.w), r3.z, r3.w);
+    // det = a c - b^2 with b^2 carried exactly
+    const ff bb = two_prod(r1.y, r1.y);
+    const float det = __fsub_rn(__fmaf_rn(r1.x, r1.z, -bb.hi), bb.lo);
+    const float A = __fdiv_rn(r1.z, det);
+    const float beta = __fdiv_rn(-r1.y, r1.z);
+    const float D = __fdiv_rn(1.f, r1.z);
+    con = make_float4(__fmul_rn(A, -0.5f * LOG2E), beta, __fmul_rn(D, -0.5f * LOG2E), r1.w);
+    rgb = make_float4(r2.x, r2.y, r2.z, __uint_as_float(slot));
 }
 
 // alpha of a staged Gaussian at pixel centre (pcx, pcy), block-relative.
 // Returns false if the Gaussian is skipped at this pixel.
-__device__ __forceinline__ bool eval_alpha(const float4 &xy, const float4 &con, float pcx, float pcy, int gate,
+__device__ __forceinline__ bool eval_alpha(const float4 &xy, const float4 &con, float pcx, float pcy,
                                            float alpha_min, float alpha_max, float &alpha, float &G, float &dx,
-                                           float &dy, bool &clamped) {
+                                           float &dy, float &u, bool &clamped) {
     dx = __fsub_rn(pcx, xy.x);
     dy = __fsub_rn(pcy, xy.y);
-    if (gate && (fabsf(dx) > xy.z || fabsf(dy) > xy.z)) return false;
-    const float p2 = __fmaf_rn(con.x, __fmul_rn(dx, dx),
-                               __fmaf_rn(con.z, __fmul_rn(dy, dy), __fmul_rn(con.y, __fmul_rn(dx, dy))));
+    if (fabsf(dx) > xy.z || fabsf(dy) > xy.w) return false;
+    u = __fmaf_rn(con.y, dy, dx);
+    const float p2 = __fmaf_rn(con.x, __fmul_rn(u, u), __fmul_rn(con.z, __fmul_rn(dy, dy)));
     if (p2 > 0.f) return false;
     G = ex2_approx(p2);
-    const float oG = __fmul_rn(xy.w, G);
+    const float oG = __fmul_rn(con.w, G);
     clamped = oG > alpha_max;
     alpha = clamped ? alpha_max : oG;
     return alpha >= alpha_min;
 }
 
-// Positions are staged relative to the origin of the enclosing 32x32-pixel
-// block (every supported tile nests in one), so a pixel's arithmetic is the
-// same for every tile shape and the image is bit-identical across shapes.
 struct TileInfo {
     int view, px, py;
     float ox, oy;     // block origin in pixels
     float pcx, pcy;   // this thread's pixel centre relative to the block origin
+    float tbx, tby;   // tile origin relative to the block origin
     bool inside;
 };
+
+// Pixels are assigned so that every warp covers an 8x4-pixel patch of the
+// tile (lane -> 8 columns x 4 rows), which lets whole warps skip Gaussians
+// that cannot reach their patch.
+template <int TW>
+__device__ __forceinline__ int pix_x(int t) { return ((t >> 5) % (TW / 8)) * 8 + (t & 7); }
+template <int TW>
+__device__ __forceinline__ int pix_y(int t) { return ((t >> 5) / (TW / 8)) * 4 + ((t & 31) >> 3); }
+
+// Bit w set if the staged Gaussian's reach box (enlarged by 1e-3 px, so the
+// test is conservative against float rounding) overlaps warp w's patch; the
+// per-pixel test |dx| <= ext_x, |dy| <= ext_y still decides exactly.
+template <int TW, int TH>
+__device__ __forceinline__ unsigned int warp_mask(const float4 &xy, float tbx, float tby) {
+    constexpr int NW = TW * TH / 32;
+    const float ex = xy.z + 1e-3f, ey = xy.w + 1e-3f;
+    unsigned int m = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const float x0 = tbx + (float)((w % (TW / 8)) * 8) + 0.5f, y0 = tby + (float)((w / (TW / 8)) * 4) + 0.5f;
+        const bool hit = xy.x + ex >= x0 && xy.x - ex <= x0 + 7.f && xy.y + ey >= y0 && xy.y - ey <= y0 + 3.f;
+        m |= (unsigned int)hit << w;
+    }
+    return m;
+}
 
 template <int TW, int TH>
 __device__ __forceinline__ TileInfo tile_info(const Launch &L, int tile) {
@@ -74,21 +115,36 @@ __device__ __forceinline__ TileInfo tile_info(const Launch &L, int tile) {
     const ViewDesc &vd = L.v[ti.view];
     const int lt = tile - vd.tile_base;
     const int tx = lt % vd.Gx, ty = lt / vd.Gx;
-    ti.px = tx * TW + (int)(threadIdx.x % TW);
-    ti.py = ty * TH + (int)(threadIdx.x / TW);
+    ti.px = tx * TW + pix_x<TW>((int)threadIdx.x);
+    ti.py = ty * TH + pix_y<TW>((int)threadIdx.x);
     const int bx = (tx * TW) & ~31, by = (ty * TH) & ~31;
     ti.ox = (float)bx;
     ti.oy = (float)by;
     ti.pcx = (float)(ti.px - bx) + 0.5f;
     ti.pcy = (float)(ti.py - by) + 0.5f;
+    ti.tbx = (float)(tx * TW - bx);
+    ti.tby = (float)(ty * TH - by);
     ti.inside = ti.px < vd.W && ti.py < vd.H;
     return ti;
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sum 16 per-lane values over the warp by recursive halving: after the four
+// halving steps lane l holds partial sums of value index
+// idx(l) = 8 [l&16] + 4 [l&8] + 2 [l&4] + [l&2] over the 16 lanes that share
+// bit 0, and the last exchange completes the 32-lane sum. 16 shuffles instead
+// of 5 per value.
+__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int o = 16, h = 8; o >= 2; o >>= 1, h >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const float send = up ? v[k] : v[k + h];
+            const float keep = up ? v[k + h] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 // add a thread's pair counts to the 64-bit counters at c[0], c[1] (one atomic per warp)
@@ -113,8 +169,10 @@ __global__ void __launch_bounds__(TW * TH) k_render_fwd(const Launch L, const fl
                                                         float *__restrict__ image) {
     constexpr int BS = TW * TH;
     __shared__ float4 s_xy[BS], s_con[BS], s_rgb[BS];
+    __shared__ unsigned int s_mask[BS];
     __shared__ int s_item;
     const bool abort = counters[CNT_ABORT] != 0;
+    const unsigned int wbit = 1u << (threadIdx.x >> 5);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counters + CNT_Q_FWD, 1);
         __syncthreads();
@@ -130,14 +188,18 @@ __global__ void __launch_bounds__(TW * TH) k_render_fwd(const Launch L, const fl
         for (int b0 = r.x; b0 < r.y; b0 += BS) {
             if (__syncthreads_count(done) == BS) break;
             const int j = b0 + threadIdx.x;
-            if (j < r.y) stage(proj, ids[j], ti.ox, ti.oy, s_xy[threadIdx.x], s_con[threadIdx.x], s_rgb[threadIdx.x]);
+            if (j < r.y) {
+                stage(proj, ids[j], ti.ox, ti.oy, s_xy[threadIdx.x], s_con[threadIdx.x], s_rgb[threadIdx.x]);
+                s_mask[threadIdx.x] = warp_mask<TW, TH>(s_xy[threadIdx.x], ti.tbx, ti.tby);
+            }
             __syncthreads();
             const int nb = min(BS, r.y - b0);
             for (int k = 0; k < nb && !done; ++k) {
-                float alpha, G = 0.f, dx, dy;
+                if (!(s_mask[k] & wbit)) continue;
+                float alpha, G = 0.f, dx, dy, u;
                 bool clamped;
-                const bool use = eval_alpha(s_xy[k], s_con[k], ti.pcx, ti.pcy, L.pixel_gate, L.alpha_min,
-                                            L.alpha_max, alpha, G, dx, dy, clamped);
+                const bool use = eval_alpha(s_xy[k], s_con[k], ti.pcx, ti.pcy, L.alpha_min, L.alpha_max, alpha, G,
+                                            dx, dy, u, clamped);
                 n_eval += G > 0.f || use;
                 if (!use) continue;
                 const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
@@ -155,13 +217,13 @@ __global__ void __launch_bounds__(TW * TH) k_render_fwd(const Launch L, const fl
         if (ti.inside) {
             const ViewDesc &vd = L.v[ti.view];
             const long long hw = (long long)vd.W * vd.H;
-            float *img = image + vd.pix_base + (long long)ti.py * vd.W + ti.px;
+            const long long o = vd.pix_base + (long long)ti.py * vd.W + ti.px;
             if (abort) {
-                img[0] = 0.f; img[hw] = 0.f; img[2 * hw] = 0.f;
+                image[o] = 0.f; image[o + hw] = 0.f; image[o + 2 * hw] = 0.f;
             } else {
-                img[0] = __fmaf_rn(T, L.bg[0], C0);
-                img[hw] = __fmaf_rn(T, L.bg[1], C1);
-                img[2 * hw] = __fmaf_rn(T, L.bg[2], C2);
+                image[o] = __fmaf_rn(T, L.bg[0], C0);
+                image[o + hw] = __fmaf_rn(T, L.bg[1], C1);
+                image[o + 2 * hw] = __fmaf_rn(T, L.bg[2], C2);
             }
         }
     }
@@ -178,12 +240,14 @@ __global__ void __launch_bounds__(TW * TH) k_render_bwd(const Launch L, const fl
                                                         float4 *__restrict__ grad2d) {
     constexpr int BS = TW * TH;
     __shared__ float4 s_xy[BS], s_con[BS], s_rgb[BS];
-    __shared__ float s_g[9][BS];
+    __shared__ unsigned int s_mask[BS];
+    __shared__ float s_g[BS][9];   // per staged Gaussian: summed gradient (odd stride: no bank conflicts)
     __shared__ int s_item;
+    const unsigned int wbit = 1u << (threadIdx.x >> 5);
     if (counters[CNT_ABORT]) return;
     const int lane = threadIdx.x & 31;
-    for (int k = threadIdx.x; k < BS; k += BS)
-        for (int c = 0; c < 9; ++c) s_g[c][k] = 0.f;
+    const int red_idx = ((lane & 16) ? 8 : 0) + ((lane & 8) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
+    for (int c = 0; c < 9; ++c) s_g[threadIdx.x][c] = 0.f;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counters + CNT_Q_BWD, 1);
         __syncthreads();
@@ -207,22 +271,26 @@ __global__ void __launch_bounds__(TW * TH) k_render_bwd(const Launch L, const fl
         for (int b0 = r.x; b0 < r.y; b0 += BS) {
             if (__syncthreads_count(done) == BS) break;
             const int j = b0 + threadIdx.x;
-            if (j < r.y) stage(proj, ids[j], ti.ox, ti.oy, s_xy[threadIdx.x], s_con[threadIdx.x], s_rgb[threadIdx.x]);
+            if (j < r.y) {
+                stage(proj, ids[j], ti.ox, ti.oy, s_xy[threadIdx.x], s_con[threadIdx.x], s_rgb[threadIdx.x]);
+                s_mask[threadIdx.x] = warp_mask<TW, TH>(s_xy[threadIdx.x], ti.tbx, ti.tby);
+            }
             __syncthreads();
             const int nb = min(BS, r.y - b0);
             for (int k = 0; k < nb; ++k) {
-                // gradient of this pixel w.r.t. (x, y, A, B, C, o, r, g, b) of Gaussian k
-                float gv[9];
+                if (!(s_mask[k] & wbit)) continue;   // warp-uniform: no lane of this warp can be hit
+                // gradient of this pixel w.r.t. (x, y, a, b, c, o, r, g, b) of Gaussian k
+                float gv[16];
 #pragma unroll
-                for (int c = 0; c < 9; ++c) gv[c] = 0.f;
+                for (int c = 0; c < 16; ++c) gv[c] = 0.f;
                 bool hit = false;
                 if (!done) {
-                    float alpha, G, dx, dy;
+                    float alpha, G, dx, dy, u;
                     bool clamped;
                     const float4 xy = s_xy[k], con = s_con[k];
                     G = 0.f;
-                    const bool use = eval_alpha(xy, con, ti.pcx, ti.pcy, L.pixel_gate, L.alpha_min, L.alpha_max,
-                                                alpha, G, dx, dy, clamped);
+                    const bool use = eval_alpha(xy, con, ti.pcx, ti.pcy, L.alpha_min, L.alpha_max, alpha, G, dx,
+                                                dy, u, clamped);
                     n_eval += G > 0.f || use;
                     if (use) {
                         const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
@@ -239,52 +307,58 @@ __global__ void __launch_bounds__(TW * TH) k_render_bwd(const Launch L, const fl
                             gv[6] = w * g0;
                             gv[7] = w * g1;
                             gv[8] = w * g2;
+                            // colour behind this Gaussian: image - running sum
                             const float S0 = img0 - C0, S1 = img1 - C1, S2 = img2 - C2;
                             const float dL_dalpha =
                                 T * (c.x * g0 + c.y * g1 + c.z * g2) - (S0 * g0 + S1 * g1 + S2 * g2) / (1.f - alpha);
                             if (!clamped) {
-                                // alpha = o G, G = exp(power), power = -1/2 (A dx^2 + 2B dx dy + C dy^2),
-                                // dx = pixel - mean: d power / d mean = (A dx + B dy, B dx + C dy)
+                                // alpha = o G, G = exp(power), power = -1/2 d^T Q d with Q the conic
+                                // (inverse of the covariance Sigma' = (a, b, c)), d = pixel - mean.
+                                // With v = Q d = (A u, A beta u + D dy) from the staged form,
+                                // d power / d mean = v and d power / d Sigma' = v v^T / 2, i.e.
+                                // (v0^2/2, v0 v1, v1^2/2) for (a, b, c): summing these well-scaled
+                                // terms over pixels avoids the ill-conditioned conic -> covariance
+                                // conversion of summed conic gradients for elongated Gaussians.
                                 gv[5] = dL_dalpha * G;
                                 const float dp = dL_dalpha * alpha;
-                                const float A = con.x * (-2.f * LN2), B = con.y * (-LN2), Cc = con.z * (-2.f * LN2);
-                                gv[0] = dp * (A * dx + B * dy);
-                                gv[1] = dp * (B * dx + Cc * dy);
-                                gv[2] = -0.5f * dp * dx * dx;
-                                gv[3] = -dp * dx * dy;
-                                gv[4] = -0.5f * dp * dy * dy;
+                                const float A = con.x * (-2.f * LN2), D = con.z * (-2.f * LN2);
+                                const float v0 = A * u;
+                                const float v1 = v0 * con.y + D * dy;
+                                const float dv0 = dp * v0, dv1 = dp * v1;
+                                gv[0] = dv0;
+                                gv[1] = dv1;
+                                gv[2] = 0.5f * dv0 * v0;
+                                gv[3] = dv0 * v1;
+                                gv[4] = 0.5f * dv1 * v1;
                             }
                             T = Tn;
                         }
                     }
                 }
                 if (__any_sync(0xffffffffu, hit)) {
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) gv[c] = warp_sum(gv[c]);
-                    if (lane == 0) {
-#pragma unroll
-                        for (int c = 0; c < 9; ++c) atomicAdd(&s_g[c][k], gv[c]);
-                    }
+                    const float sum = warp_reduce_scatter16(gv, lane);
+                    if (!(lane & 1) && red_idx < 9) atomicAdd(&s_g[k][red_idx], sum);
                 }
             }
             __syncthreads();
             // flush this batch's per-Gaussian sums
             const int k = threadIdx.x;
             if (k < nb) {
-                const float a0 = s_g[0][k], a1 = s_g[1][k], a2 = s_g[2][k], a3 = s_g[3][k], a4 = s_g[4][k];
-                const float a5 = s_g[5][k], a6 = s_g[6][k], a7 = s_g[7][k], a8 = s_g[8][k];
+                const float a0 = s_g[k][0], a1 = s_g[k][1], a2 = s_g[k][2], a3 = s_g[k][3], a4 = s_g[k][4];
+                const float a5 = s_g[k][5], a6 = s_g[k][6], a7 = s_g[k][7], a8 = s_g[k][8];
                 if (a0 != 0.f || a1 != 0.f || a2 != 0.f || a3 != 0.f || a4 != 0.f || a5 != 0.f || a6 != 0.f ||
                     a7 != 0.f || a8 != 0.f) {
-                    const unsigned int slot = __float_as_uint(s_con[k].w);
+                    const unsigned int slot = __float_as_uint(s_rgb[k].w);
                     float4 *dst = grad2d + 3ull * slot;
                     atomicAdd(dst, make_float4(a0, a1, a2, a3));
                     atomicAdd(dst + 1, make_float4(a4, a5, a6, a7));
                     atomicAdd(dst + 2, make_float4(a8, 0.f, 0.f, 0.f));
                 }
 #pragma unroll
-                for (int c = 0; c < 9; ++c) s_g[c][k] = 0.f;
+                for (int c = 0; c < 9; ++c) s_g[k][c] = 0.f;
             }
         }
+        count_pairs(counters, 12, n_eval, n_comp);
     }
 }
 

@@ -63,6 +63,19 @@ def upstream(views, ref, seed=1, masks=None):
     return ups
 
 
+def conic_to_cov_grads(g2d, conic):
+    """Oracle 2D gradients w.r.t. (x, y, A, B, C, o, r, g, b) with the conic
+    (A, B, C) -> the same w.r.t. the covariance (a, b, c) it inverts:
+    G_cov = -Q G_Q Q with G_Q = [[gA, gB/2], [gB/2, gC]] (FP64, exact map)."""
+    out = np.array(g2d, np.float64, copy=True)
+    A, B, C = conic[:, 0], conic[:, 1], conic[:, 2]
+    Q = np.stack([np.stack([A, B], -1), np.stack([B, C], -1)], -2)
+    G = np.stack([np.stack([g2d[:, 2], 0.5 * g2d[:, 3]], -1), np.stack([0.5 * g2d[:, 3], g2d[:, 4]], -1)], -2)
+    Gc = -Q @ G @ Q
+    out[:, 2], out[:, 3], out[:, 4] = Gc[:, 0, 0], 2 * Gc[:, 0, 1], Gc[:, 1, 1]
+    return out
+
+
 def check_grad(g, ref, what, rel_norm=1e-3, rel_elem=1e-3, abs_frac=1e-5):
     """Gradient tolerance: ||g - g*|| <= 1e-3 ||g*|| and elementwise
     |g - g*| <= 1e-3 |g*| + 1e-5 max|g*|."""

@@ -6,7 +6,8 @@ import torch
 from oracle import oracle as O
 from paper_2509_25191_gb300 import _lib, synth
 from paper_2509_25191_gb300.autograd import Rasterizer
-from tests.gpu_util import (check_grad, gpu_forward, image_errors, oracle_forward, split, upstream)
+from tests.gpu_util import (check_grad, conic_to_cov_grads, gpu_forward, image_errors, oracle_forward, split,
+                            upstream)
 
 pytestmark = pytest.mark.gpu
 
@@ -113,15 +114,18 @@ def test_projection_parity(case):
         y = rec[:, 1].astype(np.float64) + rec[:, 3]
         assert np.abs(x - ref["xy"][:, 0])[both].max() < 2e-5 * max(1.0, np.abs(ref["xy"][both]).max())
         assert np.abs(y - ref["xy"][:, 1])[both].max() < 2e-5 * max(1.0, np.abs(ref["xy"][both]).max())
-        con = rec[:, 4:7][both]
-        rc = ref["conic"][both]
+        cov = rec[:, 4:7][both]
+        rc = ref["cov"][both]
         scale = np.abs(rc).max(axis=1, keepdims=True)
-        assert (np.abs(con - rc) / scale).max() < 1e-4
+        assert (np.abs(cov - rc) / scale).max() < 1e-5
         assert np.abs(rec[:, 7][both] - ref["opac"][both]).max() < 1e-6
         assert np.abs(rec[:, 8:11][both] - ref["rgb"][both]).max() < 1e-5
         ok_r = both & ~amb
         assert np.array_equal(rad[ok_r], ref["radius"][ok_r].astype(np.float32))
         assert np.abs(rec[:, 12][both] / ref["depth"][both] - 1).max() < 1e-6
+        # reach extents: the float32 value is enlarged by 2^-14 unless clipped to the radius
+        ext, rext = rec[:, 14:16][ok_r], ref["ext"][ok_r]
+        assert (ext >= rext * (1 - 1e-6)).all() and (ext <= rext * (1 + 2e-4) + 1e-5).all()
 
 
 # ---------------------------------------------------------------------------
@@ -137,6 +141,7 @@ def _records_from_oracle(sc, vw):
         r[:, 1] = ref["xy"][:, 1].astype(np.float32)
         r[:, 11] = ref["radius"].astype(np.float32)
         r[:, 12] = ref["depth"].astype(np.float32)
+        r[:, 14:16] = ref["ext"].astype(np.float32)
         recs.append((ref, r))
     return recs
 
@@ -153,7 +158,7 @@ def test_binning_bit_exact(case, tile):
     refs = []
     for v, (ref, r) in enumerate(recs):
         W, H = int(vw.width[v]), int(vw.height[v])
-        refs.append(O.bin_view(r[:, 0], r[:, 1], ref["radius"], r[:, 12], W, H, *tile))
+        refs.append(O.bin_view(r[:, 0], r[:, 1], ref["radius"], r[:, 12], W, H, *tile, ext=r[:, 14:16]))
         n_inst += len(refs[-1][2])
     bins = _lib.Bins(views.num_tiles(cfg), n_inst)
     status = _lib.new_status()
@@ -187,13 +192,15 @@ def test_binning_large_tiles_bit_exact():
     r[:, 1] = rng.uniform(0, 48, n)
     r[:, 11] = rng.integers(1, 3, n)
     r[:, 12] = rng.uniform(1.0, 9.0, n).astype(np.float32)
+    r[:, 14] = r[:, 11] * rng.uniform(0.3, 1.0, n)
+    r[:, 15] = r[:, 11]
     r[:40000, 0] = rng.uniform(17, 30, 40000)   # one very crowded tile column
     r[:40000, 1] = rng.uniform(17, 30, 40000)
     vw = synth.Views(np.zeros((1, 12), np.float32), np.ones((1, 4), np.float32), np.array([W], np.int32),
                      np.array([H], np.int32), np.array([0]), np.array([n]))
     views = _lib.Views.from_synth(vw)
     cfg = _lib.config(tile=(16, 16))
-    rr, kk, ii = O.bin_view(r[:, 0], r[:, 1], r[:, 11].astype(np.int32), r[:, 12], W, H, 16, 16)
+    rr, kk, ii = O.bin_view(r[:, 0], r[:, 1], r[:, 11].astype(np.int32), r[:, 12], W, H, 16, 16, ext=r[:, 14:16])
     assert (rr[:, 1] - rr[:, 0]).max() > 16384
     bins = _lib.Bins(views.num_tiles(cfg), len(ii))
     _lib.gs_bin_sort(views, cfg, torch.as_tensor(r).cuda(), bins, _lib.new_status())
@@ -286,7 +293,7 @@ def test_backward_parity(case):
     for v in range(vw.n):
         sb = views.slot_base(v)
         got = G2[sb: sb + int(vw.gauss_count[v])][:, :9]
-        check_grad(got, g2ds[v], f"grad2d view {v}")
+        check_grad(got, conic_to_cov_grads(g2ds[v], ref[v]["proj"]["conic"]), f"grad2d view {v}")
     for name in ["means", "log_scales", "quats", "opacity_logits", "sh"]:
         check_grad(getattr(grads, name).cpu().numpy(), rg[name], name)
     check_grad(dvm.cpu().numpy(), dRt, "dL/d(R,t)")

@@ -133,6 +133,29 @@ def test_projection_matches_monte_carlo_moments(rotated_camera):
     assert abs(u.mean() - p["xy"][0, 0]) < 0.02 and abs(v.mean() - p["xy"][0, 1]) < 0.02
 
 
+def test_opacity_aware_extent_bounds_the_alpha_region():
+    """Every pixel that gets alpha >= alpha_min lies within the tile extents,
+    and the extents are tight: the ellipse o G = alpha_min touches them."""
+    sc, vw = _small(n=200, seed=9)
+    p = O.project_view(sc, vw, 0)
+    ok = p["radius"] > 0
+    for g in np.nonzero(ok)[0][:50]:
+        A, B, C = p["conic"][g]
+        k = 2 * math.log(p["opac"][g] * 255.0)
+        # extreme x of the ellipse d^T Q d = k: d = t Q^-1 e_x scaled to the boundary
+        cov = np.linalg.inv(np.array([[A, B], [B, C]]))
+        ex_true = math.sqrt(k * cov[0, 0])
+        assert abs(min(p["radius"][g], ex_true) - p["ext"][g, 0]) < 1e-9 * max(1, ex_true)
+        d = cov[:, 0] * math.sqrt(k / cov[0, 0])           # boundary point with the largest |dx|
+        alpha = p["opac"][g] * math.exp(-0.5 * d @ np.array([[A, B], [B, C]]) @ d)
+        assert abs(alpha - 1 / 255) < 1e-9
+
+
+def test_transparent_gaussians_are_culled():
+    sc = make_scene([[0, 0, 2.0]], 0.05, 0.5 / 255, [[0.5] * 3])
+    assert O.project_view(sc, pinhole_views(32, 32, 40.0), 0)["radius"][0] == 0
+
+
 def test_near_plane_and_nonfinite_culled():
     sc = make_scene([[0, 0, 0.19], [0, 0, 0.21], [0, 0, 3.0]], 0.01, 0.5, [[0.5] * 3] * 3)
     sc.means[2, 0] = np.nan
@@ -152,11 +175,12 @@ def test_binning_matches_interval_bruteforce():
     r = rng.integers(0, 25, n).astype(np.int32)
     z = rng.uniform(1, 5, n).astype(np.float32)
     z[5] = z[6]            # one exact depth tie: broken by index
+    ext = (r[:, None] * rng.uniform(0.2, 1.0, (n, 2))).astype(np.float32)
     for TW, TH in [(16, 16), (8, 8), (32, 16)]:
-        ranges, keys, ids = O.bin_view(x, y, r, z, W, H, TW, TH)
+        ranges, keys, ids = O.bin_view(x, y, r, z, W, H, TW, TH, ext)
         Gx, Gy = O.tile_grid(W, H, TW, TH)
-        lo_x, hi_x = x - r.astype(np.float32), x + r.astype(np.float32)   # float32 arithmetic
-        lo_y, hi_y = y - r.astype(np.float32), y + r.astype(np.float32)
+        lo_x, hi_x = x - ext[:, 0], x + ext[:, 0]   # float32 arithmetic
+        lo_y, hi_y = y - ext[:, 1], y + ext[:, 1]
         for ty in range(Gy):
             for tx in range(Gx):
                 member = (r > 0) & (np.float32(tx * TW) <= hi_x) & (np.float32((tx + 1) * TW) > lo_x) & \
@@ -228,9 +252,9 @@ def _small(n=300, W=40, H=36, seed=2):
 
 
 def _bruteforce_image(proj, W, H, TW, TH, prm):
-    """Per pixel, all listed Gaussians (tile rectangle by float32 interval
-    intersection) passing the square gate, sorted by (float32 depth, index),
-    composited directly."""
+    """Per pixel, all listed Gaussians (square tile rectangle by float32
+    interval intersection) passing the square gate, sorted by (float32 depth,
+    index), composited directly."""
     n = proj["xy"].shape[0]
     xf = proj["xy"][:, 0].astype(np.float32)
     yf = proj["xy"][:, 1].astype(np.float32)
@@ -273,10 +297,14 @@ def test_oracle_render_equals_bruteforce():
     prm = O.Params(bg=(0.2, 0.1, 0.05))
     proj = O.project_view(sc, vw, 0, prm)
     for TW, TH in [(16, 16), (8, 8)]:
-        bins = O.bin_view(proj["xy"][:, 0], proj["xy"][:, 1], proj["radius"], proj["depth"], 40, 36, TW, TH)
+        bins = O.bin_view(proj["xy"][:, 0], proj["xy"][:, 1], proj["radius"], proj["depth"], 40, 36, TW, TH)   # square rectangles
         out = O.render_view(proj, 40, 36, TW, TH, prm, bins)
         ref = _bruteforce_image(proj, 40, 36, TW, TH, prm)
         assert np.abs(out["image"] - ref).max() < 1e-12
+        # lists bounded by the opacity-aware extents give the same image
+        assert (proj["ext"][proj["radius"] > 0] < proj["radius"][proj["radius"] > 0, None] - 0.5).any()
+        tight = O.forward(sc, vw, TW, TH, prm)[0]["image"]
+        assert np.abs(tight - ref).max() < 1e-12
 
 
 def test_permutation_invariance():
