@@ -54,7 +54,8 @@ typedef enum gs_status {
     GS_ERR_CUDA = 2,         /* a CUDA call or launch failed */
     GS_ERR_CAPACITY = 3,     /* device: instance capacity too small; detail = instances needed */
     GS_ERR_UNSUPPORTED = 4,  /* configuration not compiled in (tile shape, SH degree) */
-    GS_ERR_OVERFLOW = 5      /* device: more than 2^31-1 tile instances */
+    GS_ERR_OVERFLOW = 5,     /* device: more than 2^31-1 tile instances */
+    GS_ERR_TOO_LARGE = 6     /* exceeds the fixed scratch of gs_project_bwd_noalloc */
 } gs_status;
 
 /* Rasterizer settings. gs_config_default() fills the defaults in brackets. */
@@ -214,6 +215,36 @@ int gs_pose_grad(const gs_views *views, const float *pose_partials, int n_blocks
  * dL_dimage DEVICE [count] = sign(image - target) / count. */
 int gs_l1_loss(const float *image, const float *target, int64_t count, float *loss,
                float *dL_dimage, void *stream);
+
+/* Allocation-free variant of gs_project_bwd followed by gs_pose_grad (the
+ * paper has no counterpart: this exists for callers, not for the method).
+ *
+ * Some callers cannot hand the library a scratch buffer: code that runs
+ * under a memory planner or inside another runtime that owns every device
+ * allocation (a plugin host, an inference server or graph executor that
+ * forbids cudaMalloc after start-up) has no way to allocate the per-block
+ * pose partials that gs_project_bwd needs. This entry point takes the same
+ * inputs and the same parameter-gradient outputs as gs_project_bwd, and
+ * writes the reduced pose gradients like gs_pose_grad (dL_dviewmat [V,12],
+ * dL_dtwist [V,6] or NULL); grads->grad2d and grads->pose_partials are
+ * ignored. It calls no cudaMalloc/cudaFree and no allocating library
+ * routine.
+ *
+ * Its scratch is a file-scope static device array of GS_NOALLOC_POSE_FLOATS
+ * floats (3 MB) that every GPU which loads the library keeps until the
+ * process exits. The pose partials of one call need V * gs_pose_blocks(n) *
+ * 12 floats; a call beyond that returns GS_ERR_TOO_LARGE before enqueuing
+ * anything. Every call shares the one array and leaves its contents behind
+ * (each call overwrites all the partials it reads, so nothing needs
+ * clearing): calls that overlap on the GPU (other streams, other host
+ * threads on the same device) race and must be serialised by the caller.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture. */
+#define GS_NOALLOC_MAX_BLOCKS 1024
+#define GS_NOALLOC_POSE_FLOATS (GS_MAX_VIEWS * GS_NOALLOC_MAX_BLOCKS * 12)
+int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *views, const gs_config *cfg, const float *proj,
+                           const float *grad2d, const gs_grads *grads, int want_gaussian_grads,
+                           float *dL_dviewmat, float *dL_dtwist, int32_t *status, void *stream);
 
 const char *gs_error_string(int code);
 int gs_version(void);

@@ -15,7 +15,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgsplat_gb300.so")
 
-GS_OK, GS_ERR_ARG, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_UNSUPPORTED, GS_ERR_OVERFLOW = range(6)
+GS_OK, GS_ERR_ARG, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_UNSUPPORTED, GS_ERR_OVERFLOW, GS_ERR_TOO_LARGE = range(7)
 GS_MAX_VIEWS = 64
 GS_RECORD_FLOATS = 16
 GS_GRAD2D_FLOATS = 12
@@ -23,7 +23,8 @@ GS_NUM_COUNTERS = 16
 
 EXPORTED = ["gs_config_default", "gs_num_slots", "gs_slot_base", "gs_num_tiles", "gs_tile_base",
             "gs_num_image_floats", "gs_pixel_base", "gs_pose_blocks", "gs_project", "gs_bin_sort",
-            "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version"]
+            "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version",
+            "gs_project_bwd_noalloc"]
 
 
 class GsError(RuntimeError):
@@ -278,6 +279,18 @@ def gs_project_bwd(g: Gaussians, views: Views, cfg: gs_config, proj, grads: Grad
     _check(load().gs_project_bwd(ctypes.byref(g.c()), ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj),
                                  _ptr(grads.grad2d), ctypes.byref(grads.c()), int(bool(want_gaussian_grads)),
                                  _ptr(status), _stream(stream)), "gs_project_bwd")
+
+
+def gs_project_bwd_noalloc(g: Gaussians, views: Views, cfg: gs_config, proj, grads: Grads, dL_dviewmat,
+                           dL_dtwist=None, want_gaussian_grads=True, status=None, stream=None):
+    """gs_project_bwd + gs_pose_grad without caller scratch: the pose partials
+    live in the library's static device array (for callers that cannot
+    allocate device memory). grads.grad2d is the input; grads.pose_partials
+    is not used."""
+    _check(load().gs_project_bwd_noalloc(ctypes.byref(g.c()), ctypes.byref(views.c()), ctypes.byref(cfg),
+                                         _ptr(proj), _ptr(grads.grad2d), ctypes.byref(grads.c()),
+                                         int(bool(want_gaussian_grads)), _ptr(dL_dviewmat), _ptr(dL_dtwist),
+                                         _ptr(status), _stream(stream)), "gs_project_bwd_noalloc")
 
 
 def pair_counts(bins: Bins):

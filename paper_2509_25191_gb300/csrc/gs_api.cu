@@ -295,6 +295,7 @@ const char *gs_error_string(int code) {
     case GS_ERR_CAPACITY: return "instance capacity exceeded";
     case GS_ERR_UNSUPPORTED: return "unsupported configuration";
     case GS_ERR_OVERFLOW: return "more than 2^31-1 tile instances";
+    case GS_ERR_TOO_LARGE: return "pose partials exceed the fixed scratch of the allocation-free entry point";
     default: return "unknown status";
     }
 }
@@ -302,3 +303,72 @@ const char *gs_error_string(int code) {
 int gs_version(void) { return 1; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free projection backward (gs_project_bwd_noalloc): the pose
+// partials live in this file-scope device array instead of a caller buffer.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) float g_noalloc_pose[GS_NOALLOC_POSE_FLOATS];
+
+namespace {
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[64];   // device address of g_noalloc_pose, per device
+
+// Host code cannot use the array's name as a device address; look the
+// address up once per device, with that device current.
+int noalloc_scratch(float **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_pose) != cudaSuccess || !p) return GS_ERR_CUDA;
+        g_noalloc_ptr[dev] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return GS_OK;
+}
+}  // namespace
+
+extern "C" int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg,
+                                      const float *proj, const float *grad2d, const gs_grads *grads,
+                                      int want_gaussian_grads, float *dL_dviewmat, float *dL_dtwist,
+                                      int32_t *status, void *stream) {
+    (void)status;
+    Launch L;
+    int rc = build_launch(vw, cfg, L);
+    if (rc) return rc;
+    if ((rc = check_gaussians(g, vw))) return rc;
+    if (!proj || !grad2d || !grads || !dL_dviewmat || !vw->viewmats || !vw->intrinsics) return GS_ERR_ARG;
+    if (want_gaussian_grads && g->n > 0 &&
+        (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh))
+        return GS_ERR_ARG;
+    if (!aligned16(grad2d) || (want_gaussian_grads && g->n > 0 && !aligned16(grads->quats))) return GS_ERR_ARG;
+    const int nblk = pose_blocks(g->n);
+    if ((long long)L.n_views * nblk * 12 > (long long)GS_NOALLOC_POSE_FLOATS) return GS_ERR_TOO_LARGE;
+    float *scratch = nullptr;
+    if ((rc = noalloc_scratch(&scratch))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (want_gaussian_grads) {
+        long long covered = 0;
+        for (int a = 0; a < L.n_scenes; ++a) covered += L.s[a].g_count;
+        if (covered != g->n && g->n > 0) {
+            const int K = (g->sh_degree + 1) * (g->sh_degree + 1);
+            const size_t n = (size_t)g->n;
+            if (cudaMemsetAsync(grads->means, 0, sizeof(float) * 3 * n, st) ||
+                cudaMemsetAsync(grads->log_scales, 0, sizeof(float) * 3 * n, st) ||
+                cudaMemsetAsync(grads->quats, 0, sizeof(float) * 4 * n, st) ||
+                cudaMemsetAsync(grads->opacity_logits, 0, sizeof(float) * n, st) ||
+                cudaMemsetAsync(grads->sh, 0, sizeof(float) * 3 * K * n, st))
+                return GS_ERR_CUDA;
+        }
+    }
+    gs_grads out = *grads;
+    out.pose_partials = scratch;   // every partial the reduction reads is written first
+    rc = launch_project_bwd(L, g->sh_degree, g, vw->viewmats, vw->intrinsics, proj, grad2d, &out,
+                            want_gaussian_grads, nblk, st);
+    if (rc) return rc;
+    return launch_pose_reduce(L.n_views, scratch, nblk, vw->viewmats, dL_dviewmat, dL_dtwist, st);
+}
