@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--ref-fraction", type=float, default=1.0 / 16.0,
                     help="pixel fraction of each reference-arm step")
     return ap.parse_args()
@@ -152,7 +153,7 @@ def run_native(args, rank, world, local_rank):
     import torch.distributed as dist
 
     from paper_2509_25191_gb300 import _lib, build
-    from paper_2509_25191_gb300.autograd import Rasterizer
+    from paper_2509_25191_gb300.step import GraphStep
 
     build.build()
     torch.cuda.set_device(local_rank)
@@ -165,42 +166,10 @@ def run_native(args, rank, world, local_rank):
     rng = np.random.default_rng(1234)
     target = torch.as_tensor(rng.uniform(0, 1, views.num_image_floats()).astype(np.float32), device=dev)
 
-    rast = Rasterizer(tile=tile)
-    # eager step to size the instance capacity (the one host readback)
-    image, proj = rast.forward(g, views)
-    torch.cuda.synchronize()
-    n_inst = rast.last_instances
-    rast.reserve(views, int(n_inst * 1.25) + 4096, dev)
-    proj = torch.empty_like(proj)
-    image = torch.empty(views.num_image_floats(), device=dev)
-    dimg = torch.empty_like(image)
-    loss = torch.empty(1, device=dev)
-    grads = rast.grads_buffers(g, views)
-    dvm = torch.empty(views.n, 12, device=dev)
-    dtw = torch.empty(views.n, 6, device=dev)
-    cfg, bins, status = rast.cfg, rast.bins, rast.status
-
-    def step(events=None):
-        rec = (lambda: events.append(torch.cuda.Event(enable_timing=True)) or events[-1].record()) \
-            if events is not None else (lambda: None)
-        rec()
-        _lib.gs_project(g, views, cfg, proj, status)
-        rec()
-        _lib.gs_bin_sort(views, cfg, proj, bins, status)
-        rec()
-        _lib.gs_render_fwd(views, cfg, proj, bins, image, status)
-        rec()
-        _lib.gs_l1_loss(image, target, loss, dimg)
-        rec()
-        _lib.gs_rasterize_bwd(views, cfg, proj, bins, image, dimg, grads.grad2d, status)
-        rec()
-        _lib.gs_project_bwd(g, views, cfg, proj, grads, True, status)
-        rec()
-        _lib.gs_pose_grad(views, grads.pose_partials, grads.n_blocks, dvm, dtw)
-        rec()
-
-    kernels_per_step = 1 + 5 + 1 + 1 + 1 + 1 + 1   # project, bin(5), fwd, l1, rbwd, pbwd, pose
-    step()
+    step = GraphStep(g, views, target, tile=tile)
+    rast, cfg, bins = step.rast, step.cfg, step.bins
+    image, dvm, loss = step.image, step.dviewmat, step.loss
+    kernels_per_step = GraphStep.KERNELS_PER_STEP
     torch.cuda.synchronize()
     rast.check_status()
 
@@ -211,24 +180,14 @@ def run_native(args, rank, world, local_rank):
     reps = 10
     for _ in range(reps):
         ev = []
-        step(ev)
+        step.run(ev)
         torch.cuda.synchronize()
         acc += [ev[i].elapsed_time(ev[i + 1]) for i in range(len(names))]
     stage_ms = acc / reps
     pairs = _lib.pair_counts(bins)
     n_inst = int(bins.counters[0].item())
 
-    # capture the whole step in a CUDA graph
-    s = torch.cuda.Stream(device=dev)
-    s.wait_stream(torch.cuda.current_stream())
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(s):
-        step()
-        torch.cuda.synchronize()
-        with torch.cuda.graph(graph, stream=s):
-            step()
-    torch.cuda.synchronize()
-
+    graph = step.graph
     for _ in range(max(3, args.warmup)):
         graph.replay()
     torch.cuda.synchronize()
@@ -316,6 +275,7 @@ def run_native(args, rank, world, local_rank):
         hbm = peaks["hbm_gbs"]
         roof = {"kernel": names[top], "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                 "traffic": None}
+    batched = None if args.no_batched else batched_vs_plain(dev, tile)
     step_bytes = algorithmic_bytes(g.n, g.sh_degree, views.num_slots(), n_inst, P, views.num_tiles(cfg))
     hbm_frac_step = step_bytes / (ms * 1e-3) / (peaks["hbm_gbs"] * 1e9)
 
@@ -332,10 +292,51 @@ def run_native(args, rank, world, local_rank):
                               "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src},
         "stages_ms": {n: round(float(t), 4) for n, t in zip(names, stage_ms)},
         "clocks": clocks,
+        "batched_vs_plain": batched,
         "e2e": e2e,
         "gpu_launches": kernels_per_step * args.steps,
     }
     return out, sc, vw
+
+
+def batched_vs_plain(dev, tile, steps=20, plain_steps=5):
+    """16 views 979x546 of one 500K-Gaussian clustered SH3 scene on a circular
+    orbit: the whole batch in one captured step versus the same work as 16
+    uncaptured single-view calls (each with its instance-count readback)."""
+    import torch
+
+    from paper_2509_25191_gb300 import _lib, synth
+    from paper_2509_25191_gb300.step import GraphStep, PlainStep
+    sc, vw = synth.orbit_views(0, 500_000, 16, 979, 546)
+    g = _lib.Gaussians.from_scene(sc, dev)
+    views = _lib.Views.from_synth(vw, dev)
+    rng = np.random.default_rng(99)
+    target = torch.as_tensor(rng.uniform(0, 1, views.num_image_floats()).astype(np.float32), device=dev)
+    gs = GraphStep(g, views, target, tile=tile)
+    ps = PlainStep(g, views, target, tile=tile)
+    for _ in range(3):
+        gs.replay()
+        ps.run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        gs.replay()
+    b.record()
+    torch.cuda.synchronize()
+    tb = a.elapsed_time(b) / steps
+    gs.rast.check_status()
+    a.record()
+    for _ in range(plain_steps):
+        ps.run()
+    b.record()
+    torch.cuda.synchronize()
+    tp = a.elapsed_time(b) / plain_steps
+    px = views.pixels
+    return {"workload": "16 views 979x546 on a radius-5 orbit, 500K clustered SH3 Gaussians (seed 0), "
+                        "fwd+L1+bwd+pose", "batched_ms": round(tb, 4), "plain_ms": round(tp, 4),
+            "batched_mpix_s": round(px / tb / 1e3, 2), "plain_mpix_s": round(px / tp / 1e3, 2),
+            "ratio": round(tp / tb, 3), "steps": steps, "plain_steps": plain_steps}
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,128 @@
+"""One training step of the rasterizer, captured as a CUDA graph.
+
+A step over a batch of views is: gs_project -> gs_bin_sort -> gs_render_fwd
+-> gs_l1_loss (against the step's target images) -> gs_rasterize_bwd ->
+gs_project_bwd -> gs_pose_grad, i.e. the photometric supervision of
+Section 3.1 with gradients to every Gaussian parameter and to every view's
+pose (Section 3.4). All buffers are allocated once; the tile-instance
+capacity is sized from one uncaptured forward (with headroom) and the step is
+captured into a CUDA graph, so replaying it launches every kernel with no
+host synchronisation. New inputs (Gaussian parameters, view matrices,
+targets) are copied into the captured tensors before a replay; an instance
+count above the capacity is reported in the device status word and
+``GraphStep.check()`` re-plans.
+
+``PlainStep`` is the uncaptured reference path: the same calls made view by
+view, each with the host readback of the instance count that an uncaptured
+call needs.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import Gaussians, Grads, Views
+from .autograd import Rasterizer
+
+
+class GraphStep:
+    KERNELS_PER_STEP = 11   # project 1, bin/sort 5, render 1, loss 1, raster bwd 1, projection bwd 1, pose 1
+
+    def __init__(self, g: Gaussians, views: Views, target, tile=(16, 16), headroom=1.25, capture=True,
+                 want_gaussian_grads=True):
+        self.g, self.views, self.target = g, views, target
+        self.want = want_gaussian_grads
+        dev = g.means.device
+        self.rast = Rasterizer(tile=tile)
+        _, _ = self.rast.forward(g, views)
+        torch.cuda.synchronize(dev)
+        self.capacity = int(self.rast.last_instances * headroom) + 4096
+        self.rast.reserve(views, self.capacity, dev)
+        self.cfg, self.bins, self.status = self.rast.cfg, self.rast.bins, self.rast.status
+        self.proj = torch.empty(max(1, views.num_slots()), _lib.GS_RECORD_FLOATS, device=dev)
+        self.image = torch.empty(views.num_image_floats(), device=dev)
+        self.dimg = torch.empty_like(self.image)
+        self.loss = torch.empty(1, device=dev)
+        self.grads = Grads(g.n, g.sh_degree, views.num_slots(), views.n, dev, want_gaussian_grads)
+        self.dviewmat = torch.empty(views.n, 12, device=dev)
+        self.dtwist = torch.empty(views.n, 6, device=dev)
+        self.graph = None
+        if capture:
+            self.capture()
+
+    def run(self, events=None):
+        """Enqueue the step on the current stream (optionally recording an
+        event before and after every call)."""
+        rec = (lambda: events.append(torch.cuda.Event(enable_timing=True)) or events[-1].record()) \
+            if events is not None else (lambda: None)
+        g, v, cfg, b, st = self.g, self.views, self.cfg, self.bins, self.status
+        rec()
+        _lib.gs_project(g, v, cfg, self.proj, st)
+        rec()
+        _lib.gs_bin_sort(v, cfg, self.proj, b, st)
+        rec()
+        _lib.gs_render_fwd(v, cfg, self.proj, b, self.image, st)
+        rec()
+        _lib.gs_l1_loss(self.image, self.target, self.loss, self.dimg)
+        rec()
+        _lib.gs_rasterize_bwd(v, cfg, self.proj, b, self.image, self.dimg, self.grads.grad2d, st)
+        rec()
+        _lib.gs_project_bwd(g, v, cfg, self.proj, self.grads, self.want, st)
+        rec()
+        _lib.gs_pose_grad(v, self.grads.pose_partials, self.grads.n_blocks, self.dviewmat, self.dtwist)
+        rec()
+
+    def capture(self):
+        dev = self.g.means.device
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            self.run()
+            torch.cuda.synchronize(dev)
+            with torch.cuda.graph(self.graph, stream=s):
+                self.run()
+        torch.cuda.synchronize(dev)
+
+    def replay(self):
+        self.graph.replay()
+
+    def check(self):
+        """Read the status word (synchronises). On a capacity overflow, grow
+        the capacity, re-capture, and report True (the step must be rerun)."""
+        st = self.status.cpu().numpy()
+        if st[0] == 0:
+            return False
+        if st[0] != _lib.GS_ERR_CAPACITY:
+            raise _lib.GsError(int(st[0]), "device status")
+        needed = (int(st[1]) & 0xffffffff) | (int(st[2]) << 32)
+        self.capacity = int(needed * 1.25) + 4096
+        self.rast.reserve(self.views, self.capacity, self.g.means.device)
+        self.bins, self.status = self.rast.bins, self.rast.status
+        self.capture()
+        return True
+
+
+class PlainStep:
+    """The same step, uncaptured and view by view."""
+
+    def __init__(self, g: Gaussians, views: Views, target, tile=(16, 16)):
+        self.g = g
+        self.one = []
+        off = 0
+        for v in range(views.n):
+            vv = Views(views.viewmats[v:v + 1], views.intrinsics[v:v + 1], views.width[v:v + 1],
+                       views.height[v:v + 1], views.gauss_begin[v:v + 1], views.gauss_count[v:v + 1])
+            n = vv.num_image_floats()
+            self.one.append((vv, target[off:off + n], Rasterizer(tile=tile)))
+            off += n
+        dev = g.means.device
+        self.loss = torch.empty(1, device=dev)
+
+    def run(self):
+        for vv, tgt, rast in self.one:
+            image, proj = rast.forward(self.g, vv)          # includes the instance-count readback
+            dimg = torch.empty_like(image)
+            _lib.gs_l1_loss(image, tgt, self.loss, dimg)
+            rast.backward(self.g, vv, proj, image, dimg)
