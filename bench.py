@@ -135,6 +135,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(value, device=None):
+    """Largest value over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpix_s(pixels_per_rank, world, ms_per_step):
+    """Whole-job throughput of N replicas, each doing pixels_per_rank per step."""
+    return world * pixels_per_rank / (ms_per_step * 1e-3) / 1e6
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -205,14 +221,10 @@ def run_native(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-    ms = t0.elapsed_time(t1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, dev)
     clocks = clk.summary()
     rast.check_status()
-    value = world * P / (ms * 1e-3) / 1e6
+    value = whole_job_mpix_s(P, world, ms)
 
     # end to end through the public API: pinned host inputs copied in, result out
     e2e = None
@@ -247,12 +259,8 @@ def run_native(args, rank, world, local_rank):
             e2e_step()
         b.record()
         torch.cuda.synchronize()
-        ems = a.elapsed_time(b) / k_e2e
-        if world > 1:
-            tt = torch.tensor([ems], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt.item())
-        e2e = {"value": round(world * P / (ems * 1e-3) / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        ems = max_over_ranks(a.elapsed_time(b) / k_e2e, dev)
+        e2e = {"value": round(whole_job_mpix_s(P, world, ems), 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ems, 4), "steps": k_e2e}
 
     # roofline of the dominant kernel
