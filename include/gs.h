@@ -149,16 +149,19 @@ int gs_pose_blocks(int64_t n);
 
 /* Project every Gaussian into every view that sees it (Section 3.1
  * primitive; EWA splatting). Per slot p, proj[16p..16p+15] =
- *   {x, y, x_lo, y_lo}  mean in pixels as an unevaluated float pair x+x_lo,
+ *   {x, y, ext_x, ext_y} mean in pixels (high part) and the half-extents of
+ *                       the pixels the Gaussian can reach: min(radius,
+ *                       sqrt(k Sigma'_xx)) (and yy) with k = 2 ln(o /
+ *                       alpha_min), the bounding box of the ellipse where
+ *                       alpha >= alpha_min (culled if k <= 0),
  *   {a, b, c, o}        dilated 2D covariance Sigma' (b off-diagonal; its
  *                       inverse is the conic) and opacity,
  *   {r, g, b, radius}   colour (SH evaluated, +0.5, clamped at 0) and the
  *                       integer radius ceil(3 sqrt(lambda_max)) (0 = culled),
- *   {depth, clamp_bits, ext_x, ext_y}  camera z; bit c set if channel c was
- *                       clamped; half-extents of the pixels the Gaussian can
- *                       reach: min(radius, sqrt(k Sigma'_xx)) (and yy) with
- *                       k = 2 ln(o / alpha_min), i.e. the bounding box of the
- *                       ellipse where alpha >= alpha_min (culled if k <= 0).
+ *   {x_lo, y_lo, depth, clamp_bits}  low parts of the mean (x + x_lo is the
+ *                       position to ~1e-5 px), camera z, bit c set if colour
+ *                       channel c was clamped.
+ * Culled records are all zero.
  * proj: DEVICE [P,16]. status: DEVICE int32[4] (unused here, may be NULL). */
 int gs_project(const gs_gaussians *g, const gs_views *views, const gs_config *cfg,
                float *proj, int32_t *status, void *stream);

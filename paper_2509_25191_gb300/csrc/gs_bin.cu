@@ -30,16 +30,16 @@ constexpr int LARGE_BUCKET = 13;        // bucket of counts >= 4096 (chunked sor
 // removes almost all same-address contention on the per-tile counters.
 // Views with more tiles than BIN_SMEM_TILES fall back to direct atomics.
 constexpr int BIN_THREADS = 512;
-constexpr int BIN_CHUNK = 4096;
-constexpr int BIN_SMEM_TILES = 12288;   // 48 KB of int counters
+constexpr int BIN_CHUNK = 2048;
+constexpr int BIN_SMEM_TILES = 12288;   // at most 48 KB of int counters, sized per launch
 
+// The first float4 of a record holds everything binning needs (one sector);
+// culled records are all zero, valid ones have positive extents.
 __device__ __forceinline__ bool slot_rect(const Launch &L, const float4 *__restrict__ proj, long long p,
                                           const ViewDesc &vd, int &x0, int &x1, int &y0, int &y1) {
-    const float4 r2 = proj[4 * p + 2];
-    if (!(r2.w > 0.f)) return false;
     const float4 r0 = proj[4 * p];
-    const float4 r3 = proj[4 * p + 3];
-    tile_rect(r0.x, r0.y, r3.z, r3.w, 1.f / (float)L.tw, 1.f / (float)L.th, vd.Gx, vd.Gy, x0, x1, y0, y1);
+    if (!(r0.z > 0.f)) return false;
+    tile_rect(r0.x, r0.y, r0.z, r0.w, 1.f / (float)L.tw, 1.f / (float)L.th, vd.Gx, vd.Gy, x0, x1, y0, y1);
     return true;
 }
 
@@ -50,8 +50,8 @@ __device__ __forceinline__ long long segment_end(const Launch &L, int v, long lo
 }
 
 __global__ void __launch_bounds__(BIN_THREADS) k_bin_count(const Launch L, const float4 *__restrict__ proj,
-                                                           int *__restrict__ tile_count) {
-    __shared__ int s_cnt[BIN_SMEM_TILES];
+                                                           int *__restrict__ tile_count, int smem_tiles) {
+    extern __shared__ int s_cnt[];
     const long long c0 = (long long)blockIdx.x * BIN_CHUNK;
     const long long c1 = c0 + BIN_CHUNK < L.n_slots ? c0 + BIN_CHUNK : L.n_slots;
     for (long long seg = c0; seg < c1;) {
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_count(const Launch L, const
         const long long seg_end = segment_end(L, v, c1);
         const ViewDesc &vd = L.v[v];
         const int Tv = vd.Gx * vd.Gy;
-        const bool on_chip = Tv <= BIN_SMEM_TILES;
+        const bool on_chip = Tv <= smem_tiles;
         if (on_chip) {
             for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) s_cnt[t] = 0;
             __syncthreads();
@@ -180,8 +180,8 @@ __global__ void __launch_bounds__(1024) k_bin_scan(const Launch L, long long cap
 __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, const float4 *__restrict__ proj,
                                                              int *__restrict__ cursor,
                                                              unsigned long long *__restrict__ keys,
-                                                             const int *__restrict__ counters) {
-    __shared__ int s_cnt[BIN_SMEM_TILES];
+                                                             const int *__restrict__ counters, int smem_tiles) {
+    extern __shared__ int s_cnt[];
     if (counters[CNT_ABORT]) return;
     const long long c0 = (long long)blockIdx.x * BIN_CHUNK;
     const long long c1 = c0 + BIN_CHUNK < L.n_slots ? c0 + BIN_CHUNK : L.n_slots;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, con
         const long long seg_end = segment_end(L, v, c1);
         const ViewDesc &vd = L.v[v];
         const int Tv = vd.Gx * vd.Gy;
-        const bool on_chip = Tv <= BIN_SMEM_TILES;
+        const bool on_chip = Tv <= smem_tiles;
         if (on_chip) {
             for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) s_cnt[t] = 0;
             __syncthreads();
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, con
         for (long long p = seg + threadIdx.x; p < seg_end; p += BIN_THREADS) {
             int x0, x1, y0, y1;
             if (!slot_rect(L, proj, p, vd, x0, x1, y0, y1)) continue;
-            const float depth = proj[4 * p + 3].x;
+            const float depth = proj[4 * p + 3].z;
             const unsigned long long key =
                 ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned long long)(unsigned int)p;
             for (int ty = y0; ty < y1; ++ty)
@@ -240,19 +240,19 @@ constexpr int SORT_SEG_MIN = 128;   // at least this many keys per active warp
 struct SortSmem {
     unsigned int key[2][SORT_CAP];
     unsigned int val[2][SORT_CAP];
-    unsigned int hist[SORT_WARPS][256];   // digit counts, then running offsets
+    unsigned int hist[256][SORT_WARPS + 1];   // [digit][warp] counts, then running offsets (odd pitch)
     unsigned int part[SORT_THREADS];
     unsigned int kmin, kmax;
     int item;
 };
 
-// exclusive scan of the (digit, warp)-ordered counts hist[w][d], w < nwa
+// exclusive scan of the (digit, warp)-ordered counts hist[d][w], w < nwa
 __device__ __forceinline__ void scan_hist(SortSmem &S, int nwa) {
     const int E = 256 * nwa;
     const int per = (E + SORT_THREADS - 1) / SORT_THREADS;
     const int e0 = min(E, (int)threadIdx.x * per), e1 = min(E, e0 + per);
     unsigned int sum = 0;
-    for (int e = e0; e < e1; ++e) sum += S.hist[e % nwa][e / nwa];
+    for (int e = e0; e < e1; ++e) sum += S.hist[e / nwa][e % nwa];
     // block exclusive scan of the per-thread sums
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned int incl = sum;
@@ -275,7 +275,7 @@ __device__ __forceinline__ void scan_hist(SortSmem &S, int nwa) {
     __syncthreads();
     unsigned int run = S.part[wid] + incl - sum;
     for (int e = e0; e < e1; ++e) {
-        unsigned int &h = S.hist[e % nwa][e / nwa];
+        unsigned int &h = S.hist[e / nwa][e % nwa];
         const unsigned int c = h;
         h = run;
         run += c;
@@ -310,7 +310,7 @@ __device__ void radix_sort_tile(SortSmem &S, unsigned long long *__restrict__ ke
     int cur = 0;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
-        for (int e = threadIdx.x; e < 256 * nwa; e += SORT_THREADS) S.hist[e / 256][e % 256] = 0;
+        for (int e = threadIdx.x; e < 256 * nwa; e += SORT_THREADS) S.hist[e / nwa][e % nwa] = 0;
         __syncthreads();
         if (wid < nwa) {
             for (int b = s0; b < s1; b += 32) {
@@ -318,7 +318,7 @@ __device__ void radix_sort_tile(SortSmem &S, unsigned long long *__restrict__ ke
                 const bool act = i < s1;
                 const unsigned int d = act ? (S.key[cur][i] >> shift) & 255u : 256u + lane;
                 const unsigned int peers = __match_any_sync(0xffffffffu, d);
-                if (act && lane == __ffs(peers) - 1) S.hist[wid][d] += __popc(peers);
+                if (act && lane == __ffs(peers) - 1) S.hist[d][wid] += __popc(peers);
                 __syncwarp();
             }
         }
@@ -331,9 +331,9 @@ __device__ void radix_sort_tile(SortSmem &S, unsigned long long *__restrict__ ke
                 const unsigned int d = act ? (S.key[cur][i] >> shift) & 255u : 256u + lane;
                 const unsigned int peers = __match_any_sync(0xffffffffu, d);
                 unsigned int pos = 0;
-                if (act) pos = S.hist[wid][d] + __popc(peers & lt_mask);
+                if (act) pos = S.hist[d][wid] + __popc(peers & lt_mask);
                 __syncwarp();
-                if (act && lane == __ffs(peers) - 1) S.hist[wid][d] += __popc(peers);
+                if (act && lane == __ffs(peers) - 1) S.hist[d][wid] += __popc(peers);
                 if (act) {
                     S.key[cur ^ 1][pos] = S.key[cur][i];
                     S.val[cur ^ 1][pos] = S.val[cur][i];
@@ -437,12 +437,17 @@ int launch_bin_sort(const Launch &L, const float *proj, const gs_bins *b, int32_
     if (cudaMemsetAsync(b->tile_scratch, 0, sizeof(int) * (size_t)L.n_tiles, st) != cudaSuccess) return GS_ERR_CUDA;
     if (cudaMemsetAsync(b->counters, 0, sizeof(int) * GS_NUM_COUNTERS, st) != cudaSuccess) return GS_ERR_CUDA;
     const long long nb = (L.n_slots + BIN_CHUNK - 1) / BIN_CHUNK;
-    if (nb > 0) k_bin_count<<<nb, BIN_THREADS, 0, st>>>(L, p, b->tile_scratch);
+    int smem_tiles = 0;
+    for (int v = 0; v < L.n_views; ++v) smem_tiles = max(smem_tiles, L.v[v].Gx * L.v[v].Gy);
+    smem_tiles = min(smem_tiles, BIN_SMEM_TILES);
+    const size_t bin_smem = sizeof(int) * (size_t)max(smem_tiles, 1);
+    if (nb > 0) k_bin_count<<<nb, BIN_THREADS, bin_smem, st>>>(L, p, b->tile_scratch, smem_tiles);
     k_bin_scan<<<1, 1024, 0, st>>>(L, b->capacity, b->tile_scratch, reinterpret_cast<int2 *>(b->tile_ranges),
                                    b->tile_order, b->counters, status);
     if (nb > 0)
-        k_bin_scatter<<<nb, BIN_THREADS, 0, st>>>(L, p, b->tile_scratch,
-                                                  reinterpret_cast<unsigned long long *>(b->keys), b->counters);
+        k_bin_scatter<<<nb, BIN_THREADS, bin_smem, st>>>(L, p, b->tile_scratch,
+                                                         reinterpret_cast<unsigned long long *>(b->keys), b->counters,
+                                                         smem_tiles);
     static int smem_set = 0;
     const int smem = (int)sizeof(SortSmem);
     if (!smem_set) {

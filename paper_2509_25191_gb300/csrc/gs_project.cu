@@ -3,7 +3,7 @@
 // One thread per Gaussian; the thread reads the Gaussian's raw record once
 // (mean, log-scale, quaternion, opacity logit, SH) and loops over the views
 // of its scene, writing one 64-byte record per (view, Gaussian) slot:
-//   {x, y, x_lo, y_lo} {a, b, c, o} {r, g, b, radius} {depth, clamp_bits, ext_x, ext_y}
+//   {x, y, ext_x, ext_y} {a, b, c, o} {r, g, b, radius} {x_lo, y_lo, depth, clamp_bits}
 // with (a, b, c) the dilated 2D covariance (its inverse is the conic).
 // Section 3.1: Sigma = R S S^T R^T, opacity, SH colour. EWA splatting:
 // Sigma' = J W Sigma W^T J^T + dilation I, conic = inverse, radius =
@@ -148,10 +148,10 @@ __global__ void __launch_bounds__(128) k_project_fwd(const Launch L, const float
             const float grow = 1.f + 6.103515625e-05f;   // 1 + 2^-14
             const float ex = fminf(radius, sqrtf(kext * ca) * grow);
             const float ey = fminf(radius, sqrtf(kext * cc) * grow);
-            out[0] = make_float4(PX.hi, PY.hi, PX.lo, PY.lo);
+            out[0] = make_float4(PX.hi, PY.hi, ex, ey);
             out[1] = make_float4(ca, cb, cc, opac);
             out[2] = make_float4(rgb[0], rgb[1], rgb[2], radius);
-            out[3] = make_float4(z, __int_as_float(clamp_bits), ex, ey);
+            out[3] = make_float4(PX.lo, PY.lo, z, __int_as_float(clamp_bits));
         } else {
             const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
             out[0] = zero; out[1] = zero; out[2] = zero; out[3] = zero;

@@ -20,11 +20,11 @@
 
 namespace gsk {
 
-constexpr int PB_THREADS = 256;
+constexpr int PB_THREADS = 128;   // 168 registers: 3 blocks per SM, no spills
 constexpr int PB_WARPS = PB_THREADS / 32;
 
 template <int DEG, bool GAUSS>
-__global__ void __launch_bounds__(PB_THREADS) k_project_bwd(
+__global__ void __launch_bounds__(PB_THREADS, 3) k_project_bwd(
     const Launch L, const float *__restrict__ means, const float *__restrict__ log_scales,
     const float *__restrict__ quats, const float *__restrict__ logits, const float *__restrict__ sh,
     const float *__restrict__ viewmats, const float *__restrict__ intr, const float4 *__restrict__ proj,
@@ -49,9 +49,8 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(
 
         float mx = 0.f, my = 0.f, mz = 0.f, sc[3] = {0.f, 0.f, 0.f}, qn[4] = {1.f, 0.f, 0.f, 0.f}, qlen = 1.f;
         float Rq[9], M[9], S00 = 0, S01 = 0, S02 = 0, S11 = 0, S12 = 0, S22 = 0, opac = 0.f;
-        float f[3 * K];
-#pragma unroll
-        for (int k = 0; k < 3 * K; ++k) f[k] = 0.f;
+        // SH coefficients are read per view where needed (L1-resident), not held in registers
+        const float *f = sh + (long long)3 * K * (valid ? i : 0);
         if (valid) {
             mx = means[3 * i]; my = means[3 * i + 1]; mz = means[3 * i + 2];
 #pragma unroll
@@ -61,8 +60,6 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(
             const float iq = 1.f / qlen;
             qn[0] = q.x * iq; qn[1] = q.y * iq; qn[2] = q.z * iq; qn[3] = q.w * iq;
             opac = 1.f / (1.f + expf(-logits[i]));
-#pragma unroll
-            for (int k = 0; k < 3 * K; ++k) f[k] = sh[(long long)3 * K * i + k];
         }
         quat_rot(qn[0], qn[1], qn[2], qn[3], Rq);
 #pragma unroll
@@ -96,7 +93,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(
                 if (contrib) {
                     const float gx = ga4.x, gy = ga4.y, gsa = ga4.z, gsb = ga4.w, gsc = gb4.x, gop = gb4.y;
                     const float grgb[3] = {gb4.z, gb4.w, gc4.x};
-                    const int clamp_bits = __float_as_int(proj[4 * slot + 3].y);
+                    const int clamp_bits = __float_as_int(proj[4 * slot + 3].w);
                     const ViewDesc &vd = L.v[v];
                     const float *vm = viewmats + 12 * v;
                     float R[9], t[3];
@@ -145,7 +142,8 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(
                         float gY[16];
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
-                            gY[k] = f[3 * k] * graw[0] + f[3 * k + 1] * graw[1] + f[3 * k + 2] * graw[2];
+                            gY[k] = __ldg(f + 3 * k) * graw[0] + __ldg(f + 3 * k + 1) * graw[1] +
+                                    __ldg(f + 3 * k + 2) * graw[2];
                             if (GAUSS) {
                                 gf[3 * k] += Yb[k] * graw[0];
                                 gf[3 * k + 1] += Yb[k] * graw[1];
@@ -291,7 +289,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(
 
 int pose_blocks(long long n) {
     long long b = (n + PB_THREADS - 1) / PB_THREADS;
-    const long long cap = 4LL * num_sms();
+    const long long cap = 3LL * num_sms();   // one wave of resident blocks
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;

@@ -46,7 +46,7 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ proj, unsigned 
     const float4 r1 = proj[4ull * slot + 1];
     const float4 r2 = proj[4ull * slot + 2];
     const float4 r3 = proj[4ull * slot + 3];
-    xy = make_float4(__fadd_rn(__fsub_rn(r0.x, ox), r0.z), __fadd_rn(__fsub_rn(r0.y, oy), r0.w), r3.z, r3.w);
+    xy = make_float4(__fadd_rn(__fsub_rn(r0.x, ox), r3.x), __fadd_rn(__fsub_rn(r0.y, oy), r3.y), r0.z, r0.w);
     // det = a c - b^2 with b^2 carried exactly
     const ff bb = two_prod(r1.y, r1.y);
     const float det = __fsub_rn(__fmaf_rn(r1.x, r1.z, -bb.hi), bb.lo);
@@ -91,19 +91,43 @@ __device__ __forceinline__ int pix_x(int t) { return ((t >> 5) % (TW / 8)) * 8 +
 template <int TW>
 __device__ __forceinline__ int pix_y(int t) { return ((t >> 5) / (TW / 8)) * 4 + ((t & 31) >> 3); }
 
-// Bit w set if the staged Gaussian's reach box (enlarged by 1e-3 px, so the
-// test is conservative against float rounding) overlaps warp w's patch; the
-// per-pixel test |dx| <= ext_x, |dy| <= ext_y still decides exactly.
+// Bit w set if the staged Gaussian may reach warp w's 8x4 patch. Two
+// conservative tests (the per-pixel test still decides exactly):
+//  * the reach box |dx| <= ext_x, |dy| <= ext_y overlaps the patch (box
+//    enlarged by 1e-3 px against float rounding);
+//  * the exponent can reach log2(alpha_min / o) somewhere in the patch: with
+//    u = dx + beta dy, the base-2 exponent Ah u^2 + Dh dy^2 (Ah, Dh < 0) is at
+//    most Ah umin^2 + Dh dymin^2, where umin and dymin are the smallest |u|
+//    and |dy| over the patch (u ranges over the patch's dx interval shifted
+//    by beta times its dy interval). A 1e-3 margin keeps the test safe.
 template <int TW, int TH>
-__device__ __forceinline__ unsigned int warp_mask(const float4 &xy, float tbx, float tby) {
-    constexpr int NW = TW * TH / 32;
+__device__ __forceinline__ unsigned int warp_mask(const float4 &xy, const float4 &con, float alpha_min, float tbx,
+                                                  float tby) {
+    constexpr int WX = TW / 8, WY = TH / 4;
     const float ex = xy.z + 1e-3f, ey = xy.w + 1e-3f;
+    const float lim = __log2f(alpha_min / con.w) - 1e-3f;
+    float dxlo[WX], dylo[WY], dyhi[WY], bmin[WY], bmax[WY], dy2[WY];
+#pragma unroll
+    for (int c = 0; c < WX; ++c) dxlo[c] = tbx + (float)(c * 8) + 0.5f - xy.x;
+#pragma unroll
+    for (int r = 0; r < WY; ++r) {
+        dylo[r] = tby + (float)(r * 4) + 0.5f - xy.y;
+        dyhi[r] = dylo[r] + 3.f;
+        const float b0 = con.y * dylo[r], b1 = con.y * dyhi[r];
+        bmin[r] = fminf(b0, b1);
+        bmax[r] = fmaxf(b0, b1);
+        const float dm = fmaxf(0.f, fmaxf(dylo[r], -dyhi[r]));
+        dy2[r] = con.z * dm * dm;
+    }
     unsigned int m = 0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        const float x0 = tbx + (float)((w % (TW / 8)) * 8) + 0.5f, y0 = tby + (float)((w / (TW / 8)) * 4) + 0.5f;
-        const bool hit = xy.x + ex >= x0 && xy.x - ex <= x0 + 7.f && xy.y + ey >= y0 && xy.y - ey <= y0 + 3.f;
-        m |= (unsigned int)hit << w;
+    for (int w = 0; w < WX * WY; ++w) {
+        const int c = w % WX, r = w / WX;
+        const bool box = dxlo[c] <= ex && dxlo[c] + 7.f >= -ex && dylo[r] <= ey && dyhi[r] >= -ey;
+        const float ulo = dxlo[c] + bmin[r], uhi = dxlo[c] + 7.f + bmax[r];
+        const float um = fmaxf(0.f, fmaxf(ulo, -uhi));
+        const bool reach = con.x * um * um + dy2[r] >= lim;
+        m |= (unsigned int)(box && reach) << w;
     }
     return m;
 }
@@ -190,7 +214,8 @@ __global__ void __launch_bounds__(TW * TH) k_render_fwd(const Launch L, const fl
             const int j = b0 + threadIdx.x;
             if (j < r.y) {
                 stage(proj, ids[j], ti.ox, ti.oy, s_xy[threadIdx.x], s_con[threadIdx.x], s_rgb[threadIdx.x]);
-                s_mask[threadIdx.x] = warp_mask<TW, TH>(s_xy[threadIdx.x], ti.tbx, ti.tby);
+                s_mask[threadIdx.x] = warp_mask<TW, TH>(s_xy[threadIdx.x], s_con[threadIdx.x], L.alpha_min, ti.tbx,
+                                                         ti.tby);
             }
             __syncthreads();
             const int nb = min(BS, r.y - b0);
@@ -273,7 +298,8 @@ __global__ void __launch_bounds__(TW * TH) k_render_bwd(const Launch L, const fl
             const int j = b0 + threadIdx.x;
             if (j < r.y) {
                 stage(proj, ids[j], ti.ox, ti.oy, s_xy[threadIdx.x], s_con[threadIdx.x], s_rgb[threadIdx.x]);
-                s_mask[threadIdx.x] = warp_mask<TW, TH>(s_xy[threadIdx.x], ti.tbx, ti.tby);
+                s_mask[threadIdx.x] = warp_mask<TW, TH>(s_xy[threadIdx.x], s_con[threadIdx.x], L.alpha_min, ti.tbx,
+                                                         ti.tby);
             }
             __syncthreads();
             const int nb = min(BS, r.y - b0);

@@ -110,8 +110,8 @@ def test_projection_parity(case):
         amb = (frac < 1e-4) | (frac > 1 - 1e-4)
         disagree = ((rad > 0) != (ref["radius"] > 0)) & ~amb
         assert disagree.sum() <= max(2, 1e-4 * len(rad)), disagree.sum()
-        x = rec[:, 0].astype(np.float64) + rec[:, 2]
-        y = rec[:, 1].astype(np.float64) + rec[:, 3]
+        x = rec[:, 0].astype(np.float64) + rec[:, 12]
+        y = rec[:, 1].astype(np.float64) + rec[:, 13]
         assert np.abs(x - ref["xy"][:, 0])[both].max() < 2e-5 * max(1.0, np.abs(ref["xy"][both]).max())
         assert np.abs(y - ref["xy"][:, 1])[both].max() < 2e-5 * max(1.0, np.abs(ref["xy"][both]).max())
         cov = rec[:, 4:7][both]
@@ -122,9 +122,9 @@ def test_projection_parity(case):
         assert np.abs(rec[:, 8:11][both] - ref["rgb"][both]).max() < 1e-5
         ok_r = both & ~amb
         assert np.array_equal(rad[ok_r], ref["radius"][ok_r].astype(np.float32))
-        assert np.abs(rec[:, 12][both] / ref["depth"][both] - 1).max() < 1e-6
+        assert np.abs(rec[:, 14][both] / ref["depth"][both] - 1).max() < 1e-6
         # reach extents: the float32 value is enlarged by 2^-14 unless clipped to the radius
-        ext, rext = rec[:, 14:16][ok_r], ref["ext"][ok_r]
+        ext, rext = rec[:, 2:4][ok_r], ref["ext"][ok_r]
         assert (ext >= rext * (1 - 1e-6)).all() and (ext <= rext * (1 + 2e-4) + 1e-5).all()
 
 
@@ -140,8 +140,8 @@ def _records_from_oracle(sc, vw):
         r[:, 0] = ref["xy"][:, 0].astype(np.float32)
         r[:, 1] = ref["xy"][:, 1].astype(np.float32)
         r[:, 11] = ref["radius"].astype(np.float32)
-        r[:, 12] = ref["depth"].astype(np.float32)
-        r[:, 14:16] = ref["ext"].astype(np.float32)
+        r[:, 14] = ref["depth"].astype(np.float32)
+        r[:, 2:4] = ref["ext"].astype(np.float32)
         recs.append((ref, r))
     return recs
 
@@ -158,7 +158,7 @@ def test_binning_bit_exact(case, tile):
     refs = []
     for v, (ref, r) in enumerate(recs):
         W, H = int(vw.width[v]), int(vw.height[v])
-        refs.append(O.bin_view(r[:, 0], r[:, 1], ref["radius"], r[:, 12], W, H, *tile, ext=r[:, 14:16]))
+        refs.append(O.bin_view(r[:, 0], r[:, 1], ref["radius"], r[:, 14], W, H, *tile, ext=r[:, 2:4]))
         n_inst += len(refs[-1][2])
     bins = _lib.Bins(views.num_tiles(cfg), n_inst)
     status = _lib.new_status()
@@ -191,16 +191,16 @@ def test_binning_large_tiles_bit_exact():
     r[:, 0] = rng.uniform(0, 64, n)
     r[:, 1] = rng.uniform(0, 48, n)
     r[:, 11] = rng.integers(1, 3, n)
-    r[:, 12] = rng.uniform(1.0, 9.0, n).astype(np.float32)
-    r[:, 14] = r[:, 11] * rng.uniform(0.3, 1.0, n)
-    r[:, 15] = r[:, 11]
+    r[:, 14] = rng.uniform(1.0, 9.0, n).astype(np.float32)
+    r[:, 2] = r[:, 11] * rng.uniform(0.3, 1.0, n)
+    r[:, 3] = r[:, 11]
     r[:40000, 0] = rng.uniform(17, 30, 40000)   # one very crowded tile column
     r[:40000, 1] = rng.uniform(17, 30, 40000)
     vw = synth.Views(np.zeros((1, 12), np.float32), np.ones((1, 4), np.float32), np.array([W], np.int32),
                      np.array([H], np.int32), np.array([0]), np.array([n]))
     views = _lib.Views.from_synth(vw)
     cfg = _lib.config(tile=(16, 16))
-    rr, kk, ii = O.bin_view(r[:, 0], r[:, 1], r[:, 11].astype(np.int32), r[:, 12], W, H, 16, 16, ext=r[:, 14:16])
+    rr, kk, ii = O.bin_view(r[:, 0], r[:, 1], r[:, 11].astype(np.int32), r[:, 14], W, H, 16, 16, ext=r[:, 2:4])
     assert (rr[:, 1] - rr[:, 0]).max() > 16384
     bins = _lib.Bins(views.num_tiles(cfg), len(ii))
     _lib.gs_bin_sort(views, cfg, torch.as_tensor(r).cuda(), bins, _lib.new_status())
