@@ -226,10 +226,10 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, con
 }
 
 // ---------------------------------------------------------------------------
-// per-tile sort: stable block-wide LSD radix sort of the 32-bit depth bits
-// (8-bit digits; passes above the tile's highest differing bit are skipped),
-// carrying the slot, then a fix-up that orders runs of equal depth by slot.
-// The result is the unique (depth, slot) order. Tiles longer than SORT_CAP
+// per-tile sort: stable block-wide LSD radix sort (8-bit digits) of a 16-bit
+// monotone compression of the depth bits, carrying the slot, then a fix-up
+// that orders each run of equal compressed keys by (depth bits, slot). The
+// result is the unique (depth, slot) order. Tiles longer than SORT_CAP
 // are sorted in chunks and merged (merge path) through keys_tmp.
 // ---------------------------------------------------------------------------
 constexpr int SORT_THREADS = 512;
@@ -301,22 +301,27 @@ __device__ void radix_sort_tile(SortSmem &S, unsigned long long *__restrict__ ke
     atomicMin(&S.kmin, lmin);
     atomicMax(&S.kmax, lmax);
     __syncthreads();
-    const unsigned int diff = S.kmin ^ S.kmax;
-    const int passes = diff ? (32 - __clz(diff) + 7) / 8 : 0;
+    // Radix-sort a 16-bit monotone compression of the depth bits,
+    // (bits - kmin) >> shift, then order each run of equal compressed keys by
+    // the full (depth bits, slot): the same total order in at most 2 passes.
+    const unsigned int kmin = S.kmin, range = S.kmax - S.kmin;
+    const int nbits = range ? 32 - __clz(range) : 0;
+    const int shift = nbits > 16 ? nbits - 16 : 0;
+    const int passes = (min(nbits, 16) + 7) / 8;
     const int nwa = max(1, min(SORT_WARPS, (n + SORT_SEG_MIN - 1) / SORT_SEG_MIN));
     const int seg = ((n + nwa - 1) / nwa + 31) & ~31;
     const int s0 = wid * seg, s1 = min(n, s0 + seg);
     const unsigned int lt_mask = (1u << lane) - 1u;
     int cur = 0;
     for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
+        const int dshift = shift + 8 * pass;
         for (int e = threadIdx.x; e < 256 * nwa; e += SORT_THREADS) S.hist[e / nwa][e % nwa] = 0;
         __syncthreads();
         if (wid < nwa) {
             for (int b = s0; b < s1; b += 32) {
                 const int i = b + lane;
                 const bool act = i < s1;
-                const unsigned int d = act ? (S.key[cur][i] >> shift) & 255u : 256u + lane;
+                const unsigned int d = act ? ((S.key[cur][i] - kmin) >> dshift) & 255u : 256u + lane;
                 const unsigned int peers = __match_any_sync(0xffffffffu, d);
                 if (act && lane == __ffs(peers) - 1) S.hist[d][wid] += __popc(peers);
                 __syncwarp();
@@ -328,7 +333,7 @@ __device__ void radix_sort_tile(SortSmem &S, unsigned long long *__restrict__ ke
             for (int b = s0; b < s1; b += 32) {
                 const int i = b + lane;
                 const bool act = i < s1;
-                const unsigned int d = act ? (S.key[cur][i] >> shift) & 255u : 256u + lane;
+                const unsigned int d = act ? ((S.key[cur][i] - kmin) >> dshift) & 255u : 256u + lane;
                 const unsigned int peers = __match_any_sync(0xffffffffu, d);
                 unsigned int pos = 0;
                 if (act) pos = S.hist[d][wid] + __popc(peers & lt_mask);
@@ -344,17 +349,23 @@ __device__ void radix_sort_tile(SortSmem &S, unsigned long long *__restrict__ ke
         __syncthreads();
         cur ^= 1;
     }
-    // equal depths: order each run by slot (runs are rare and short)
+    // runs of equal compressed key: insertion sort by (depth bits, slot)
     for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
-        const unsigned int k = S.key[cur][i];
-        if ((i == 0 || S.key[cur][i - 1] != k) && i + 1 < n && S.key[cur][i + 1] == k) {
+        const unsigned int c = (S.key[cur][i] - kmin) >> shift;
+        if ((i == 0 || ((S.key[cur][i - 1] - kmin) >> shift) != c) && i + 1 < n &&
+            ((S.key[cur][i + 1] - kmin) >> shift) == c) {
             int e = i + 1;
-            while (e < n && S.key[cur][e] == k) ++e;
+            while (e < n && ((S.key[cur][e] - kmin) >> shift) == c) ++e;
             for (int a = i + 1; a < e; ++a) {
-                const unsigned int v = S.val[cur][a];
+                const unsigned int ka = S.key[cur][a], va = S.val[cur][a];
                 int b = a - 1;
-                while (b >= i && S.val[cur][b] > v) { S.val[cur][b + 1] = S.val[cur][b]; --b; }
-                S.val[cur][b + 1] = v;
+                while (b >= i && (S.key[cur][b] > ka || (S.key[cur][b] == ka && S.val[cur][b] > va))) {
+                    S.key[cur][b + 1] = S.key[cur][b];
+                    S.val[cur][b + 1] = S.val[cur][b];
+                    --b;
+                }
+                S.key[cur][b + 1] = ka;
+                S.val[cur][b + 1] = va;
             }
         }
     }

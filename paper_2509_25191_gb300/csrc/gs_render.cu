@@ -9,8 +9,10 @@
 //   and the pixel stops.
 //
 // Both kernels are persistent: blocks pull tiles from an atomic queue over
-// tile_order (largest tiles first), one thread per pixel, and stage each
-// tile's instances through shared memory in batches of one per thread.
+// tile_order (largest tiles first). Each thread owns two pixels and each warp
+// an 8x8-pixel patch of the tile; a tile's instances are staged through
+// shared memory in batches (two per thread), and a warp skips every staged
+// Gaussian that cannot reach its patch.
 //
 // The backward does not store or replay transmittance: it walks the same list
 // front to back with bit-identical arithmetic (explicit-rounding intrinsics,
@@ -76,22 +78,42 @@ __device__ __forceinline__ bool eval_alpha(const float4 &xy, const float4 &con, 
 }
 
 struct TileInfo {
-    int view, px, py;
-    float ox, oy;     // block origin in pixels
-    float pcx, pcy;   // this thread's pixel centre relative to the block origin
+    int view;
+    int px, py0;      // this thread's pixels: (px, py0) and (px, py0 + 4)
+    float ox, oy;     // origin of the enclosing 32x32-pixel block
+    float pcx, pcy0;  // pixel centres relative to the block origin (second pixel: pcy0 + 4)
     float tbx, tby;   // tile origin relative to the block origin
-    bool inside;
+    bool in0, in1;    // pixels inside the image
 };
 
-// Pixels are assigned so that every warp covers an 8x4-pixel patch of the
-// tile (lane -> 8 columns x 4 rows), which lets whole warps skip Gaussians
-// that cannot reach their patch.
-template <int TW>
-__device__ __forceinline__ int pix_x(int t) { return ((t >> 5) % (TW / 8)) * 8 + (t & 7); }
-template <int TW>
-__device__ __forceinline__ int pix_y(int t) { return ((t >> 5) / (TW / 8)) * 4 + ((t & 31) >> 3); }
+// Pixels: warp w covers the 8x8 patch (w % (TW/8), w / (TW/8)) of the tile;
+// lane l owns column l & 7 and rows (l >> 3) and (l >> 3) + 4 of the patch.
+// Positions are relative to the enclosing 32x32-pixel block (every supported
+// tile nests in one), so a pixel's arithmetic is the same for every tile
+// shape and the image is bit-identical across shapes.
+template <int TW, int TH>
+__device__ __forceinline__ TileInfo tile_info(const Launch &L, int tile) {
+    TileInfo ti;
+    ti.view = view_of_tile(L, tile);
+    const ViewDesc &vd = L.v[ti.view];
+    const int lt = tile - vd.tile_base;
+    const int tx = lt % vd.Gx, ty = lt / vd.Gx;
+    const int w = (int)threadIdx.x >> 5, l = (int)threadIdx.x & 31;
+    ti.px = tx * TW + (w % (TW / 8)) * 8 + (l & 7);
+    ti.py0 = ty * TH + (w / (TW / 8)) * 8 + (l >> 3);
+    const int bx = (tx * TW) & ~31, by = (ty * TH) & ~31;
+    ti.ox = (float)bx;
+    ti.oy = (float)by;
+    ti.pcx = (float)(ti.px - bx) + 0.5f;
+    ti.pcy0 = (float)(ti.py0 - by) + 0.5f;
+    ti.tbx = (float)(tx * TW - bx);
+    ti.tby = (float)(ty * TH - by);
+    ti.in0 = ti.px < vd.W && ti.py0 < vd.H;
+    ti.in1 = ti.px < vd.W && ti.py0 + 4 < vd.H;
+    return ti;
+}
 
-// Bit w set if the staged Gaussian may reach warp w's 8x4 patch. Two
+// Bit w set if the staged Gaussian may reach warp w's 8x8 patch. Two
 // conservative tests (the per-pixel test still decides exactly):
 //  * the reach box |dx| <= ext_x, |dy| <= ext_y overlaps the patch (box
 //    enlarged by 1e-3 px against float rounding);
@@ -103,53 +125,32 @@ __device__ __forceinline__ int pix_y(int t) { return ((t >> 5) / (TW / 8)) * 4 +
 template <int TW, int TH>
 __device__ __forceinline__ unsigned int warp_mask(const float4 &xy, const float4 &con, float alpha_min, float tbx,
                                                   float tby) {
-    constexpr int WX = TW / 8, WY = TH / 4;
+    constexpr int WX = TW / 8, WY = TH / 8;
     const float ex = xy.z + 1e-3f, ey = xy.w + 1e-3f;
     const float lim = __log2f(alpha_min / con.w) - 1e-3f;
-    float dxlo[WX], dylo[WY], dyhi[WY], bmin[WY], bmax[WY], dy2[WY];
+    float dxlo[WX], dylo[WY], bmin[WY], bmax[WY], dy2[WY];
 #pragma unroll
     for (int c = 0; c < WX; ++c) dxlo[c] = tbx + (float)(c * 8) + 0.5f - xy.x;
 #pragma unroll
     for (int r = 0; r < WY; ++r) {
-        dylo[r] = tby + (float)(r * 4) + 0.5f - xy.y;
-        dyhi[r] = dylo[r] + 3.f;
-        const float b0 = con.y * dylo[r], b1 = con.y * dyhi[r];
+        dylo[r] = tby + (float)(r * 8) + 0.5f - xy.y;
+        const float b0 = con.y * dylo[r], b1 = con.y * (dylo[r] + 7.f);
         bmin[r] = fminf(b0, b1);
         bmax[r] = fmaxf(b0, b1);
-        const float dm = fmaxf(0.f, fmaxf(dylo[r], -dyhi[r]));
+        const float dm = fmaxf(0.f, fmaxf(dylo[r], -(dylo[r] + 7.f)));
         dy2[r] = con.z * dm * dm;
     }
     unsigned int m = 0;
 #pragma unroll
     for (int w = 0; w < WX * WY; ++w) {
         const int c = w % WX, r = w / WX;
-        const bool box = dxlo[c] <= ex && dxlo[c] + 7.f >= -ex && dylo[r] <= ey && dyhi[r] >= -ey;
+        const bool box = dxlo[c] <= ex && dxlo[c] + 7.f >= -ex && dylo[r] <= ey && dylo[r] + 7.f >= -ey;
         const float ulo = dxlo[c] + bmin[r], uhi = dxlo[c] + 7.f + bmax[r];
         const float um = fmaxf(0.f, fmaxf(ulo, -uhi));
         const bool reach = con.x * um * um + dy2[r] >= lim;
         m |= (unsigned int)(box && reach) << w;
     }
     return m;
-}
-
-template <int TW, int TH>
-__device__ __forceinline__ TileInfo tile_info(const Launch &L, int tile) {
-    TileInfo ti;
-    ti.view = view_of_tile(L, tile);
-    const ViewDesc &vd = L.v[ti.view];
-    const int lt = tile - vd.tile_base;
-    const int tx = lt % vd.Gx, ty = lt / vd.Gx;
-    ti.px = tx * TW + pix_x<TW>((int)threadIdx.x);
-    ti.py = ty * TH + pix_y<TW>((int)threadIdx.x);
-    const int bx = (tx * TW) & ~31, by = (ty * TH) & ~31;
-    ti.ox = (float)bx;
-    ti.oy = (float)by;
-    ti.pcx = (float)(ti.px - bx) + 0.5f;
-    ti.pcy = (float)(ti.py - by) + 0.5f;
-    ti.tbx = (float)(tx * TW - bx);
-    ti.tby = (float)(ty * TH - by);
-    ti.inside = ti.px < vd.W && ti.py < vd.H;
-    return ti;
 }
 
 // Sum 16 per-lane values over the warp by recursive halving: after the four
@@ -171,7 +172,7 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// add a thread's pair counts to the 64-bit counters at c[0], c[1] (one atomic per warp)
+// add a thread's pair counts to the 64-bit counters at counters + at (one atomic per warp)
 __device__ __forceinline__ void count_pairs(int *counters, int at, unsigned int n_eval, unsigned int n_comp) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -185,15 +186,32 @@ __device__ __forceinline__ void count_pairs(int *counters, int at, unsigned int 
     }
 }
 
+// Stage instances [b0, min(b0 + 2 BS, end)) of a tile: two per thread.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) k_render_fwd(const Launch L, const float4 *__restrict__ proj,
-                                                        const int2 *__restrict__ ranges,
-                                                        const unsigned int *__restrict__ ids,
-                                                        const int *__restrict__ order, int *__restrict__ counters,
-                                                        float *__restrict__ image) {
-    constexpr int BS = TW * TH;
-    __shared__ float4 s_xy[BS], s_con[BS], s_rgb[BS];
-    __shared__ unsigned int s_mask[BS];
+__device__ __forceinline__ void stage_batch(const Launch &L, const float4 *__restrict__ proj,
+                                            const unsigned int *__restrict__ ids, int b0, int end,
+                                            const TileInfo &ti, float4 *s_xy, float4 *s_con, float4 *s_rgb,
+                                            unsigned int *s_mask) {
+    constexpr int BS = TW * TH / 2;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = threadIdx.x + h * BS;
+        if (b0 + k < end) {
+            stage(proj, ids[b0 + k], ti.ox, ti.oy, s_xy[k], s_con[k], s_rgb[k]);
+            s_mask[k] = warp_mask<TW, TH>(s_xy[k], s_con[k], L.alpha_min, ti.tbx, ti.tby);
+        }
+    }
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, const float4 *__restrict__ proj,
+                                                            const int2 *__restrict__ ranges,
+                                                            const unsigned int *__restrict__ ids,
+                                                            const int *__restrict__ order, int *__restrict__ counters,
+                                                            float *__restrict__ image) {
+    constexpr int BS = TW * TH / 2, NB = TW * TH;
+    __shared__ float4 s_xy[NB], s_con[NB], s_rgb[NB];
+    __shared__ unsigned int s_mask[NB];
     __shared__ int s_item;
     const bool abort = counters[CNT_ABORT] != 0;
     const unsigned int wbit = 1u << (threadIdx.x >> 5);
@@ -206,73 +224,135 @@ __global__ void __launch_bounds__(TW * TH) k_render_fwd(const Launch L, const fl
         const int tile = order[item];
         const TileInfo ti = tile_info<TW, TH>(L, tile);
         const int2 r = abort ? make_int2(0, 0) : ranges[tile];
-        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-        bool done = !ti.inside;
-        unsigned int n_eval = 0, n_comp = 0;
-        for (int b0 = r.x; b0 < r.y; b0 += BS) {
-            if (__syncthreads_count(done) == BS) break;
-            const int j = b0 + threadIdx.x;
-            if (j < r.y) {
-                stage(proj, ids[j], ti.ox, ti.oy, s_xy[threadIdx.x], s_con[threadIdx.x], s_rgb[threadIdx.x]);
-                s_mask[threadIdx.x] = warp_mask<TW, TH>(s_xy[threadIdx.x], s_con[threadIdx.x], L.alpha_min, ti.tbx,
-                                                         ti.tby);
-            }
+        float T0 = 1.f, T1 = 1.f, C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
+        bool done0 = !ti.in0, done1 = !ti.in1;
+        const float pcy1 = ti.pcy0 + 4.f;
+        for (int b0 = r.x; b0 < r.y; b0 += NB) {
+            if (__syncthreads_count(done0 && done1) == BS) break;
+            stage_batch<TW, TH>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
             __syncthreads();
-            const int nb = min(BS, r.y - b0);
-            for (int k = 0; k < nb && !done; ++k) {
+            const int nb = min(NB, r.y - b0);
+            for (int k = 0; k < nb && !(done0 && done1); ++k) {
                 if (!(s_mask[k] & wbit)) continue;
-                float alpha, G = 0.f, dx, dy, u;
+                const float4 xy = s_xy[k], con = s_con[k];
+                float alpha, G, dx, dy, u;
                 bool clamped;
-                const bool use = eval_alpha(s_xy[k], s_con[k], ti.pcx, ti.pcy, L.alpha_min, L.alpha_max, alpha, G,
-                                            dx, dy, u, clamped);
-                n_eval += G > 0.f || use;
-                if (!use) continue;
-                const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                if (Tn < L.t_min) { done = true; break; }
-                ++n_comp;
-                const float w = __fmul_rn(alpha, T);
-                const float4 c = s_rgb[k];
-                C0 = __fmaf_rn(c.x, w, C0);
-                C1 = __fmaf_rn(c.y, w, C1);
-                C2 = __fmaf_rn(c.z, w, C2);
-                T = Tn;
+                if (!done0 && eval_alpha(xy, con, ti.pcx, ti.pcy0, L.alpha_min, L.alpha_max, alpha, G, dx, dy, u,
+                                         clamped)) {
+                    const float Tn = __fmul_rn(T0, __fsub_rn(1.f, alpha));
+                    if (Tn < L.t_min) {
+                        done0 = true;
+                    } else {
+                        const float w = __fmul_rn(alpha, T0);
+                        const float4 c = s_rgb[k];
+                        C00 = __fmaf_rn(c.x, w, C00);
+                        C01 = __fmaf_rn(c.y, w, C01);
+                        C02 = __fmaf_rn(c.z, w, C02);
+                        T0 = Tn;
+                    }
+                }
+                if (!done1 && eval_alpha(xy, con, ti.pcx, pcy1, L.alpha_min, L.alpha_max, alpha, G, dx, dy, u,
+                                         clamped)) {
+                    const float Tn = __fmul_rn(T1, __fsub_rn(1.f, alpha));
+                    if (Tn < L.t_min) {
+                        done1 = true;
+                    } else {
+                        const float w = __fmul_rn(alpha, T1);
+                        const float4 c = s_rgb[k];
+                        C10 = __fmaf_rn(c.x, w, C10);
+                        C11 = __fmaf_rn(c.y, w, C11);
+                        C12 = __fmaf_rn(c.z, w, C12);
+                        T1 = Tn;
+                    }
+                }
             }
         }
-        count_pairs(counters, 8, n_eval, n_comp);
-        if (ti.inside) {
-            const ViewDesc &vd = L.v[ti.view];
-            const long long hw = (long long)vd.W * vd.H;
-            const long long o = vd.pix_base + (long long)ti.py * vd.W + ti.px;
-            if (abort) {
-                image[o] = 0.f; image[o + hw] = 0.f; image[o + 2 * hw] = 0.f;
-            } else {
-                image[o] = __fmaf_rn(T, L.bg[0], C0);
-                image[o + hw] = __fmaf_rn(T, L.bg[1], C1);
-                image[o + 2 * hw] = __fmaf_rn(T, L.bg[2], C2);
-            }
+        const ViewDesc &vd = L.v[ti.view];
+        const long long hw = (long long)vd.W * vd.H;
+        if (ti.in0) {
+            const long long o = vd.pix_base + (long long)ti.py0 * vd.W + ti.px;
+            image[o] = abort ? 0.f : __fmaf_rn(T0, L.bg[0], C00);
+            image[o + hw] = abort ? 0.f : __fmaf_rn(T0, L.bg[1], C01);
+            image[o + 2 * hw] = abort ? 0.f : __fmaf_rn(T0, L.bg[2], C02);
+        }
+        if (ti.in1) {
+            const long long o = vd.pix_base + (long long)(ti.py0 + 4) * vd.W + ti.px;
+            image[o] = abort ? 0.f : __fmaf_rn(T1, L.bg[0], C10);
+            image[o + hw] = abort ? 0.f : __fmaf_rn(T1, L.bg[1], C11);
+            image[o + 2 * hw] = abort ? 0.f : __fmaf_rn(T1, L.bg[2], C12);
         }
     }
 }
 
+// One pixel's contribution to the gradient of Gaussian k (added into gv),
+// advancing the pixel's transmittance and colour sum exactly as the forward.
+// Returns 0 if the Gaussian was not evaluated at this pixel, 1 if its alpha
+// was evaluated but it was not composited, 2 if it was composited.
+__device__ __forceinline__ int pixel_grad(const float4 &xy, const float4 &con, const float4 &c, float pcx,
+                                           float pcy, const Launch &L, float img0, float img1, float img2,
+                                           float g0, float g1, float g2, float &T, float &C0, float &C1, float &C2,
+                                           bool &done, float *gv) {
+    float alpha, G = 0.f, dx, dy, u;
+    bool clamped;
+    if (!eval_alpha(xy, con, pcx, pcy, L.alpha_min, L.alpha_max, alpha, G, dx, dy, u, clamped)) return G > 0.f;
+    const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+    if (Tn < L.t_min) {
+        done = true;
+        return 1;
+    }
+    const float w = __fmul_rn(alpha, T);
+    C0 = __fmaf_rn(c.x, w, C0);
+    C1 = __fmaf_rn(c.y, w, C1);
+    C2 = __fmaf_rn(c.z, w, C2);
+    gv[6] += w * g0;
+    gv[7] += w * g1;
+    gv[8] += w * g2;
+    // colour behind this Gaussian: image - running sum
+    const float S0 = img0 - C0, S1 = img1 - C1, S2 = img2 - C2;
+    const float dL_dalpha = T * (c.x * g0 + c.y * g1 + c.z * g2) - (S0 * g0 + S1 * g1 + S2 * g2) / (1.f - alpha);
+    if (!clamped) {
+        // alpha = o G, G = exp(power), power = -1/2 d^T Q d with Q the conic
+        // (inverse of the covariance Sigma' = (a, b, c)), d = pixel - mean.
+        // With v = Q d = (A u, A beta u + D dy) from the staged form,
+        // d power / d mean = v and d power / d Sigma' = v v^T / 2, i.e.
+        // (v0^2/2, v0 v1, v1^2/2) for (a, b, c): summing these well-scaled
+        // terms over pixels avoids the ill-conditioned conic -> covariance
+        // conversion of summed conic gradients for elongated Gaussians.
+        gv[5] += dL_dalpha * G;
+        const float dp = dL_dalpha * alpha;
+        const float A = con.x * (-2.f * LN2), D = con.z * (-2.f * LN2);
+        const float v0 = A * u;
+        const float v1 = v0 * con.y + D * dy;
+        const float dv0 = dp * v0, dv1 = dp * v1;
+        gv[0] += dv0;
+        gv[1] += dv1;
+        gv[2] += 0.5f * dv0 * v0;
+        gv[3] += dv0 * v1;
+        gv[4] += 0.5f * dv1 * v1;
+    }
+    T = Tn;
+    return 2;
+}
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) k_render_bwd(const Launch L, const float4 *__restrict__ proj,
-                                                        const int2 *__restrict__ ranges,
-                                                        const unsigned int *__restrict__ ids,
-                                                        const int *__restrict__ order, int *__restrict__ counters,
-                                                        const float *__restrict__ image,
-                                                        const float *__restrict__ dL_dimage,
-                                                        float4 *__restrict__ grad2d) {
-    constexpr int BS = TW * TH;
-    __shared__ float4 s_xy[BS], s_con[BS], s_rgb[BS];
-    __shared__ unsigned int s_mask[BS];
-    __shared__ float s_g[BS][9];   // per staged Gaussian: summed gradient (odd stride: no bank conflicts)
+__global__ void __launch_bounds__(TW * TH / 2) k_render_bwd(const Launch L, const float4 *__restrict__ proj,
+                                                            const int2 *__restrict__ ranges,
+                                                            const unsigned int *__restrict__ ids,
+                                                            const int *__restrict__ order, int *__restrict__ counters,
+                                                            const float *__restrict__ image,
+                                                            const float *__restrict__ dL_dimage,
+                                                            float4 *__restrict__ grad2d) {
+    constexpr int BS = TW * TH / 2, NB = TW * TH;
+    __shared__ float4 s_xy[NB], s_con[NB], s_rgb[NB];
+    __shared__ unsigned int s_mask[NB];
+    __shared__ float s_g[NB][9];   // per staged Gaussian: summed gradient (odd stride: no bank conflicts)
     __shared__ int s_item;
-    const unsigned int wbit = 1u << (threadIdx.x >> 5);
     if (counters[CNT_ABORT]) return;
     const int lane = threadIdx.x & 31;
+    const unsigned int wbit = 1u << (threadIdx.x >> 5);
     const int red_idx = ((lane & 16) ? 8 : 0) + ((lane & 8) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
-    for (int c = 0; c < 9; ++c) s_g[threadIdx.x][c] = 0.f;
+    for (int k = threadIdx.x; k < NB; k += BS)
+        for (int c = 0; c < 9; ++c) s_g[k][c] = 0.f;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counters + CNT_Q_BWD, 1);
         __syncthreads();
@@ -282,84 +362,45 @@ __global__ void __launch_bounds__(TW * TH) k_render_bwd(const Launch L, const fl
         const int tile = order[item];
         const TileInfo ti = tile_info<TW, TH>(L, tile);
         const int2 r = ranges[tile];
-        float img0 = 0.f, img1 = 0.f, img2 = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-        if (ti.inside) {
-            const ViewDesc &vd = L.v[ti.view];
-            const long long hw = (long long)vd.W * vd.H;
-            const long long o = vd.pix_base + (long long)ti.py * vd.W + ti.px;
-            img0 = image[o]; img1 = image[o + hw]; img2 = image[o + 2 * hw];
-            g0 = dL_dimage[o]; g1 = dL_dimage[o + hw]; g2 = dL_dimage[o + 2 * hw];
-        }
-        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-        bool done = !ti.inside || (g0 == 0.f && g1 == 0.f && g2 == 0.f);
-        unsigned int n_eval = 0, n_comp = 0;
-        for (int b0 = r.x; b0 < r.y; b0 += BS) {
-            if (__syncthreads_count(done) == BS) break;
-            const int j = b0 + threadIdx.x;
-            if (j < r.y) {
-                stage(proj, ids[j], ti.ox, ti.oy, s_xy[threadIdx.x], s_con[threadIdx.x], s_rgb[threadIdx.x]);
-                s_mask[threadIdx.x] = warp_mask<TW, TH>(s_xy[threadIdx.x], s_con[threadIdx.x], L.alpha_min, ti.tbx,
-                                                         ti.tby);
+        const ViewDesc &vd = L.v[ti.view];
+        const long long hw = (long long)vd.W * vd.H;
+        float im[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, gg[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        bool done[2] = {!ti.in0, !ti.in1};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (done[h]) continue;
+            const long long o = vd.pix_base + (long long)(ti.py0 + 4 * h) * vd.W + ti.px;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                im[h][ch] = image[o + ch * hw];
+                gg[h][ch] = dL_dimage[o + ch * hw];
             }
+            done[h] = gg[h][0] == 0.f && gg[h][1] == 0.f && gg[h][2] == 0.f;
+        }
+        float T[2] = {1.f, 1.f}, C[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        unsigned int n_eval = 0, n_comp = 0;
+        for (int b0 = r.x; b0 < r.y; b0 += NB) {
+            if (__syncthreads_count(done[0] && done[1]) == BS) break;
+            stage_batch<TW, TH>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
             __syncthreads();
-            const int nb = min(BS, r.y - b0);
+            const int nb = min(NB, r.y - b0);
             for (int k = 0; k < nb; ++k) {
                 if (!(s_mask[k] & wbit)) continue;   // warp-uniform: no lane of this warp can be hit
-                // gradient of this pixel w.r.t. (x, y, a, b, c, o, r, g, b) of Gaussian k
+                // gradient of this thread's pixels w.r.t. (x, y, a, b, c, o, r, g, b) of Gaussian k
                 float gv[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) gv[c] = 0.f;
                 bool hit = false;
-                if (!done) {
-                    float alpha, G, dx, dy, u;
-                    bool clamped;
-                    const float4 xy = s_xy[k], con = s_con[k];
-                    G = 0.f;
-                    const bool use = eval_alpha(xy, con, ti.pcx, ti.pcy, L.alpha_min, L.alpha_max, alpha, G, dx,
-                                                dy, u, clamped);
-                    n_eval += G > 0.f || use;
-                    if (use) {
-                        const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                        if (Tn < L.t_min) {
-                            done = true;
-                        } else {
-                            hit = true;
-                            ++n_comp;
-                            const float w = __fmul_rn(alpha, T);
-                            const float4 c = s_rgb[k];
-                            C0 = __fmaf_rn(c.x, w, C0);
-                            C1 = __fmaf_rn(c.y, w, C1);
-                            C2 = __fmaf_rn(c.z, w, C2);
-                            gv[6] = w * g0;
-                            gv[7] = w * g1;
-                            gv[8] = w * g2;
-                            // colour behind this Gaussian: image - running sum
-                            const float S0 = img0 - C0, S1 = img1 - C1, S2 = img2 - C2;
-                            const float dL_dalpha =
-                                T * (c.x * g0 + c.y * g1 + c.z * g2) - (S0 * g0 + S1 * g1 + S2 * g2) / (1.f - alpha);
-                            if (!clamped) {
-                                // alpha = o G, G = exp(power), power = -1/2 d^T Q d with Q the conic
-                                // (inverse of the covariance Sigma' = (a, b, c)), d = pixel - mean.
-                                // With v = Q d = (A u, A beta u + D dy) from the staged form,
-                                // d power / d mean = v and d power / d Sigma' = v v^T / 2, i.e.
-                                // (v0^2/2, v0 v1, v1^2/2) for (a, b, c): summing these well-scaled
-                                // terms over pixels avoids the ill-conditioned conic -> covariance
-                                // conversion of summed conic gradients for elongated Gaussians.
-                                gv[5] = dL_dalpha * G;
-                                const float dp = dL_dalpha * alpha;
-                                const float A = con.x * (-2.f * LN2), D = con.z * (-2.f * LN2);
-                                const float v0 = A * u;
-                                const float v1 = v0 * con.y + D * dy;
-                                const float dv0 = dp * v0, dv1 = dp * v1;
-                                gv[0] = dv0;
-                                gv[1] = dv1;
-                                gv[2] = 0.5f * dv0 * v0;
-                                gv[3] = dv0 * v1;
-                                gv[4] = 0.5f * dv1 * v1;
-                            }
-                            T = Tn;
-                        }
-                    }
+                const float4 xy = s_xy[k], con = s_con[k], c = s_rgb[k];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (done[h]) continue;
+                    const int res = pixel_grad(xy, con, c, ti.pcx, ti.pcy0 + 4.f * h, L, im[h][0], im[h][1],
+                                               im[h][2], gg[h][0], gg[h][1], gg[h][2], T[h], C[h][0], C[h][1],
+                                               C[h][2], done[h], gv);
+                    hit |= res == 2;
+                    n_eval += res > 0;
+                    n_comp += res == 2;
                 }
                 if (__any_sync(0xffffffffu, hit)) {
                     const float sum = warp_reduce_scatter16(gv, lane);
@@ -368,20 +409,23 @@ __global__ void __launch_bounds__(TW * TH) k_render_bwd(const Launch L, const fl
             }
             __syncthreads();
             // flush this batch's per-Gaussian sums
-            const int k = threadIdx.x;
-            if (k < nb) {
-                const float a0 = s_g[k][0], a1 = s_g[k][1], a2 = s_g[k][2], a3 = s_g[k][3], a4 = s_g[k][4];
-                const float a5 = s_g[k][5], a6 = s_g[k][6], a7 = s_g[k][7], a8 = s_g[k][8];
-                if (a0 != 0.f || a1 != 0.f || a2 != 0.f || a3 != 0.f || a4 != 0.f || a5 != 0.f || a6 != 0.f ||
-                    a7 != 0.f || a8 != 0.f) {
-                    const unsigned int slot = __float_as_uint(s_rgb[k].w);
-                    float4 *dst = grad2d + 3ull * slot;
-                    atomicAdd(dst, make_float4(a0, a1, a2, a3));
-                    atomicAdd(dst + 1, make_float4(a4, a5, a6, a7));
-                    atomicAdd(dst + 2, make_float4(a8, 0.f, 0.f, 0.f));
-                }
 #pragma unroll
-                for (int c = 0; c < 9; ++c) s_g[k][c] = 0.f;
+            for (int h = 0; h < 2; ++h) {
+                const int k = threadIdx.x + h * BS;
+                if (k < nb) {
+                    const float a0 = s_g[k][0], a1 = s_g[k][1], a2 = s_g[k][2], a3 = s_g[k][3], a4 = s_g[k][4];
+                    const float a5 = s_g[k][5], a6 = s_g[k][6], a7 = s_g[k][7], a8 = s_g[k][8];
+                    if (a0 != 0.f || a1 != 0.f || a2 != 0.f || a3 != 0.f || a4 != 0.f || a5 != 0.f || a6 != 0.f ||
+                        a7 != 0.f || a8 != 0.f) {
+                        const unsigned int slot = __float_as_uint(s_rgb[k].w);
+                        float4 *dst = grad2d + 3ull * slot;
+                        atomicAdd(dst, make_float4(a0, a1, a2, a3));
+                        atomicAdd(dst + 1, make_float4(a4, a5, a6, a7));
+                        atomicAdd(dst + 2, make_float4(a8, 0.f, 0.f, 0.f));
+                    }
+#pragma unroll
+                    for (int cc = 0; cc < 9; ++cc) s_g[k][cc] = 0.f;
+                }
             }
         }
         count_pairs(counters, 12, n_eval, n_comp);
@@ -392,16 +436,16 @@ template <int TW, int TH>
 static int launch_fwd_t(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st) {
     static int blocks_per_sm = 0;
     if (!blocks_per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_fwd<TW, TH>, TW * TH, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_fwd<TW, TH>, TW * TH / 2, 0) !=
                 cudaSuccess || blocks_per_sm < 1)
             blocks_per_sm = 1;
     }
     const int grid = min(num_sms() * blocks_per_sm, max(1, L.n_tiles));
     // every call walks all tiles again: reset this kernel's work-queue head
     if (cudaMemsetAsync(b->counters + CNT_Q_FWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
-    k_render_fwd<TW, TH><<<grid, TW * TH, 0, st>>>(L, reinterpret_cast<const float4 *>(proj),
-                                                   reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
-                                                   b->tile_order, b->counters, image);
+    k_render_fwd<TW, TH><<<grid, TW * TH / 2, 0, st>>>(L, reinterpret_cast<const float4 *>(proj),
+                                                       reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
+                                                       b->tile_order, b->counters, image);
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
@@ -410,16 +454,16 @@ static int launch_bwd_t(const Launch &L, const float *proj, const gs_bins *b, co
                         const float *dL_dimage, float *grad2d, cudaStream_t st) {
     static int blocks_per_sm = 0;
     if (!blocks_per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_bwd<TW, TH>, TW * TH, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_bwd<TW, TH>, TW * TH / 2, 0) !=
                 cudaSuccess || blocks_per_sm < 1)
             blocks_per_sm = 1;
     }
     const int grid = min(num_sms() * blocks_per_sm, max(1, L.n_tiles));
     if (cudaMemsetAsync(b->counters + CNT_Q_BWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
-    k_render_bwd<TW, TH><<<grid, TW * TH, 0, st>>>(L, reinterpret_cast<const float4 *>(proj),
-                                                   reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
-                                                   b->tile_order, b->counters, image, dL_dimage,
-                                                   reinterpret_cast<float4 *>(grad2d));
+    k_render_bwd<TW, TH><<<grid, TW * TH / 2, 0, st>>>(L, reinterpret_cast<const float4 *>(proj),
+                                                       reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
+                                                       b->tile_order, b->counters, image, dL_dimage,
+                                                       reinterpret_cast<float4 *>(grad2d));
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
