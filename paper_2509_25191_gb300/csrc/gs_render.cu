@@ -21,7 +21,7 @@
 //   S_i = sum_{j>i} c_j alpha_j T_j + T_final bg = image - sum_{j<=i} c_j alpha_j T_j,
 // so that dL/dalpha_i = T_i (c_i . g) - (S_i . g) / (1 - alpha_i).
 // Per-Gaussian gradients (mean2D, 2D covariance, opacity, colour) are summed over a
-// warp with a shuffle reduce-scatter, over the block in shared memory, and
+// warp with a 12-shuffle reduce-scatter, over the block in shared memory, and
 // added to the per-slot grad2d record with one vector atomic per float4.
 #include "gs_common.cuh"
 
@@ -153,23 +153,40 @@ __device__ __forceinline__ unsigned int warp_mask(const float4 &xy, const float4
     return m;
 }
 
-// Sum 16 per-lane values over the warp by recursive halving: after the four
-// halving steps lane l holds partial sums of value index
-// idx(l) = 8 [l&16] + 4 [l&8] + 2 [l&4] + [l&2] over the 16 lanes that share
-// bit 0, and the last exchange completes the 32-lane sum. 16 shuffles instead
-// of 5 per value.
-__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane) {
+// Sum 9 per-lane values over the warp by recursive halving (a reduce-scatter):
+// each exchange keeps one part of the current values and sends the other,
+// splitting 9+1 -> 5, 5+1 -> 3, 3+1 -> 2, 2 -> 1 over lane bits 16, 8, 4, 2
+// (one zero pad where the count is odd), and the last exchange over bit 0
+// completes the 32-lane sum. Lane l then holds the sum of value
+// idx(l) = 5 [l&16] + 3 [l&8] + q(l), q(l) = 2 [l&4] + [l&2]; the value is
+// real (not a pad) for q <= 2, 3 [l&8] + q <= 4 and idx <= 8. 12 shuffles
+// instead of 5 per value.
+__device__ __forceinline__ float warp_reduce_scatter9(float (&v)[9], int lane) {
+    const unsigned int F = 0xffffffffu;
+    bool up = (lane & 16) != 0;
+    float a[5];
 #pragma unroll
-    for (int o = 16, h = 8; o >= 2; o >>= 1, h >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int k = 0; k < h; ++k) {
-            const float send = up ? v[k] : v[k + h];
-            const float keep = up ? v[k + h] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
+    for (int k = 0; k < 5; ++k) {
+        const float hi = k + 5 < 9 ? v[k + 5] : 0.f;
+        a[k] = (up ? hi : v[k]) + __shfl_xor_sync(F, up ? v[k] : hi, 16);
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    up = (lane & 8) != 0;
+    float b[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float hi = k + 3 < 5 ? a[k + 3] : 0.f;
+        b[k] = (up ? hi : a[k]) + __shfl_xor_sync(F, up ? a[k] : hi, 8);
+    }
+    up = (lane & 4) != 0;
+    float c[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float hi = k + 2 < 3 ? b[k + 2] : 0.f;
+        c[k] = (up ? hi : b[k]) + __shfl_xor_sync(F, up ? b[k] : hi, 4);
+    }
+    up = (lane & 2) != 0;
+    const float d = (up ? c[1] : c[0]) + __shfl_xor_sync(F, up ? c[0] : c[1], 2);
+    return d + __shfl_xor_sync(F, d, 1);
 }
 
 // add a thread's pair counts to the 64-bit counters at counters + at (one atomic per warp)
@@ -335,7 +352,7 @@ __device__ __forceinline__ int pixel_grad(const float4 &xy, const float4 &con, c
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH / 2) k_render_bwd(const Launch L, const float4 *__restrict__ proj,
+__global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, const float4 *__restrict__ proj,
                                                             const int2 *__restrict__ ranges,
                                                             const unsigned int *__restrict__ ids,
                                                             const int *__restrict__ order, int *__restrict__ counters,
@@ -350,7 +367,10 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_bwd(const Launch L, cons
     if (counters[CNT_ABORT]) return;
     const int lane = threadIdx.x & 31;
     const unsigned int wbit = 1u << (threadIdx.x >> 5);
-    const int red_idx = ((lane & 16) ? 8 : 0) + ((lane & 8) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
+    const int red_q = ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
+    const int red_p = ((lane & 8) ? 3 : 0) + red_q;
+    const int red_idx = ((lane & 16) ? 5 : 0) + red_p;
+    const bool red_own = !(lane & 1) && red_q <= 2 && red_p <= 4 && red_idx <= 8;   // lanes holding a real sum
     for (int k = threadIdx.x; k < NB; k += BS)
         for (int c = 0; c < 9; ++c) s_g[k][c] = 0.f;
     for (;;) {
@@ -387,9 +407,9 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_bwd(const Launch L, cons
             for (int k = 0; k < nb; ++k) {
                 if (!(s_mask[k] & wbit)) continue;   // warp-uniform: no lane of this warp can be hit
                 // gradient of this thread's pixels w.r.t. (x, y, a, b, c, o, r, g, b) of Gaussian k
-                float gv[16];
+                float gv[9];
 #pragma unroll
-                for (int c = 0; c < 16; ++c) gv[c] = 0.f;
+                for (int c = 0; c < 9; ++c) gv[c] = 0.f;
                 bool hit = false;
                 const float4 xy = s_xy[k], con = s_con[k], c = s_rgb[k];
 #pragma unroll
@@ -403,8 +423,8 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_bwd(const Launch L, cons
                     n_comp += res == 2;
                 }
                 if (__any_sync(0xffffffffu, hit)) {
-                    const float sum = warp_reduce_scatter16(gv, lane);
-                    if (!(lane & 1) && red_idx < 9) atomicAdd(&s_g[k][red_idx], sum);
+                    const float sum = warp_reduce_scatter9(gv, lane);
+                    if (red_own) atomicAdd(&s_g[k][red_idx], sum);
                 }
             }
             __syncthreads();
