@@ -20,11 +20,11 @@
 
 namespace gsk {
 
-constexpr int PB_THREADS = 128;   // 168 registers: 3 blocks per SM, no spills
+constexpr int PB_THREADS = 128;   // 128 registers and 38 KB shared: 4 blocks per SM, no spills
 constexpr int PB_WARPS = PB_THREADS / 32;
 
 template <int DEG, bool GAUSS>
-__global__ void __launch_bounds__(PB_THREADS, 3) k_project_bwd(
+__global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
     const Launch L, const float *__restrict__ means, const float *__restrict__ log_scales,
     const float *__restrict__ quats, const float *__restrict__ logits, const float *__restrict__ sh,
     const float *__restrict__ viewmats, const float *__restrict__ intr, const float4 *__restrict__ proj,
@@ -32,7 +32,12 @@ __global__ void __launch_bounds__(PB_THREADS, 3) k_project_bwd(
     float *__restrict__ g_quats, float *__restrict__ g_logits, float *__restrict__ g_sh,
     float *__restrict__ pose_partials) {
     constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int GP = 3 * K + 1;   // odd row pitch: conflict-free column access
     __shared__ float s_pose[PB_WARPS][GS_MAX_VIEWS][12];
+    // per-thread SH-coefficient gradients, summed over views here and written
+    // out by the whole block with coalesced stores
+    __shared__ float s_gf[GAUSS ? PB_THREADS * GP : 1];
+    __shared__ long long s_row[GAUSS ? PB_THREADS : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < PB_WARPS * GS_MAX_VIEWS * 12; i += PB_THREADS) (&s_pose[0][0][0])[i] = 0.f;
     __syncthreads();
@@ -76,9 +81,12 @@ __global__ void __launch_bounds__(PB_THREADS, 3) k_project_bwd(
         // accumulators over views
         float gm[3] = {0.f, 0.f, 0.f}, go = 0.f;
         float GS00 = 0, GS01 = 0, GS02 = 0, GS11 = 0, GS12 = 0, GS22 = 0;   // full-matrix entries, symmetric
-        float gf[3 * K];
+        float *gf = s_gf + (GAUSS ? threadIdx.x * GP : 0);
+        if (GAUSS) {
 #pragma unroll
-        for (int k = 0; k < 3 * K; ++k) gf[k] = 0.f;
+            for (int k = 0; k < 3 * K; ++k) gf[k] = 0.f;
+            s_row[threadIdx.x] = valid ? i : -1;
+        }
 
         for (int v = wvb; v < wve; ++v) {
             float pg[12];
@@ -141,10 +149,26 @@ __global__ void __launch_bounds__(PB_THREADS, 3) k_project_bwd(
                         sh_basis<DEG>(d0, d1, d2, Yb);
                         float gY[16];
 #pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            gY[k] = __ldg(f + 3 * k) * graw[0] + __ldg(f + 3 * k + 1) * graw[1] +
-                                    __ldg(f + 3 * k + 2) * graw[2];
-                            if (GAUSS) {
+                        for (int k = 0; k < K; ++k) gY[k] = 0.f;
+                        if (DEG == 1 || DEG == 3) {
+                            // 3K floats = 3K/4 float4 (rows are 16-byte aligned for these degrees)
+                            const float4 *f4 = reinterpret_cast<const float4 *>(f);
+#pragma unroll
+                            for (int j = 0; j < 3 * K / 4; ++j) {
+                                const float4 q4 = __ldg(f4 + j);
+                                const float fv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) gY[(4 * j + e) / 3] += fv[e] * graw[(4 * j + e) % 3];
+                            }
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < K; ++k)
+                                gY[k] = __ldg(f + 3 * k) * graw[0] + __ldg(f + 3 * k + 1) * graw[1] +
+                                        __ldg(f + 3 * k + 2) * graw[2];
+                        }
+                        if (GAUSS) {
+#pragma unroll
+                            for (int k = 0; k < K; ++k) {
                                 gf[3 * k] += Yb[k] * graw[0];
                                 gf[3 * k + 1] += Yb[k] * graw[1];
                                 gf[3 * k + 2] += Yb[k] * graw[2];
@@ -273,8 +297,16 @@ __global__ void __launch_bounds__(PB_THREADS, 3) k_project_bwd(
             g_means[3 * i + 1] = gm[1];
             g_means[3 * i + 2] = gm[2];
             g_logits[i] = go * opac * (1.f - opac);
-#pragma unroll
-            for (int k = 0; k < 3 * K; ++k) g_sh[(long long)3 * K * i + k] = gf[k];
+        }
+        if (GAUSS) {
+            // the block's SH-coefficient gradients: row r goes to Gaussian s_row[r]
+            __syncthreads();
+            for (int e = threadIdx.x; e < PB_THREADS * 3 * K; e += PB_THREADS) {
+                const int r = e / (3 * K), c = e % (3 * K);
+                const long long row = s_row[r];
+                if (row >= 0) g_sh[row * 3 * K + c] = s_gf[r * GP + c];
+            }
+            __syncthreads();
         }
     }
     __syncthreads();
@@ -289,7 +321,7 @@ __global__ void __launch_bounds__(PB_THREADS, 3) k_project_bwd(
 
 int pose_blocks(long long n) {
     long long b = (n + PB_THREADS - 1) / PB_THREADS;
-    const long long cap = 3LL * num_sms();   // one wave of resident blocks
+    const long long cap = 4LL * num_sms();   // one wave of resident blocks
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
