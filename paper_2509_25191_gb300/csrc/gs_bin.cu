@@ -17,7 +17,7 @@
 //   k_bin_scatter  writes keys: one global reservation per (block, tile),
 //                  placement inside it by shared-memory atomics
 //   k_sort_tiles   persistent, largest tiles first; radix sort on chip
-//                  (chunks + merge path for tiles above 4096 instances)
+//                  (chunks + merge path for tiles above 2048 instances)
 #include "gs_common.cuh"
 
 namespace gsk {
@@ -232,9 +232,9 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, con
 // result is the unique (depth, slot) order. Tiles longer than SORT_CAP
 // are sorted in chunks and merged (merge path) through keys_tmp.
 // ---------------------------------------------------------------------------
-constexpr int SORT_THREADS = 512;
+constexpr int SORT_THREADS = 256;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr int SORT_CAP = 4096;
+constexpr int SORT_CAP = 2048;      // ~42 KB of shared memory: 5 blocks per SM
 constexpr int SORT_SEG_MIN = 128;   // at least this many keys per active warp
 
 struct SortSmem {
@@ -466,7 +466,7 @@ int launch_bin_sort(const Launch &L, const float *proj, const gs_bins *b, int32_
             return GS_ERR_CUDA;
         smem_set = 1;
     }
-    k_sort_tiles<<<2 * num_sms(), SORT_THREADS, smem, st>>>(
+    k_sort_tiles<<<5 * num_sms(), SORT_THREADS, smem, st>>>(
         L, reinterpret_cast<const int2 *>(b->tile_ranges), b->tile_order,
         reinterpret_cast<unsigned long long *>(b->keys), reinterpret_cast<unsigned long long *>(b->keys_tmp),
         b->ids, b->counters);
