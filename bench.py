@@ -56,11 +56,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--tile", default="auto", help="tile shape WxH, or auto (the project's autotuner)")
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--extra", action="store_true",
+                    help="also time the uneven multi-scene batch and the dense-view joint pose step")
     ap.add_argument("--ref-fraction", type=float, default=1.0 / 16.0,
                     help="pixel fraction of each reference-arm step")
     return ap.parse_args()
@@ -174,13 +176,19 @@ def run_native(args, rank, world, local_rank):
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    tile = tuple(int(x) for x in args.tile.split("x"))
     sc, vw = workload(args.n)
     g = _lib.Gaussians.from_scene(sc, dev)
     views = _lib.Views.from_synth(vw, dev)
     P = views.pixels
     rng = np.random.default_rng(1234)
     target = torch.as_tensor(rng.uniform(0, 1, views.num_image_floats()).astype(np.float32), device=dev)
+    tuning = None
+    if args.tile == "auto":
+        from paper_2509_25191_gb300.tune import autotune
+        tile, ms = autotune(g, views, target)
+        tuning = {"chosen": list(tile), "ms_per_step": {f"{t[0]}x{t[1]}": round(v, 4) for t, v in ms.items()}}
+    else:
+        tile = tuple(int(x) for x in args.tile.split("x"))
 
     step = GraphStep(g, views, target, tile=tile)
     rast, cfg, bins = step.rast, step.cfg, step.bins
@@ -283,7 +291,8 @@ def run_native(args, rank, world, local_rank):
         hbm = peaks["hbm_gbs"]
         roof = {"kernel": names[top], "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                 "traffic": None}
-    batched = None if args.no_batched else batched_vs_plain(dev, tile)
+    batched = None if args.no_batched else batched_vs_plain(dev, tile if args.tile != "auto" else "auto")
+    extra = {"uneven_scenes": run_uneven(dev), "dense_pose_step": run_dense(dev)} if args.extra else None
     step_bytes = algorithmic_bytes(g.n, g.sh_degree, views.num_slots(), n_inst, P, views.num_tiles(cfg))
     hbm_frac_step = step_bytes / (ms * 1e-3) / (peaks["hbm_gbs"] * 1e9)
 
@@ -299,8 +308,10 @@ def run_native(args, rank, world, local_rank):
         "step_hbm_roofline": {"algorithmic_bytes": int(step_bytes), "frac": round(hbm_frac_step, 4),
                               "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src},
         "stages_ms": {n: round(float(t), 4) for n, t in zip(names, stage_ms)},
+        "autotune": tuning,
         "clocks": clocks,
         "batched_vs_plain": batched,
+        "other_workloads": extra,
         "e2e": e2e,
         "gpu_launches": kernels_per_step * args.steps,
     }
@@ -320,6 +331,9 @@ def batched_vs_plain(dev, tile, steps=20, plain_steps=5):
     views = _lib.Views.from_synth(vw, dev)
     rng = np.random.default_rng(99)
     target = torch.as_tensor(rng.uniform(0, 1, views.num_image_floats()).astype(np.float32), device=dev)
+    if tile == "auto":
+        from paper_2509_25191_gb300.tune import autotune
+        tile, _ = autotune(g, views, target)
     gs = GraphStep(g, views, target, tile=tile)
     ps = PlainStep(g, views, target, tile=tile)
     for _ in range(3):
@@ -343,8 +357,110 @@ def batched_vs_plain(dev, tile, steps=20, plain_steps=5):
     px = views.pixels
     return {"workload": "16 views 979x546 on a radius-5 orbit, 500K clustered SH3 Gaussians (seed 0), "
                         "fwd+L1+bwd+pose", "batched_ms": round(tb, 4), "plain_ms": round(tp, 4),
-            "batched_mpix_s": round(px / tb / 1e3, 2), "plain_mpix_s": round(px / tp / 1e3, 2),
+            "tile": list(tile), "batched_mpix_s": round(px / tb / 1e3, 2), "plain_mpix_s": round(px / tp / 1e3, 2),
             "ratio": round(tp / tb, 3), "steps": steps, "plain_steps": plain_steps}
+
+
+def _time_replays(step, steps):
+    import torch
+    for _ in range(3):
+        step.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        step.replay()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_uneven(dev, steps=10):
+    """8 scenes of 0.2M..3M clustered SH3 Gaussians (seeds 1-8), 4 views each
+    at mixed resolutions: all 32 views in one captured step."""
+    import torch
+
+    from paper_2509_25191_gb300 import _lib, synth
+    from paper_2509_25191_gb300.step import GraphStep
+    from paper_2509_25191_gb300.tune import autotune
+    sc, vw = synth.uneven_scenes()
+    g = _lib.Gaussians.from_scene(sc, dev)
+    views = _lib.Views.from_synth(vw, dev)
+    target = torch.rand(views.num_image_floats(), device=dev, generator=torch.Generator(dev).manual_seed(5))
+    tile, _ = autotune(g, views, target, reps=3)
+    step = GraphStep(g, views, target, tile=tile)
+    ms = _time_replays(step, steps)
+    step.rast.check_status()
+    return {"workload": "8 scenes 0.2M-3M SH3 Gaussians (11.7M), 32 views at mixed resolutions, fwd+L1+bwd+pose",
+            "gaussians": g.n, "views": views.n, "pixels_per_step": views.pixels, "tile": list(tile),
+            "instances": int(step.bins.counters[0].item()), "ms_per_step": round(ms, 3),
+            "mpix_s": round(views.pixels / ms / 1e3, 2)}
+
+
+def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
+    """Joint pose + 3DGS step: 6M SH3 Gaussians, 300 hemisphere views
+    1600x1066 with jittered poses; per step a minibatch of 8 views, 6D +
+    translation pose residuals composed in torch, the rasterizer step
+    (fwd, L1 against targets rendered from the true poses, full backward)
+    replayed from one CUDA graph, and the residual gradients by autograd."""
+    import torch
+
+    from paper_2509_25191_gb300 import _lib, pose, synth
+    from paper_2509_25191_gb300.autograd import Rasterizer
+    from paper_2509_25191_gb300.step import GraphStep
+    sc, true_v, noisy_v = synth.dense_hemisphere(0, n, n_views)
+    g = _lib.Gaussians.from_scene(sc, dev)
+    W, H = int(true_v.width[0]), int(true_v.height[0])
+    true_vm = torch.as_tensor(true_v.viewmats, device=dev)
+    noisy_vm = torch.as_tensor(noisy_v.viewmats, device=dev)
+    intr = torch.as_tensor(true_v.intrinsics, device=dev)
+    # targets from the unperturbed poses, rendered once by the validated forward
+    targets = torch.empty(n_views, 3 * W * H, device=dev)
+    rast = Rasterizer()
+    for v0 in range(0, n_views, batch):
+        ids = list(range(v0, min(n_views, v0 + batch)))
+        vv = _lib.Views(true_vm[ids].contiguous(), intr[ids].contiguous(), [W] * len(ids), [H] * len(ids),
+                        [0] * len(ids), [n] * len(ids))
+        img, _ = rast.forward(g, vv)
+        targets[ids] = img.view(len(ids), -1)
+    del rast
+    dr = pose.identity_6d(n_views, device=dev).requires_grad_(True)
+    dt = torch.zeros(n_views, 3, device=dev, requires_grad=True)
+    vm_static = torch.empty(batch, 12, device=dev)
+    tgt_static = torch.empty(batch * 3 * W * H, device=dev)
+    views = _lib.Views(vm_static, intr[:batch].contiguous(), [W] * batch, [H] * batch, [0] * batch, [n] * batch)
+
+    def load(k):
+        ids = torch.as_tensor(synth.minibatch(k, n_views, batch), device=dev)
+        vm = pose.apply_residual(noisy_vm[ids], dr[ids], dt[ids])
+        with torch.no_grad():
+            vm_static.copy_(vm)
+            tgt_static.copy_(targets[ids].reshape(-1))
+        return vm
+
+    vm = load(0)
+    step = GraphStep(g, views, tgt_static)
+    for k in range(3):
+        vm = load(k)
+        step.replay()
+        vm.backward(step.dviewmat)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for k in range(steps):
+        vm = load(100 + k)
+        step.replay()
+        vm.backward(step.dviewmat)        # chain dL/d(R,t) to the 6D and translation residuals
+    b.record()
+    torch.cuda.synchronize()
+    if step.check():
+        raise RuntimeError("capacity overflow during the dense step")
+    ms = a.elapsed_time(b) / steps
+    px = batch * W * H
+    return {"workload": "6M SH3 Gaussians, 300 jittered hemisphere views 1600x1066, minibatch 8, L1 vs targets, "
+                        "backward to Gaussians and poses (6D + translation residuals)",
+            "ms_per_step": round(ms, 3), "mpix_s": round(px / ms / 1e3, 2), "pixels_per_step": px,
+            "pose_grad_norm": round(float(dr.grad.norm()), 6), "instances": int(step.bins.counters[0].item())}
 
 
 # ---------------------------------------------------------------------------
