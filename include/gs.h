@@ -219,6 +219,28 @@ int gs_pose_grad(const gs_views *views, const float *pose_partials, int n_blocks
 int gs_l1_loss(const float *image, const float *target, int64_t count, float *loss,
                float *dL_dimage, void *stream);
 
+/* SGLD update with an Adam direction (paper Eq. 1, the MCMC-3DGS update the
+ * method trains with): for every group,
+ *   m <- b1 m + (1-b1) g,  v <- b2 v + (1-b2) g^2,
+ *   p <- p - lr * (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps),
+ * and, for group noise_group only, p <- p + noise_scale * noise (the
+ * exploration term lambda_noise * eps; noise is drawn by the caller, DEVICE
+ * [count of that group], or NULL for none). All arrays DEVICE float32,
+ * updated in place; step >= 1 counts Adam steps; beta1, beta2, eps are
+ * doubles so that 1 - beta is formed exactly before rounding. One launch for
+ * all groups (at most GS_MAX_ADAM_GROUPS). */
+#define GS_MAX_ADAM_GROUPS 8
+typedef struct gs_adam_group {
+    float *param;
+    const float *grad;
+    float *exp_avg;
+    float *exp_avg_sq;
+    int64_t count;
+    float lr;
+} gs_adam_group;
+int gs_sgld_adam_step(const gs_adam_group *groups, int n_groups, int step, double beta1, double beta2, double eps,
+                      const float *noise, float noise_scale, int noise_group, void *stream);
+
 /* Allocation-free variant of gs_project_bwd followed by gs_pose_grad (the
  * paper has no counterpart: this exists for callers, not for the method).
  *

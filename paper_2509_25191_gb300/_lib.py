@@ -24,7 +24,8 @@ GS_NUM_COUNTERS = 16
 EXPORTED = ["gs_config_default", "gs_num_slots", "gs_slot_base", "gs_num_tiles", "gs_tile_base",
             "gs_num_image_floats", "gs_pixel_base", "gs_pose_blocks", "gs_project", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version",
-            "gs_project_bwd_noalloc"]
+            "gs_project_bwd_noalloc", "gs_sgld_adam_step"]
+GS_MAX_ADAM_GROUPS = 8
 
 
 class GsError(RuntimeError):
@@ -56,6 +57,11 @@ class gs_bins(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int64), ("tile_ranges", ctypes.c_void_p), ("keys", ctypes.c_void_p),
                 ("ids", ctypes.c_void_p), ("keys_tmp", ctypes.c_void_p), ("tile_order", ctypes.c_void_p),
                 ("tile_scratch", ctypes.c_void_p), ("counters", ctypes.c_void_p)]
+
+
+class gs_adam_group(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("exp_avg", ctypes.c_void_p),
+                ("exp_avg_sq", ctypes.c_void_p), ("count", ctypes.c_int64), ("lr", ctypes.c_float)]
 
 
 class gs_grads(ctypes.Structure):
@@ -291,6 +297,19 @@ def gs_project_bwd_noalloc(g: Gaussians, views: Views, cfg: gs_config, proj, gra
                                          _ptr(proj), _ptr(grads.grad2d), ctypes.byref(grads.c()),
                                          int(bool(want_gaussian_grads)), _ptr(dL_dviewmat), _ptr(dL_dtwist),
                                          _ptr(status), _stream(stream)), "gs_project_bwd_noalloc")
+
+
+def gs_sgld_adam_step(groups, step, beta1=0.9, beta2=0.999, eps=1e-15, noise=None, noise_scale=0.0, noise_group=0,
+                      stream=None):
+    """Eq. 1 update in one launch. groups: list of (param, grad, exp_avg,
+    exp_avg_sq, lr) CUDA float32 tensors (updated in place)."""
+    arr = (gs_adam_group * len(groups))()
+    for k, (p, g, m, v, lr) in enumerate(groups):
+        assert p.numel() == g.numel() == m.numel() == v.numel()
+        arr[k] = gs_adam_group(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), float(lr))
+    _check(load().gs_sgld_adam_step(arr, len(groups), int(step), ctypes.c_double(beta1), ctypes.c_double(beta2),
+                                    ctypes.c_double(eps), _ptr(noise), ctypes.c_float(noise_scale), int(noise_group),
+                                    _stream(stream)), "gs_sgld_adam_step")
 
 
 def pair_counts(bins: Bins):

@@ -19,6 +19,8 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
 int launch_pose_reduce(int n_views, const float *partials, int nblk, const float *viewmats, float *out_rt,
                        float *out_twist, cudaStream_t st);
 int launch_l1(const float *image, const float *target, long long n, float *loss, float *grad, cudaStream_t st);
+int launch_adam_sgld(const gs_adam_group *groups, int n_groups, int step, double beta1, double beta2, double eps,
+                     const float *noise, float noise_scale, int noise_group, cudaStream_t st);
 int pose_blocks(long long n);
 
 int num_sms() {
@@ -285,6 +287,19 @@ int gs_l1_loss(const float *image, const float *target, int64_t count, float *lo
                void *stream) {
     if (count < 0 || !loss || (count > 0 && (!image || !target || !dL_dimage))) return GS_ERR_ARG;
     return launch_l1(image, target, count, loss, dL_dimage, (cudaStream_t)stream);
+}
+
+int gs_sgld_adam_step(const gs_adam_group *groups, int n_groups, int step, double beta1, double beta2, double eps,
+                      const float *noise, float noise_scale, int noise_group, void *stream) {
+    if (!groups || n_groups < 1 || n_groups > GS_MAX_ADAM_GROUPS || step < 1) return GS_ERR_ARG;
+    if (!(beta1 >= 0.0 && beta1 < 1.0 && beta2 >= 0.0 && beta2 < 1.0 && eps >= 0.0)) return GS_ERR_ARG;
+    for (int k = 0; k < n_groups; ++k) {
+        const gs_adam_group &g = groups[k];
+        if (g.count < 0 || (g.count > 0 && (!g.param || !g.grad || !g.exp_avg || !g.exp_avg_sq))) return GS_ERR_ARG;
+    }
+    if (noise && (noise_group < 0 || noise_group >= n_groups)) return GS_ERR_ARG;
+    return launch_adam_sgld(groups, n_groups, step, beta1, beta2, eps, noise, noise_scale, noise_group,
+                            (cudaStream_t)stream);
 }
 
 const char *gs_error_string(int code) {
