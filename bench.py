@@ -291,6 +291,11 @@ def run_native(args, rank, world, local_rank):
         hbm = peaks["hbm_gbs"]
         roof = {"kernel": names[top], "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                 "traffic": None}
+    # test-time pose tuning (Gaussians frozen): the same step with the backward to the pose only
+    pstep = GraphStep(g, views, target, tile=tile, want_gaussian_grads=False)
+    pose_only = {"ms_per_step": round(_time_replays(pstep, 50), 4)}
+    pose_only["mpix_s"] = round(P / pose_only["ms_per_step"] / 1e3, 2)
+    del pstep
     batched = None if args.no_batched else batched_vs_plain(dev, tile if args.tile != "auto" else "auto")
     extra = {"uneven_scenes": run_uneven(dev), "dense_pose_step": run_dense(dev)} if args.extra else None
     step_bytes = algorithmic_bytes(g.n, g.sh_degree, views.num_slots(), n_inst, P, views.num_tiles(cfg))
@@ -310,6 +315,7 @@ def run_native(args, rank, world, local_rank):
         "stages_ms": {n: round(float(t), 4) for n, t in zip(names, stage_ms)},
         "autotune": tuning,
         "clocks": clocks,
+        "pose_only_step": pose_only,
         "batched_vs_plain": batched,
         "other_workloads": extra,
         "e2e": e2e,
