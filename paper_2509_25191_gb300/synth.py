@@ -16,6 +16,11 @@ workloads:
                            mixed resolutions.
 * ``dense_hemisphere``   : 6M Gaussians, 300 views 1600x1066 on a hemisphere,
                            with jittered (1 degree, 1 %) initial poses.
+* ``ga_cameras`` / ``ga_matches`` : cameras and keypoint correspondences for
+                           the global alignment: 300 hemisphere cameras with
+                           jittered initial estimates, up to 4,096 noisy
+                           matches per image pair, a fraction of them outliers
+                           (stand-in for a feature matcher's output).
 
 Conventions (shared by every consumer of these arrays):
 
@@ -308,3 +313,75 @@ def minibatch(step: int, n_views: int, batch: int = 8) -> np.ndarray:
     """View ids of training step ``step``: ``batch`` distinct views, drawn with
     ``default_rng(step)``."""
     return np.random.default_rng(step).choice(n_views, batch, replace=False)
+
+
+@dataclasses.dataclass
+class Matches:
+    """Correspondences of a list of image pairs: the matches of pair m are
+    rows ``offsets[m]:offsets[m+1]`` of ``matches`` = (x, y, x', y'), x in the
+    pair's first image and x' in its second, in pixels."""
+    offsets: np.ndarray   # int64 [M+1]
+    matches: np.ndarray   # float32 [K,4]
+    inlier: np.ndarray    # bool [K]
+
+
+def ga_cameras(seed=0, n_views=300, width=1600, height=1066, focal=1000.0, rot_deg=1.0, trans_frac=0.01,
+               focal_frac=0.02):
+    """True cameras on the radius-5 hemisphere and initial estimates of them
+    (the role of a feed-forward model's prediction): every pose jittered by
+    exactly ``rot_deg`` and ``trans_frac``*|t|, every focal length scaled by
+    1 + U(-focal_frac, focal_frac). Returns (true_viewmats, true_intrinsics,
+    init_viewmats, init_intrinsics), all float32."""
+    mats = hemisphere_viewmats(n_views)
+    intr = np.tile(np.array([focal, focal, width / 2.0, height / 2.0]), (n_views, 1))
+    init_mats = jitter_viewmats(mats, seed, rot_deg, trans_frac)
+    rng = np.random.default_rng(seed + 1)
+    init_intr = intr.copy()
+    init_intr[:, :2] *= (1.0 + rng.uniform(-focal_frac, focal_frac, (n_views, 1)))
+    f32 = lambda a: np.ascontiguousarray(a, np.float32)
+    return f32(mats.reshape(-1, 12)), f32(intr), f32(init_mats), f32(init_intr)
+
+
+def ga_points(seed=0, n=20_000, radius=2.0):
+    """Scene points uniform in the ball of the given radius at the origin."""
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return d * radius * rng.uniform(0.0, 1.0, (n, 1)) ** (1.0 / 3.0)
+
+
+def ga_matches(seed, points, intrinsics, viewmats, pairs, width, height, max_matches=4096, noise_px=0.5,
+               outlier_frac=0.15) -> Matches:
+    """For each pair (i, j): up to ``max_matches`` points visible in both TRUE
+    cameras (in front, inside the image), observed with N(0, noise_px^2)
+    pixel noise in both images; a fraction ``outlier_frac`` of them has x'
+    replaced by a uniform position in image j."""
+    rng = np.random.default_rng(seed)
+    vm = np.asarray(viewmats, np.float64).reshape(-1, 12)
+    K = np.asarray(intrinsics, np.float64).reshape(-1, 4)
+    P = np.asarray(points, np.float64)
+    uv, vis = [], []
+    for n in range(vm.shape[0]):
+        Xc = P @ vm[n, :9].reshape(3, 3).T + vm[n, 9:]
+        z = Xc[:, 2]
+        zs = np.where(z > 0.1, z, 1.0)
+        u = K[n, 0] * Xc[:, 0] / zs + K[n, 2]
+        v = K[n, 1] * Xc[:, 1] / zs + K[n, 3]
+        uv.append(np.stack([u, v], 1))
+        vis.append((z > 0.1) & (u >= 0) & (u < width) & (v >= 0) & (v < height))
+    offsets = [0]
+    chunks, inl = [], []
+    for i, j in np.asarray(pairs).reshape(-1, 2):
+        both = np.nonzero(vis[i] & vis[j])[0]
+        k = min(max_matches, len(both))
+        sel = rng.choice(both, k, replace=False) if k else both[:0]
+        m = np.concatenate([uv[i][sel], uv[j][sel]], 1) + rng.normal(0.0, noise_px, (k, 4))
+        out = rng.random(k) < outlier_frac
+        m[out, 2] = rng.uniform(0, width, int(out.sum()))
+        m[out, 3] = rng.uniform(0, height, int(out.sum()))
+        chunks.append(m)
+        inl.append(~out)
+        offsets.append(offsets[-1] + k)
+    matches = np.concatenate(chunks, 0) if chunks else np.zeros((0, 4))
+    inlier = np.concatenate(inl) if inl else np.zeros(0, bool)
+    return Matches(np.asarray(offsets, np.int64), np.ascontiguousarray(matches, np.float32), inlier)
