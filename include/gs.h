@@ -241,6 +241,86 @@ typedef struct gs_adam_group {
 int gs_sgld_adam_step(const gs_adam_group *groups, int n_groups, int step, double beta1, double beta2, double eps,
                       const float *noise, float noise_scale, int noise_group, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Camera global alignment (paper Section 3.3, Eqs. 2-4).
+ *
+ * Cameras n = 0..n_cams-1: intrinsics (fx, fy, cx, cy) and world-to-camera
+ * extrinsics (R row-major, t) as in gs_views. A pair (i, j) holds keypoint
+ * matches (x, y, x', y'): x in image i, x' in image j, in pixels. With
+ * R_ij = R_j R_i^T, t_ij = t_j - R_ij t_i and F = K_j^-T [t_ij]x R_ij K_i^-1
+ * (Eq. 2) a match's epipolar distance is e = |x'^T F x| / ||(F x)_{1,2}||,
+ * the distance of x' to the epipolar line of x in pixels (0, with no
+ * gradient, where the line is undefined). The loss is
+ * L = sum_k w_k e_k / sum_k w_k over all matches of all pairs (Eq. 2).
+ * ---------------------------------------------------------------------- */
+#define GS_GA_MAX_CAMS 8192
+#define GS_GA_PAIR_FLOATS 12   /* per-pair partial sums */
+#define GS_GA_MAX_BINS 16384
+
+typedef struct gs_ga_problem {
+    int n_cams;
+    const float *intrinsics;        /* DEVICE [n_cams,4] fx, fy, cx, cy */
+    const float *viewmats;          /* DEVICE [n_cams,12] R row-major, t */
+    int64_t n_pairs;
+    const int32_t *pairs;           /* DEVICE [n_pairs,2] (i, j), i != j, no pair listed twice */
+    const int64_t *match_offsets;   /* DEVICE [n_pairs+1]: pair m owns matches offsets[m]..offsets[m+1]-1 */
+    int64_t n_matches;
+    const float *matches;           /* DEVICE [n_matches,4] (x, y, x', y'), 16-byte aligned */
+    const float *weights;           /* DEVICE [n_matches] w_k, or NULL for all 1 */
+} gs_ga_problem;
+
+/* Candidate pairs (Section 3.3; threshold 30 degrees in Section 4.1): every
+ * (i, j), i < j, whose viewing directions (third rows of R_i and R_j) are
+ * less than max_angle_deg apart, i.e. d_i . d_j > cos(max_angle_deg) with
+ * the dot product rounded to float32 after each operation and the cosine
+ * formed in double, then rounded. Pairs are written in row-major order
+ * (ascending i, then j) to pairs (DEVICE int32 [capacity,2]); the number
+ * found goes to n_pairs_out (DEVICE int64 [1]). If it exceeds capacity,
+ * status = {GS_ERR_CAPACITY, count} and no pair is written. One block;
+ * n_cams <= GS_GA_MAX_CAMS. */
+int gs_ga_select_pairs(const float *viewmats, int n_cams, double max_angle_deg, int32_t *pairs, int64_t capacity,
+                       int64_t *n_pairs_out, int32_t *status, void *stream);
+
+/* Camera -> pair incidence lists for the gradient reduction: cam_offsets
+ * (DEVICE int32 [n_cams+1]) and cam_pairs (DEVICE int32 [2*n_pairs]), the
+ * entries of camera n being cam_pairs[cam_offsets[n]..cam_offsets[n+1]-1]
+ * = 2*m + (1 if n is the pair's second camera), sorted ascending (the
+ * reduction order is fixed, so gradients are bit-reproducible). A camera in
+ * more than GS_GA_MAX_CAMS pairs sets status = {GS_ERR_ARG, camera}. */
+int gs_ga_incidence(const int32_t *pairs, int64_t n_pairs, int n_cams, int32_t *cam_offsets, int32_t *cam_pairs,
+                    int32_t *status, void *stream);
+
+/* Epipolar distances, loss and camera gradients (Eq. 2). dist (DEVICE
+ * [n_matches]) receives every e_k, or NULL. pair_sums is caller scratch
+ * (DEVICE float [n_pairs, GS_GA_PAIR_FLOATS]). loss (DEVICE [1]) receives L
+ * (0 if the weights sum to 0). If d_intrinsics (DEVICE [n_cams,4]) and
+ * d_viewmats (DEVICE [n_cams,12]) are both non-NULL they are overwritten
+ * with dL/d(fx, fy, cx, cy) and dL/d(R, t) of every camera (zero for a
+ * camera in no pair); that needs the incidence lists of gs_ga_incidence.
+ * The distances are computed in float32 in normalised coordinates
+ * (K^-1 x), the gradient sums in float32 per pair and reduced per camera in
+ * a fixed order. A pair whose camera index or match range is out of
+ * bounds contributes nothing and sets status = {GS_ERR_ARG, pair} (status
+ * may be NULL). No allocation, no synchronisation: capturable. */
+int gs_ga_epipolar(const gs_ga_problem *p, float *dist, float *pair_sums, const int32_t *cam_offsets,
+                   const int32_t *cam_pairs, float *loss, float *d_intrinsics, float *d_viewmats, int32_t *status,
+                   void *stream);
+
+/* Adaptive weights (Eq. 3) and the median (Eq. 4) of n distances dist
+ * (DEVICE, finite, >= 0): a histogram with n_bins equal bins on
+ * [0, max e], bin b = min(n_bins - 1, floor(e * (n_bins / max e))) with the
+ * quotient and the product rounded to float32 (all in bin 0 if max e is 0);
+ * counts (DEVICE uint32 [n_bins]) receives it; weights (DEVICE [n]) gets
+ * w_k = (f(e_k) / mean_k f(e_k))^alpha with f the histogram density, which
+ * equals (n c_b / sum_b c_b^2)^alpha (formed in double per bin); stats
+ * (DEVICE float [4]) = {max e, lower middle, upper middle order statistic
+ * (equal for odd n; the median is their mean), 0}. scratch: DEVICE, at
+ * least gs_ga_weights_scratch_bytes(n_bins) bytes. 1 <= n_bins <=
+ * GS_GA_MAX_BINS, alpha >= 0; n = 0 writes stats = 0 and nothing else. */
+size_t gs_ga_weights_scratch_bytes(int n_bins);
+int gs_ga_weights(const float *dist, int64_t n, int n_bins, double alpha, uint32_t *counts, float *weights,
+                  float *stats, void *scratch, void *stream);
+
 /* Allocation-free variant of gs_project_bwd followed by gs_pose_grad (the
  * paper has no counterpart: this exists for callers, not for the method).
  *

@@ -24,7 +24,11 @@ GS_NUM_COUNTERS = 16
 EXPORTED = ["gs_config_default", "gs_num_slots", "gs_slot_base", "gs_num_tiles", "gs_tile_base",
             "gs_num_image_floats", "gs_pixel_base", "gs_pose_blocks", "gs_project", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version",
-            "gs_project_bwd_noalloc", "gs_sgld_adam_step"]
+            "gs_project_bwd_noalloc", "gs_sgld_adam_step", "gs_ga_select_pairs", "gs_ga_incidence",
+            "gs_ga_epipolar", "gs_ga_weights_scratch_bytes", "gs_ga_weights"]
+GS_GA_MAX_CAMS = 8192
+GS_GA_PAIR_FLOATS = 12
+GS_GA_MAX_BINS = 16384
 GS_MAX_ADAM_GROUPS = 8
 
 
@@ -64,6 +68,12 @@ class gs_adam_group(ctypes.Structure):
                 ("exp_avg_sq", ctypes.c_void_p), ("count", ctypes.c_int64), ("lr", ctypes.c_float)]
 
 
+class gs_ga_problem(ctypes.Structure):
+    _fields_ = [("n_cams", ctypes.c_int), ("intrinsics", ctypes.c_void_p), ("viewmats", ctypes.c_void_p),
+                ("n_pairs", ctypes.c_int64), ("pairs", ctypes.c_void_p), ("match_offsets", ctypes.c_void_p),
+                ("n_matches", ctypes.c_int64), ("matches", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
+
+
 class gs_grads(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
                 ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("grad2d", ctypes.c_void_p),
@@ -86,6 +96,7 @@ def load():
                  "gs_pixel_base"]:
         getattr(lib, name).restype = ctypes.c_int64
     lib.gs_error_string.restype = ctypes.c_char_p
+    lib.gs_ga_weights_scratch_bytes.restype = ctypes.c_size_t
     _lib = lib
     return lib
 
@@ -310,6 +321,50 @@ def gs_sgld_adam_step(groups, step, beta1=0.9, beta2=0.999, eps=1e-15, noise=Non
     _check(load().gs_sgld_adam_step(arr, len(groups), int(step), ctypes.c_double(beta1), ctypes.c_double(beta2),
                                     ctypes.c_double(eps), _ptr(noise), ctypes.c_float(noise_scale), int(noise_group),
                                     _stream(stream)), "gs_sgld_adam_step")
+
+
+# ---------------------------------------------------------------------------
+# camera global alignment (Section 3.3)
+# ---------------------------------------------------------------------------
+def gs_ga_select_pairs(viewmats, max_angle_deg, pairs, n_pairs_out, status=None, stream=None):
+    """Candidate pairs into pairs (int32 [capacity,2]); count into
+    n_pairs_out (int64 [1])."""
+    cap = pairs.shape[0] if pairs is not None else 0
+    _check(load().gs_ga_select_pairs(_ptr(viewmats), int(viewmats.shape[0]), ctypes.c_double(max_angle_deg),
+                                     _ptr(pairs) if cap else None, ctypes.c_int64(cap), _ptr(n_pairs_out),
+                                     _ptr(status), _stream(stream)), "gs_ga_select_pairs")
+
+
+def gs_ga_incidence(pairs, n_cams, cam_offsets, cam_pairs, status=None, stream=None):
+    _check(load().gs_ga_incidence(_ptr(pairs) if pairs.numel() else None, ctypes.c_int64(pairs.shape[0]),
+                                  int(n_cams), _ptr(cam_offsets), _ptr(cam_pairs) if cam_pairs.numel() else None,
+                                  _ptr(status), _stream(stream)), "gs_ga_incidence")
+
+
+def ga_problem(intrinsics, viewmats, pairs, match_offsets, matches, weights=None) -> gs_ga_problem:
+    return gs_ga_problem(int(intrinsics.shape[0]), _ptr(intrinsics), _ptr(viewmats), int(pairs.shape[0]),
+                         _ptr(pairs) if pairs.numel() else None, _ptr(match_offsets), int(matches.shape[0]),
+                         _ptr(matches) if matches.numel() else None, _ptr(weights))
+
+
+def gs_ga_epipolar(problem: gs_ga_problem, pair_sums, loss, dist=None, cam_offsets=None, cam_pairs=None,
+                   d_intrinsics=None, d_viewmats=None, status=None, stream=None):
+    _check(load().gs_ga_epipolar(ctypes.byref(problem), _ptr(dist),
+                                 _ptr(pair_sums) if pair_sums is not None and pair_sums.numel() else None,
+                                 _ptr(cam_offsets), _ptr(cam_pairs) if cam_pairs is not None and cam_pairs.numel()
+                                 else None, _ptr(loss), _ptr(d_intrinsics), _ptr(d_viewmats), _ptr(status),
+                                 _stream(stream)), "gs_ga_epipolar")
+
+
+def gs_ga_weights_scratch_bytes(n_bins):
+    return int(load().gs_ga_weights_scratch_bytes(int(n_bins)))
+
+
+def gs_ga_weights(dist, n_bins, alpha, counts, weights, stats, scratch, stream=None):
+    n = dist.numel()
+    _check(load().gs_ga_weights(_ptr(dist) if n else None, ctypes.c_int64(n), int(n_bins), ctypes.c_double(alpha),
+                                _ptr(counts), _ptr(weights) if n else None, _ptr(stats), _ptr(scratch),
+                                _stream(stream)), "gs_ga_weights")
 
 
 def pair_counts(bins: Bins):

@@ -1,6 +1,7 @@
 // extern "C" entry points of libgsplat_gb300.so (declared in include/gs.h):
 // host-side argument checks, the per-call launch description, and dispatch
 // to the kernels. No allocation, no synchronisation.
+#include <math.h>
 #include <string.h>
 
 #include "gs_common.cuh"
@@ -22,6 +23,15 @@ int launch_l1(const float *image, const float *target, long long n, float *loss,
 int launch_adam_sgld(const gs_adam_group *groups, int n_groups, int step, double beta1, double beta2, double eps,
                      const float *noise, float noise_scale, int noise_group, cudaStream_t st);
 int pose_blocks(long long n);
+int launch_ga_select(const float *vm, int n, float cos_thr, int32_t *pairs, long long capacity, long long *n_out,
+                     int32_t *status, cudaStream_t st);
+int launch_ga_incidence(const int32_t *pairs, long long n_pairs, int n, int32_t *cam_offsets, int32_t *cam_pairs,
+                        int32_t *status, cudaStream_t st);
+int launch_ga_epipolar(const gs_ga_problem &P, float *dist, float *pair_sums, const int32_t *cam_offsets,
+                       const int32_t *cam_pairs, float *loss, float *d_intr, float *d_vm, int32_t *status,
+                       cudaStream_t st);
+int launch_ga_weights(const float *e, long long n, int nb, double alpha, uint32_t *counts, float *w, float *stats,
+                      uint32_t *scratch, cudaStream_t st);
 
 int num_sms() {
     static int cached[64];
@@ -300,6 +310,53 @@ int gs_sgld_adam_step(const gs_adam_group *groups, int n_groups, int step, doubl
     if (noise && (noise_group < 0 || noise_group >= n_groups)) return GS_ERR_ARG;
     return launch_adam_sgld(groups, n_groups, step, beta1, beta2, eps, noise, noise_scale, noise_group,
                             (cudaStream_t)stream);
+}
+
+int gs_ga_select_pairs(const float *viewmats, int n_cams, double max_angle_deg, int32_t *pairs, int64_t capacity,
+                       int64_t *n_pairs_out, int32_t *status, void *stream) {
+    if (!viewmats || n_cams < 1 || n_cams > GS_GA_MAX_CAMS || capacity < 0 || (capacity > 0 && !pairs) ||
+        !n_pairs_out || !(max_angle_deg > 0.0 && max_angle_deg <= 180.0))
+        return GS_ERR_ARG;
+    const float cos_thr = (float)cos(max_angle_deg * (M_PI / 180.0));
+    return launch_ga_select(viewmats, n_cams, cos_thr, pairs, capacity, (long long *)n_pairs_out, status,
+                            (cudaStream_t)stream);
+}
+
+int gs_ga_incidence(const int32_t *pairs, int64_t n_pairs, int n_cams, int32_t *cam_offsets, int32_t *cam_pairs,
+                    int32_t *status, void *stream) {
+    if (n_cams < 1 || n_cams > GS_GA_MAX_CAMS || n_pairs < 0 || 2 * n_pairs > 0x7fffffffLL || !cam_offsets ||
+        (n_pairs > 0 && (!pairs || !cam_pairs)))
+        return GS_ERR_ARG;
+    return launch_ga_incidence(pairs, n_pairs, n_cams, cam_offsets, cam_pairs, status, (cudaStream_t)stream);
+}
+
+int gs_ga_epipolar(const gs_ga_problem *p, float *dist, float *pair_sums, const int32_t *cam_offsets,
+                   const int32_t *cam_pairs, float *loss, float *d_intrinsics, float *d_viewmats, int32_t *status,
+                   void *stream) {
+    if (!p || p->n_cams < 1 || p->n_cams > GS_GA_MAX_CAMS || !p->intrinsics || !p->viewmats || p->n_pairs < 0 ||
+        p->n_matches < 0 || !loss || 2 * p->n_pairs > 0x7fffffffLL)
+        return GS_ERR_ARG;
+    if (p->n_pairs > 0 && (!p->pairs || !p->match_offsets || !pair_sums)) return GS_ERR_ARG;
+    if (p->n_matches > 0 && (!p->matches || ((uintptr_t)p->matches & 15))) return GS_ERR_ARG;
+    const bool grads = d_intrinsics || d_viewmats;
+    if (grads && (!d_intrinsics || !d_viewmats || (p->n_pairs > 0 && (!cam_offsets || !cam_pairs))))
+        return GS_ERR_ARG;
+    return launch_ga_epipolar(*p, dist, pair_sums, cam_offsets, cam_pairs, loss, d_intrinsics, d_viewmats, status,
+                              (cudaStream_t)stream);
+}
+
+size_t gs_ga_weights_scratch_bytes(int n_bins) {
+    if (n_bins < 1 || n_bins > GS_GA_MAX_BINS) return 0;
+    return (size_t)(8 + 2048 + n_bins) * 4;
+}
+
+int gs_ga_weights(const float *dist, int64_t n, int n_bins, double alpha, uint32_t *counts, float *weights,
+                  float *stats, void *scratch, void *stream) {
+    if (n < 0 || n > 0xffffffffLL || n_bins < 1 || n_bins > GS_GA_MAX_BINS || !(alpha >= 0.0) || !counts ||
+        !stats || !scratch || (n > 0 && (!dist || !weights)))
+        return GS_ERR_ARG;
+    return launch_ga_weights(dist, n, n_bins, alpha, counts, weights, stats, (uint32_t *)scratch,
+                             (cudaStream_t)stream);
 }
 
 const char *gs_error_string(int code) {
