@@ -306,6 +306,38 @@ int gs_ga_epipolar(const gs_ga_problem *p, float *dist, float *pair_sums, const 
                    const int32_t *cam_pairs, float *loss, float *d_intrinsics, float *d_viewmats, int32_t *status,
                    void *stream);
 
+/* One whole global-alignment iteration on the device (three launches, no
+ * host work, capturable): the cameras from per-camera residuals, the Eq. 2
+ * loss and camera gradients (as gs_ga_epipolar), the gradients chained to
+ * the residuals and one Adam step on them. The residuals of camera n,
+ * residuals[10n..10n+9], are a 6D rotation residual (a1, a2: dR has columns
+ * b1 = a1/|a1|, b2 = normalised a2 - (b1.a2) b1, b3 = b1 x b2), a
+ * translation residual dt and a log-focal residual df (Section 3.4's pose
+ * residual plus a focal scale): R = dR R0, t = t0 + dt, (fx, fy) = (fx0,
+ * fy0) exp(df), principal point fixed (df stays 0 unless optimise_focal).
+ * The call increments *step (DEVICE int32, 0 before the first call), writes
+ * the cameras it used to intrinsics / viewmats (which p->intrinsics and
+ * p->viewmats must point at), the loss at those cameras, dL/d(residuals) to
+ * d_residuals (DEVICE [n,10], or NULL), and updates residuals, exp_avg and
+ * exp_avg_sq in place with Adam (bias-corrected with the incremented step,
+ * 1 - beta formed in double): p <- p - lr m^ / (sqrt(v^) + eps). */
+typedef struct gs_ga_state {
+    int n_cams;
+    const float *intrinsics0;   /* DEVICE [n_cams,4] */
+    const float *viewmats0;     /* DEVICE [n_cams,12] */
+    float *residuals;           /* DEVICE [n_cams,10]; identity (1,0,0, 0,1,0, 0,0,0, 0) */
+    float *exp_avg;             /* DEVICE [n_cams,10] */
+    float *exp_avg_sq;          /* DEVICE [n_cams,10] */
+    int32_t *step;              /* DEVICE [1] */
+    float *intrinsics;          /* DEVICE [n_cams,4], written */
+    float *viewmats;            /* DEVICE [n_cams,12], written */
+    float lr;
+    double beta1, beta2, eps;
+    int optimise_focal;
+} gs_ga_state;
+int gs_ga_step(const gs_ga_state *s, const gs_ga_problem *p, float *pair_sums, const int32_t *cam_offsets,
+               const int32_t *cam_pairs, float *loss, float *d_residuals, int32_t *status, void *stream);
+
 /* Adaptive weights (Eq. 3) and the median (Eq. 4) of n distances dist
  * (DEVICE, finite, >= 0): a histogram with n_bins equal bins on
  * [0, max e], bin b = min(n_bins - 1, floor(e * (n_bins / max e))) with the

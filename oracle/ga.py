@@ -223,3 +223,69 @@ def lr_rule(median, lr=(5e-4, 1e-3, 1e-2), b=(2.5, 7.5)):
     if median > b[1]:
         return lr[2]
     return lr[1]
+
+
+def rotation_6d(a):
+    """6D rotation residual (Section 3.4) -> 3x3: b1 = a1/|a1|,
+    b2 = normalise(a2 - (b1.a2) b1), b3 = b1 x b2, as columns."""
+    a = np.asarray(a, np.float64)
+    b1 = a[:3] / np.linalg.norm(a[:3])
+    u = a[3:] - (b1 @ a[3:]) * b1
+    b2 = u / np.linalg.norm(u)
+    return np.stack([b1, b2, np.cross(b1, b2)], 1)
+
+
+def apply_residuals(intr0, vm0, res, optimise_focal=True):
+    """Cameras from per-camera residuals res [N,10] = (6D rotation,
+    translation, log focal): R' = dR R, t' = t + dt, (fx', fy') =
+    (fx, fy) exp(df) (df ignored unless optimise_focal)."""
+    intr0 = np.asarray(intr0, np.float64).reshape(-1, 4)
+    vm0 = np.asarray(vm0, np.float64).reshape(-1, 12)
+    res = np.asarray(res, np.float64).reshape(-1, 10)
+    intr = intr0.copy()
+    vm = vm0.copy()
+    for n in range(len(vm0)):
+        vm[n, :9] = (rotation_6d(res[n, :6]) @ vm0[n, :9].reshape(3, 3)).reshape(-1)
+        vm[n, 9:] = vm0[n, 9:] + res[n, 6:9]
+        if optimise_focal:
+            intr[n, :2] = intr0[n, :2] * np.exp(res[n, 9])
+    return intr, vm
+
+
+def residual_vjp(intr0, vm0, res, d_intr, d_vm, optimise_focal=True):
+    """dL/d(residuals) [N,10] from dL/d(intrinsics) and dL/d(viewmats) at
+    apply_residuals(...), by the chain rule through the Gram-Schmidt map:
+      G_dR = G_R' R^T (columns g1, g2, g3), b3 = b1 x b2:
+        g1 += b2 x g3, g2 += g3 x b1;
+      b2 = u/|u|: g_u = (g2 - b2 (b2.g2))/|u|;
+      u = a2 - (b1.a2) b1: g_a2 = g_u - (b1.g_u) b1, g1 += -(b1.a2) g_u - (b1.g_u) a2;
+      b1 = a1/|a1|: g_a1 = (g1 - b1 (b1.g1))/|a1|;
+      dt: G_t'; df: fx' dL/dfx' + fy' dL/dfy'."""
+    intr0 = np.asarray(intr0, np.float64).reshape(-1, 4)
+    vm0 = np.asarray(vm0, np.float64).reshape(-1, 12)
+    res = np.asarray(res, np.float64).reshape(-1, 10)
+    d_intr = np.asarray(d_intr, np.float64).reshape(-1, 4)
+    d_vm = np.asarray(d_vm, np.float64).reshape(-1, 12)
+    out = np.zeros_like(res)
+    for n in range(len(res)):
+        a1, a2 = res[n, :3], res[n, 3:6]
+        n1 = np.linalg.norm(a1)
+        b1 = a1 / n1
+        s = b1 @ a2
+        u = a2 - s * b1
+        nu = np.linalg.norm(u)
+        b2 = u / nu
+        G = d_vm[n, :9].reshape(3, 3) @ vm0[n, :9].reshape(3, 3).T
+        g1, g2, g3 = G[:, 0].copy(), G[:, 1].copy(), G[:, 2].copy()
+        g1 += np.cross(b2, g3)
+        g2 += np.cross(g3, b1)
+        gu = (g2 - b2 * (b2 @ g2)) / nu
+        ga2 = gu - (b1 @ gu) * b1
+        g1 += -s * gu - (b1 @ gu) * a2
+        out[n, :3] = (g1 - b1 * (b1 @ g1)) / n1
+        out[n, 3:6] = ga2
+        out[n, 6:9] = d_vm[n, 9:]
+        if optimise_focal:
+            f = intr0[n, :2] * np.exp(res[n, 9])
+            out[n, 9] = d_intr[n, 0] * f[0] + d_intr[n, 1] * f[1]
+    return out

@@ -25,7 +25,7 @@ EXPORTED = ["gs_config_default", "gs_num_slots", "gs_slot_base", "gs_num_tiles",
             "gs_num_image_floats", "gs_pixel_base", "gs_pose_blocks", "gs_project", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version",
             "gs_project_bwd_noalloc", "gs_sgld_adam_step", "gs_ga_select_pairs", "gs_ga_incidence",
-            "gs_ga_epipolar", "gs_ga_weights_scratch_bytes", "gs_ga_weights"]
+            "gs_ga_epipolar", "gs_ga_weights_scratch_bytes", "gs_ga_weights", "gs_ga_step"]
 GS_GA_MAX_CAMS = 8192
 GS_GA_PAIR_FLOATS = 12
 GS_GA_MAX_BINS = 16384
@@ -72,6 +72,14 @@ class gs_ga_problem(ctypes.Structure):
     _fields_ = [("n_cams", ctypes.c_int), ("intrinsics", ctypes.c_void_p), ("viewmats", ctypes.c_void_p),
                 ("n_pairs", ctypes.c_int64), ("pairs", ctypes.c_void_p), ("match_offsets", ctypes.c_void_p),
                 ("n_matches", ctypes.c_int64), ("matches", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
+
+
+class gs_ga_state(ctypes.Structure):
+    _fields_ = [("n_cams", ctypes.c_int), ("intrinsics0", ctypes.c_void_p), ("viewmats0", ctypes.c_void_p),
+                ("residuals", ctypes.c_void_p), ("exp_avg", ctypes.c_void_p), ("exp_avg_sq", ctypes.c_void_p),
+                ("step", ctypes.c_void_p), ("intrinsics", ctypes.c_void_p), ("viewmats", ctypes.c_void_p),
+                ("lr", ctypes.c_float), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("optimise_focal", ctypes.c_int)]
 
 
 class gs_grads(ctypes.Structure):
@@ -354,6 +362,21 @@ def gs_ga_epipolar(problem: gs_ga_problem, pair_sums, loss, dist=None, cam_offse
                                  _ptr(cam_offsets), _ptr(cam_pairs) if cam_pairs is not None and cam_pairs.numel()
                                  else None, _ptr(loss), _ptr(d_intrinsics), _ptr(d_viewmats), _ptr(status),
                                  _stream(stream)), "gs_ga_epipolar")
+
+
+def ga_state(intrinsics0, viewmats0, residuals, exp_avg, exp_avg_sq, step, intrinsics, viewmats, lr, beta1=0.9,
+             beta2=0.999, eps=1e-15, optimise_focal=True) -> gs_ga_state:
+    return gs_ga_state(int(intrinsics0.shape[0]), _ptr(intrinsics0), _ptr(viewmats0), _ptr(residuals),
+                       _ptr(exp_avg), _ptr(exp_avg_sq), _ptr(step), _ptr(intrinsics), _ptr(viewmats), float(lr),
+                       float(beta1), float(beta2), float(eps), int(bool(optimise_focal)))
+
+
+def gs_ga_step(state: gs_ga_state, problem: gs_ga_problem, pair_sums, cam_offsets, cam_pairs, loss,
+               d_residuals=None, status=None, stream=None):
+    _check(load().gs_ga_step(ctypes.byref(state), ctypes.byref(problem),
+                             _ptr(pair_sums) if pair_sums.numel() else None, _ptr(cam_offsets),
+                             _ptr(cam_pairs) if cam_pairs.numel() else None, _ptr(loss), _ptr(d_residuals),
+                             _ptr(status), _stream(stream)), "gs_ga_step")
 
 
 def gs_ga_weights_scratch_bytes(n_bins):

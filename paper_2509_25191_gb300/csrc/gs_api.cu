@@ -32,6 +32,8 @@ int launch_ga_epipolar(const gs_ga_problem &P, float *dist, float *pair_sums, co
                        cudaStream_t st);
 int launch_ga_weights(const float *e, long long n, int nb, double alpha, uint32_t *counts, float *w, float *stats,
                       uint32_t *scratch, cudaStream_t st);
+int launch_ga_step(const gs_ga_state &s, const gs_ga_problem &P, float *pair_sums, const int32_t *cam_offsets,
+                   const int32_t *cam_pairs, float *loss, float *d_res, int32_t *status, cudaStream_t st);
 
 int num_sms() {
     static int cached[64];
@@ -343,6 +345,23 @@ int gs_ga_epipolar(const gs_ga_problem *p, float *dist, float *pair_sums, const 
         return GS_ERR_ARG;
     return launch_ga_epipolar(*p, dist, pair_sums, cam_offsets, cam_pairs, loss, d_intrinsics, d_viewmats, status,
                               (cudaStream_t)stream);
+}
+
+int gs_ga_step(const gs_ga_state *s, const gs_ga_problem *p, float *pair_sums, const int32_t *cam_offsets,
+               const int32_t *cam_pairs, float *loss, float *d_residuals, int32_t *status, void *stream) {
+    if (!s || !p || s->n_cams != p->n_cams || !s->intrinsics0 || !s->viewmats0 || !s->residuals || !s->exp_avg ||
+        !s->exp_avg_sq || !s->step || !s->intrinsics || !s->viewmats || p->intrinsics != s->intrinsics ||
+        p->viewmats != s->viewmats)
+        return GS_ERR_ARG;
+    if (!(s->beta1 >= 0.0 && s->beta1 < 1.0 && s->beta2 >= 0.0 && s->beta2 < 1.0 && s->eps >= 0.0)) return GS_ERR_ARG;
+    if (p->n_cams < 1 || p->n_cams > GS_GA_MAX_CAMS || p->n_pairs < 0 || p->n_matches < 0 || !loss ||
+        2 * p->n_pairs > 0x7fffffffLL)
+        return GS_ERR_ARG;
+    if (p->n_pairs > 0 && (!p->pairs || !p->match_offsets || !pair_sums || !cam_offsets || !cam_pairs))
+        return GS_ERR_ARG;
+    if (p->n_matches > 0 && (!p->matches || ((uintptr_t)p->matches & 15))) return GS_ERR_ARG;
+    return launch_ga_step(*s, *p, pair_sums, cam_offsets, cam_pairs, loss, d_residuals, status,
+                          (cudaStream_t)stream);
 }
 
 size_t gs_ga_weights_scratch_bytes(int n_bins) {

@@ -69,11 +69,56 @@ __device__ __forceinline__ void warp_sum(float (&v)[NV]) {
 // ---------------------------------------------------------------------------
 // Per pair: distances, sum w e, sum w and G^ (9 values).
 // ---------------------------------------------------------------------------
+struct GaPairGeom {
+    float E[9];
+    float cxi, cyi, cxj, cyj, rfi, rgi, rfj, rgj;
+};
+
+// One match: e = |x^'.m| / |(m0/fx_j, m1/fy_j)| with m = E x^, and its
+// contribution to sum w e, sum w and G^ = sum a^ x^^T.
+template <bool WRITE_DIST>
+__device__ __forceinline__ void ga_match(const GaPairGeom &g, float4 q, float w, float *acc, float *dist_k) {
+    const float x0 = (q.x - g.cxi) * g.rfi, x1 = (q.y - g.cyi) * g.rgi;
+    const float y0 = (q.z - g.cxj) * g.rfj, y1 = (q.w - g.cyj) * g.rgj;
+    const float m0 = fmaf(g.E[0], x0, fmaf(g.E[1], x1, g.E[2]));
+    const float m1 = fmaf(g.E[3], x0, fmaf(g.E[4], x1, g.E[5]));
+    const float m2 = fmaf(g.E[6], x0, fmaf(g.E[7], x1, g.E[8]));
+    const float s = fmaf(y0, m0, fmaf(y1, m1, m2));
+    const float l0 = m0 * g.rfj, l1 = m1 * g.rgj;
+    const float n2 = fmaf(l0, l0, l1 * l1);
+    float e = 0.f;
+    if (n2 > 0.f && n2 < INFINITY) {
+        const float rn = rsqrtf(n2);
+        const float as = fabsf(s);
+        e = as * rn;
+        const float c1 = s > 0.f ? w * rn : (s < 0.f ? -w * rn : 0.f);
+        const float c2 = w * as * rn * rn * rn;
+        const float h0 = c1 * y0 - c2 * l0 * g.rfj;
+        const float h1 = c1 * y1 - c2 * l1 * g.rgj;
+        const float h2 = c1;
+        acc[2] = fmaf(h0, x0, acc[2]);
+        acc[3] = fmaf(h0, x1, acc[3]);
+        acc[4] += h0;
+        acc[5] = fmaf(h1, x0, acc[5]);
+        acc[6] = fmaf(h1, x1, acc[6]);
+        acc[7] += h1;
+        acc[8] = fmaf(h2, x0, acc[8]);
+        acc[9] = fmaf(h2, x1, acc[9]);
+        acc[10] += h2;
+    }
+    if (WRITE_DIST) *dist_k = e;
+    acc[0] = fmaf(w, e, acc[0]);
+    acc[1] += w;
+}
+
+constexpr int GA_UNROLL = 4;
+
 template <bool WRITE_DIST>
 __global__ void __launch_bounds__(GA_THREADS) k_ga_pairs(const gs_ga_problem P, float *__restrict__ dist,
                                                          float *__restrict__ pair_sums, int32_t *status) {
     __shared__ float s_red[GA_THREADS / 32][11];
     const float4 *__restrict__ M4 = reinterpret_cast<const float4 *>(P.matches);
+    const float *__restrict__ Wt = P.weights;
     for (long long m = blockIdx.x; m < P.n_pairs; m += gridDim.x) {
         const int ci = P.pairs[2 * m], cj = P.pairs[2 * m + 1];
         const long long a = P.match_offsets[m], b = P.match_offsets[m + 1];
@@ -90,52 +135,41 @@ __global__ void __launch_bounds__(GA_THREADS) k_ga_pairs(const gs_ga_problem P, 
         GaCam A, B;
         ga_load_cam(P.intrinsics, P.viewmats, ci, A);
         ga_load_cam(P.intrinsics, P.viewmats, cj, B);
-        float R[9], t[3], E[9];
-        ga_relative(A, B, R, t, E);
-        const float rfi = 1.f / A.fx, rgi = 1.f / A.fy, rfj = 1.f / B.fx, rgj = 1.f / B.fy;
+        GaPairGeom g;
+        float R[9], t[3];
+        ga_relative(A, B, R, t, g.E);
+        g.cxi = A.cx;
+        g.cyi = A.cy;
+        g.cxj = B.cx;
+        g.cyj = B.cy;
+        g.rfi = 1.f / A.fx;
+        g.rgi = 1.f / A.fy;
+        g.rfj = 1.f / B.fx;
+        g.rgj = 1.f / B.fy;
         float acc[11];
 #pragma unroll
         for (int k = 0; k < 11; ++k) acc[k] = 0.f;
-        for (long long k = a + threadIdx.x; k < b; k += GA_THREADS) {
-            const float4 q = M4[k];
-            const float w = P.weights ? P.weights[k] : 1.f;
-            const float x0 = (q.x - A.cx) * rfi, x1 = (q.y - A.cy) * rgi;
-            const float y0 = (q.z - B.cx) * rfj, y1 = (q.w - B.cy) * rgj;
-            const float m0 = fmaf(E[0], x0, fmaf(E[1], x1, E[2]));
-            const float m1 = fmaf(E[3], x0, fmaf(E[4], x1, E[5]));
-            const float m2 = fmaf(E[6], x0, fmaf(E[7], x1, E[8]));
-            const float s = fmaf(y0, m0, fmaf(y1, m1, m2));
-            const float l0 = m0 * rfj, l1 = m1 * rgj;
-            const float n2 = fmaf(l0, l0, l1 * l1);
-            float e = 0.f;
-            if (n2 > 0.f && n2 < INFINITY) {
-                const float rn = rsqrtf(n2);
-                const float as = fabsf(s);
-                e = as * rn;
-                const float c1 = s > 0.f ? w * rn : (s < 0.f ? -w * rn : 0.f);
-                const float c2 = w * as * rn * rn * rn;
-                const float h0 = c1 * y0 - c2 * l0 * rfj;
-                const float h1 = c1 * y1 - c2 * l1 * rgj;
-                const float h2 = c1;
-                acc[2] = fmaf(h0, x0, acc[2]);
-                acc[3] = fmaf(h0, x1, acc[3]);
-                acc[4] += h0;
-                acc[5] = fmaf(h1, x0, acc[5]);
-                acc[6] = fmaf(h1, x1, acc[6]);
-                acc[7] += h1;
-                acc[8] = fmaf(h2, x0, acc[8]);
-                acc[9] = fmaf(h2, x1, acc[9]);
-                acc[10] += h2;
+        long long k = a + threadIdx.x;
+        // GA_UNROLL matches in flight per thread: all loads first, then the math
+        for (; k + (GA_UNROLL - 1) * GA_THREADS < b; k += GA_UNROLL * GA_THREADS) {
+            float4 q[GA_UNROLL];
+            float w[GA_UNROLL];
+#pragma unroll
+            for (int u = 0; u < GA_UNROLL; ++u) {
+                q[u] = __ldcs(M4 + k + u * GA_THREADS);
+                w[u] = Wt ? __ldcs(Wt + k + u * GA_THREADS) : 1.f;
             }
-            if (WRITE_DIST) dist[k] = e;
-            acc[0] = fmaf(w, e, acc[0]);
-            acc[1] += w;
+#pragma unroll
+            for (int u = 0; u < GA_UNROLL; ++u)
+                ga_match<WRITE_DIST>(g, q[u], w[u], acc, WRITE_DIST ? dist + k + u * GA_THREADS : nullptr);
         }
+        for (; k < b; k += GA_THREADS)
+            ga_match<WRITE_DIST>(g, __ldcs(M4 + k), Wt ? __ldcs(Wt + k) : 1.f, acc, WRITE_DIST ? dist + k : nullptr);
         warp_sum(acc);
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         if (lane == 0)
 #pragma unroll
-            for (int k = 0; k < 11; ++k) s_red[warp][k] = acc[k];
+            for (int k2 = 0; k2 < 11; ++k2) s_red[warp][k2] = acc[k2];
         __syncthreads();
         if (threadIdx.x < 11) {
             float v = 0.f;
@@ -174,10 +208,22 @@ __device__ __forceinline__ void block_sum_cam(float (&v)[NV], float (*s_red)[NV]
 // reduce in a fixed order and divide by W = sum of all weights. Block 0 also
 // writes the loss.
 // ---------------------------------------------------------------------------
+struct GaStepArgs {
+    const float *intr0, *vm0;
+    float *res, *m, *v, *d_res;
+    const int32_t *step;
+    float lr, eps;
+    double b1, b2;
+    int focal;
+};
+
+__device__ void ga_residual_step(const GaStepArgs &S, int c, const float gI[4], const float gV[12]);
+
+template <bool STEP>
 __global__ void __launch_bounds__(GA_CAM_THREADS) k_ga_cams(const gs_ga_problem P, const float *__restrict__ pair_sums,
                                                             const int32_t *__restrict__ cam_offsets,
                                                             const int32_t *__restrict__ cam_pairs, float *loss,
-                                                            float *d_intr, float *d_vm) {
+                                                            float *d_intr, float *d_vm, const GaStepArgs S) {
     __shared__ float s_red2[GA_CAM_THREADS / 32][2];
     __shared__ float s_red16[GA_CAM_THREADS / 32][16];
     float tot[2] = {0.f, 0.f};
@@ -189,7 +235,7 @@ __global__ void __launch_bounds__(GA_CAM_THREADS) k_ga_cams(const gs_ga_problem 
     const float W = tot[1];
     const float invW = W > 0.f ? 1.f / W : 0.f;
     if (blockIdx.x == 0 && threadIdx.x == 0) loss[0] = tot[0] * invW;
-    if (!d_intr || !d_vm) return;
+    if (!STEP && (!d_intr || !d_vm)) return;
     const int c = blockIdx.x;
     float g[16];
 #pragma unroll
@@ -269,8 +315,133 @@ __global__ void __launch_bounds__(GA_CAM_THREADS) k_ga_cams(const gs_ga_problem 
         }
     }
     block_sum_cam(g, s_red16);
+    if (STEP) {
+        if (threadIdx.x == 0) {
+            float gI[4], gV[12];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gI[k] = g[k] * invW;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) gV[k] = g[4 + k] * invW;
+            ga_residual_step(S, c, gI, gV);
+        }
+        return;
+    }
     if (threadIdx.x < 4) d_intr[4 * c + threadIdx.x] = g[threadIdx.x] * invW;
     else if (threadIdx.x < 16) d_vm[12 * c + threadIdx.x - 4] = g[threadIdx.x] * invW;
+}
+
+// ---------------------------------------------------------------------------
+// Residual parametrisation of the cameras and its backward (fused step).
+// ---------------------------------------------------------------------------
+struct Rot6 {
+    float b1[3], b2[3], b3[3], a2[3];
+    float n1, nu, s;
+};
+
+__device__ __forceinline__ void rot6_fwd(const float *a, Rot6 &r) {
+    r.n1 = sqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.b1[k] = a[k] / r.n1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.a2[k] = a[3 + k];
+    r.s = r.b1[0] * r.a2[0] + r.b1[1] * r.a2[1] + r.b1[2] * r.a2[2];
+    float u[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) u[k] = r.a2[k] - r.s * r.b1[k];
+    r.nu = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.b2[k] = u[k] / r.nu;
+    r.b3[0] = r.b1[1] * r.b2[2] - r.b1[2] * r.b2[1];
+    r.b3[1] = r.b1[2] * r.b2[0] - r.b1[0] * r.b2[2];
+    r.b3[2] = r.b1[0] * r.b2[1] - r.b1[1] * r.b2[0];
+}
+
+__global__ void k_ga_apply(const GaStepArgs S, int n, float *intr, float *vm, int32_t *step) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) step[0] += 1;
+    if (c >= n) return;
+    const float *res = S.res + 10 * c;
+    Rot6 r;
+    rot6_fwd(res, r);
+    const float *R0 = S.vm0 + 12 * c;
+    // R = dR R0 with dR = [b1 b2 b3] (columns): dR[i][k] = b_k[i]
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            vm[12 * c + 3 * i + j] = r.b1[i] * R0[j] + r.b2[i] * R0[3 + j] + r.b3[i] * R0[6 + j];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) vm[12 * c + 9 + k] = R0[9 + k] + res[6 + k];
+    const float sc = S.focal ? expf(res[9]) : 1.f;
+    intr[4 * c + 0] = S.intr0[4 * c + 0] * sc;
+    intr[4 * c + 1] = S.intr0[4 * c + 1] * sc;
+    intr[4 * c + 2] = S.intr0[4 * c + 2];
+    intr[4 * c + 3] = S.intr0[4 * c + 3];
+}
+
+__device__ void ga_residual_step(const GaStepArgs &S, int c, const float gI[4], const float gV[12]) {
+    float *res = S.res + 10 * c;
+    Rot6 r;
+    rot6_fwd(res, r);
+    const float *R0 = S.vm0 + 12 * c;
+    // G_dR = G_R' R0^T; its columns are the gradients of b1, b2, b3
+    float g1[3], g2[3], g3[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        g1[i] = gV[3 * i] * R0[0] + gV[3 * i + 1] * R0[1] + gV[3 * i + 2] * R0[2];
+        g2[i] = gV[3 * i] * R0[3] + gV[3 * i + 1] * R0[4] + gV[3 * i + 2] * R0[5];
+        g3[i] = gV[3 * i] * R0[6] + gV[3 * i + 1] * R0[7] + gV[3 * i + 2] * R0[8];
+    }
+    // b3 = b1 x b2
+    g1[0] += r.b2[1] * g3[2] - r.b2[2] * g3[1];
+    g1[1] += r.b2[2] * g3[0] - r.b2[0] * g3[2];
+    g1[2] += r.b2[0] * g3[1] - r.b2[1] * g3[0];
+    g2[0] += g3[1] * r.b1[2] - g3[2] * r.b1[1];
+    g2[1] += g3[2] * r.b1[0] - g3[0] * r.b1[2];
+    g2[2] += g3[0] * r.b1[1] - g3[1] * r.b1[0];
+    // b2 = u / |u|
+    const float d2 = r.b2[0] * g2[0] + r.b2[1] * g2[1] + r.b2[2] * g2[2];
+    float gu[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gu[k] = (g2[k] - r.b2[k] * d2) / r.nu;
+    // u = a2 - (b1.a2) b1
+    const float bgu = r.b1[0] * gu[0] + r.b1[1] * gu[1] + r.b1[2] * gu[2];
+    float g[10];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        g[3 + k] = gu[k] - bgu * r.b1[k];
+        g1[k] += -r.s * gu[k] - bgu * r.a2[k];
+    }
+    // b1 = a1 / |a1|
+    const float d1 = r.b1[0] * g1[0] + r.b1[1] * g1[1] + r.b1[2] * g1[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = (g1[k] - r.b1[k] * d1) / r.n1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[6 + k] = gV[9 + k];
+    if (S.focal) {
+        const float sc = expf(res[9]);
+        g[9] = gI[0] * (S.intr0[4 * c] * sc) + gI[1] * (S.intr0[4 * c + 1] * sc);
+    } else {
+        g[9] = 0.f;
+    }
+    if (S.d_res)
+#pragma unroll
+        for (int k = 0; k < 10; ++k) S.d_res[10 * c + k] = g[k];
+    // Adam with the bias correction of the incremented step
+    const int t = S.step[0];
+    const float b1 = (float)S.b1, b2 = (float)S.b2;
+    const float omb1 = (float)(1.0 - S.b1), omb2 = (float)(1.0 - S.b2);
+    const float ibc1 = (float)(1.0 / (1.0 - pow(S.b1, (double)t)));
+    const float ibc2 = (float)(1.0 / (1.0 - pow(S.b2, (double)t)));
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        float m = S.m[10 * c + k], v = S.v[10 * c + k];
+        m = b1 * m + omb1 * g[k];
+        v = b2 * v + omb2 * g[k] * g[k];
+        S.m[10 * c + k] = m;
+        S.v[10 * c + k] = v;
+        res[k] -= S.lr * (m * ibc1) / (sqrtf(v * ibc2) + S.eps);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -597,8 +768,35 @@ int launch_ga_epipolar(const gs_ga_problem &P, float *dist, float *pair_sums, co
         if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
     }
     const bool grads = d_intr && d_vm;
-    k_ga_cams<<<grads ? P.n_cams : 1, GA_CAM_THREADS, 0, st>>>(P, pair_sums, cam_offsets, cam_pairs, loss,
-                                                               grads ? d_intr : nullptr, grads ? d_vm : nullptr);
+    k_ga_cams<false><<<grads ? P.n_cams : 1, GA_CAM_THREADS, 0, st>>>(
+        P, pair_sums, cam_offsets, cam_pairs, loss, grads ? d_intr : nullptr, grads ? d_vm : nullptr, GaStepArgs{});
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+int launch_ga_step(const gs_ga_state &s, const gs_ga_problem &P, float *pair_sums, const int32_t *cam_offsets,
+                   const int32_t *cam_pairs, float *loss, float *d_res, int32_t *status, cudaStream_t st) {
+    GaStepArgs S;
+    S.intr0 = s.intrinsics0;
+    S.vm0 = s.viewmats0;
+    S.res = s.residuals;
+    S.m = s.exp_avg;
+    S.v = s.exp_avg_sq;
+    S.d_res = d_res;
+    S.step = s.step;
+    S.lr = s.lr;
+    S.eps = (float)s.eps;
+    S.b1 = s.beta1;
+    S.b2 = s.beta2;
+    S.focal = s.optimise_focal;
+    k_ga_apply<<<(s.n_cams + 127) / 128, 128, 0, st>>>(S, s.n_cams, s.intrinsics, s.viewmats, s.step);
+    if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
+    if (P.n_pairs > 0) {
+        const long long grid = P.n_pairs < (1LL << 30) ? P.n_pairs : (1LL << 30);
+        k_ga_pairs<false><<<(unsigned)grid, GA_THREADS, 0, st>>>(P, nullptr, pair_sums, status);
+        if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
+    }
+    k_ga_cams<true><<<P.n_cams, GA_CAM_THREADS, 0, st>>>(P, pair_sums, cam_offsets, cam_pairs, loss, nullptr,
+                                                          nullptr, S);
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 

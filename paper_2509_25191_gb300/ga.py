@@ -6,10 +6,12 @@ epipolar distance of Eq. 2. The weights of Eq. 3 and the learning rate of
 Eq. 4 are fixed once from the distances under the initial cameras; then
 ``iterations`` (300 in Section 4.1) Adam steps move per-camera residuals:
 the 6D rotation residual and translation residual of Section 3.4 (R' = dR R,
-t' = t + dt) and a log-focal residual (f' = f exp(df)). Every step runs
-in the library's kernels: gs_ga_epipolar (distances, loss, camera
-gradients), the torch residual ops and their autograd (a few [N, 12]
-matrices) and gs_sgld_adam_step (Adam, no noise).
+t' = t + dt) and a log-focal residual (f' = f exp(df)). By default an
+iteration is one gs_ga_step call: three kernels (cameras from the residuals;
+distances and per-pair gradient sums; per-camera reduction, chain to the
+residuals and Adam) with no host work. ``fused=False`` runs the same
+iteration as gs_ga_epipolar, the residual ops in torch with autograd, and
+gs_sgld_adam_step.
 """
 from __future__ import annotations
 
@@ -74,7 +76,7 @@ class GlobalAlignment:
     """One global-alignment problem resident on the GPU."""
 
     def __init__(self, intrinsics, viewmats, pairs, match_offsets, matches, n_bins=100, alpha=0.5, lrs=LRS,
-                 bounds=BOUNDS, optimise_focal=True):
+                 bounds=BOUNDS, optimise_focal=True, fused=True):
         dev = viewmats.device
         self.n = int(viewmats.shape[0])
         self.intr0 = intrinsics.detach().float().contiguous()
@@ -103,8 +105,21 @@ class GlobalAlignment:
         self.params = [self.dr, self.dt] + ([self.dlogf] if optimise_focal else [])
         self.moments = [(torch.zeros_like(p), torch.zeros_like(p)) for p in self.params]
         self.steps = 0
+        # fused state: residuals [N,10] = (6D rotation, translation, log focal)
+        self.fused = fused
+        self.res = torch.cat([self.dr, self.dt, self.dlogf], 1).contiguous()
+        self.res_m = torch.zeros_like(self.res)
+        self.res_v = torch.zeros_like(self.res)
+        self.step_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.intr = self.intr0.clone()
+        self.vm = self.vm0.clone()
+        self.state = _lib.ga_state(self.intr0, self.vm0, self.res, self.res_m, self.res_v, self.step_dev, self.intr,
+                                   self.vm, self.lr, optimise_focal=optimise_focal)
+        self.fused_problem = _lib.ga_problem(self.intr, self.vm, self.pairs, self.offsets, self.matches, self.weights)
 
     def cameras(self, params=None):
+        if params is None and self.fused:
+            params = (self.res[:, :6], self.res[:, 6:9], self.res[:, 9:10])
         dr, dt, dlogf = params if params is not None else (self.dr, self.dt, self.dlogf)
         vm = pose.apply_residual(self.vm0, dr, dt)
         intr = torch.cat([self.intr0[:, :2] * torch.exp(dlogf), self.intr0[:, 2:]], 1)
@@ -120,7 +135,12 @@ class GlobalAlignment:
                             d_viewmats=self.d_vm, status=self.status)
         return self.loss, self.d_intr, self.d_vm
 
-    def step(self):
+    def step(self, d_residuals=None):
+        if self.fused:
+            _lib.gs_ga_step(self.state, self.fused_problem, self.pair_sums, self.cam_offsets, self.cam_pairs,
+                            self.loss, d_residuals, self.status)
+            self.steps += 1
+            return self.loss
         leaves = [self.dr.detach().requires_grad_(True), self.dt.detach().requires_grad_(True),
                   self.dlogf.detach().requires_grad_(self.optimise_focal)]
         with torch.enable_grad():

@@ -239,3 +239,75 @@ def test_alignment_reduces_pose_error():
     d0 = OG.distances(ii, iv, pairs, M.offsets, M.matches)
     assert np.median(d1[M.inlier]) < 0.5 * np.median(d0[M.inlier]), (np.median(d0[M.inlier]), np.median(d1[M.inlier]))
     assert e1 < 0.5 * e0, (e0, e1)
+
+
+def test_fused_step_matches_the_oracle_chain():
+    """gs_ga_step: cameras from residuals, residual gradients through the
+    Gram-Schmidt chain and the Adam update, each against the FP64 oracle, over
+    two calls (the device step counter drives the bias correction)."""
+    from oracle.optim import adam_sgld_step
+    tv, ti, iv, ii, pairs, M = _problem(n_views=30, per_pair=600, seed=4)
+    n = len(iv)
+    rng = np.random.default_rng(9)
+    res = np.tile(np.array([1, 0, 0, 0, 1, 0, 0, 0, 0, 0], np.float32), (n, 1))
+    res += (0.02 * rng.standard_normal((n, 10))).astype(np.float32)
+    w = rng.uniform(0.1, 2.0, len(M.matches)).astype(np.float32)
+    intr0, vm0, pr, offs, mt, wt, r = _cuda(ii, iv, pairs, M.offsets, M.matches, w, res)
+    m = torch.zeros_like(r)
+    v = torch.zeros_like(r)
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    intr = torch.empty_like(intr0)
+    vm = torch.empty_like(vm0)
+    cam_offsets, cam_pairs, status = ga.incidence(pr, n)
+    lr = 1e-3
+    state = _lib.ga_state(intr0, vm0, r, m, v, step, intr, vm, lr)
+    sums = torch.empty(len(pairs), _lib.GS_GA_PAIR_FLOATS, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    d_res = torch.empty_like(r)
+    groups = [dict(param=res.astype(np.float64), grad=None, m=np.zeros((n, 10)), v=np.zeros((n, 10)), lr=lr)]
+    for call in (1, 2):
+        res_before = r.cpu().numpy().astype(np.float64)
+        # mask matches whose |x'^T F x| is within float32 rounding of 0 at the
+        # cameras of this call (computed from the oracle's cameras)
+        i_or, v_or = OG.apply_residuals(ii, iv, res_before)
+        e_or = OG.distances(i_or, v_or, pairs, M.offsets, M.matches)
+        kappa = _kappa(i_or, v_or, pairs, M.offsets, M.matches.astype(np.float64))
+        wm = w.copy()
+        wm[e_or <= 4 * (32 * U32 * kappa + 1e-5 * e_or)] = 0.0
+        wt.copy_(torch.as_tensor(wm))
+        prob = _lib.ga_problem(intr, vm, pr, offs, mt, wt)
+        _lib.gs_ga_step(state, prob, sums, cam_offsets, cam_pairs, loss, d_res, status)
+        torch.cuda.synchronize()
+        assert status.cpu().numpy()[0] == 0 and int(step.item()) == call
+        # cameras
+        assert np.allclose(vm.cpu().numpy(), v_or, rtol=0, atol=2e-6 * np.abs(v_or).max())
+        assert np.allclose(intr.cpu().numpy(), i_or, rtol=1e-6)
+        # loss and residual gradients at the GPU's cameras
+        gi, gv = intr.cpu().numpy().astype(np.float64), vm.cpu().numpy().astype(np.float64)
+        L_or, di, dv = OG.loss_and_grads(gi, gv, pairs, M.offsets, M.matches, wm)
+        assert abs(float(loss.item()) - L_or) <= 1e-5 * L_or
+        g_or = OG.residual_vjp(ii, iv, res_before, di, dv)
+        g_gpu = d_res.cpu().numpy()
+        check_grad(g_gpu, g_or, f"call {call}: dL/d(residuals)")
+        # Adam update from the GPU's gradient, in FP64
+        groups[0]["param"] = res_before.copy()
+        groups[0]["grad"] = g_gpu.astype(np.float64)
+        adam_sgld_step(groups, call, 0.9, 0.999, 1e-15)
+        assert np.allclose(r.cpu().numpy(), groups[0]["param"], rtol=0, atol=1e-6)
+        assert np.allclose(m.cpu().numpy(), groups[0]["m"], rtol=1e-5, atol=1e-7 * np.abs(groups[0]["m"]).max())
+
+
+def test_unfused_iteration_converges_like_the_fused_one():
+    tv, ti, iv, ii = synth.ga_cameras(6, 40)
+    pairs = OG.select_pairs(iv, 30.0)
+    M = synth.ga_matches(6, synth.ga_points(6, 6000), ti, tv, pairs, 1600, 1066, 1000)
+    intr, vm, pr, offs, mt = _cuda(ii, iv, pairs, M.offsets, M.matches)
+    e0 = _rel_rot_err(tv.astype(np.float64), iv.astype(np.float64), pairs)
+    out = []
+    for fused in (True, False):
+        G = ga.GlobalAlignment(intr, vm, pr, offs, mt, fused=fused)
+        _, vm1 = G.run(150)
+        torch.cuda.synchronize()
+        G.check()
+        out.append(_rel_rot_err(tv.astype(np.float64), vm1.detach().cpu().numpy().astype(np.float64), pairs))
+    assert out[0] < 0.3 * e0 and out[1] < 0.3 * e0, (e0, out)

@@ -215,3 +215,41 @@ def test_pair_selection_by_viewing_angle():
             ang = np.degrees(np.arccos(np.clip(d[i] @ d[j] / np.linalg.norm(d[i]) / np.linalg.norm(d[j]), -1, 1)))
             if abs(ang - 30.0) > 1e-3:
                 assert ((i, j) in pairs) == (ang < 30.0), (i, j, ang)
+
+
+def test_residual_identity_and_orthonormality():
+    _, _, iv, ii = _cams(4)
+    ident = np.tile([1.0, 0, 0, 0, 1.0, 0, 0, 0, 0, 0], (4, 1))
+    intr, vm = ga.apply_residuals(ii, iv, ident)
+    assert np.allclose(vm, iv, atol=1e-15) and np.allclose(intr, ii, atol=1e-12)
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        R = ga.rotation_6d(rng.standard_normal(6))
+        assert np.allclose(R.T @ R, np.eye(3), atol=1e-13) and abs(np.linalg.det(R) - 1) < 1e-13
+    # a rotation about z by theta has 6D representation (cos, sin, 0, -sin, cos, 0)
+    th = 0.3
+    R = ga.rotation_6d([np.cos(th), np.sin(th), 0, -np.sin(th), np.cos(th), 0])
+    assert np.allclose(R, _axis_rot([0, 0, 1], th), atol=1e-15)
+
+
+def test_residual_vjp_matches_central_differences():
+    intr0, vm0, pairs, M, w = _problem(seed=2)
+    rng = np.random.default_rng(3)
+    res = np.tile([1.0, 0, 0, 0, 1.0, 0, 0, 0, 0, 0], (len(vm0), 1)) + 0.05 * rng.standard_normal((len(vm0), 10))
+
+    def loss(r):
+        intr, vm = ga.apply_residuals(intr0, vm0, r)
+        return ga.loss_and_grads(intr, vm, pairs, M.offsets, M.matches, w)
+
+    L, d_intr, d_vm = loss(res)
+    g = ga.residual_vjp(intr0, vm0, res, d_intr, d_vm)
+    h = 1e-6
+    for idx in np.ndindex(res.shape):
+        r = res.copy()
+        r[idx] += h
+        Lp = loss(r)[0]
+        r[idx] -= 2 * h
+        Lm = loss(r)[0]
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * (1 + abs(fd)), (idx, fd, g[idx])
+    assert np.abs(g).max() > 1e-2
