@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-ga", action="store_true", help="skip the global-alignment workload")
+    ap.add_argument("--only", choices=["ga"], default=None,
+                    help="run only the named secondary workload and print its figures (for profiling)")
     ap.add_argument("--extra", action="store_true",
                     help="also time the uneven multi-scene batch and the dense-view joint pose step")
     ap.add_argument("--ref-fraction", type=float, default=1.0 / 16.0,
@@ -658,6 +660,10 @@ def main():
         out = run_reference(args, rank, world)
         if out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.only == "ga":
+        import torch
+        print(json.dumps(run_ga(torch.device("cuda", local_rank))), flush=True)
         return
     if world > 1:
         import torch

@@ -320,7 +320,8 @@ int gs_ga_epipolar(const gs_ga_problem *p, float *dist, float *pair_sums, const 
  * p->viewmats must point at), the loss at those cameras, dL/d(residuals) to
  * d_residuals (DEVICE [n,10], or NULL), and updates residuals, exp_avg and
  * exp_avg_sq in place with Adam (bias-corrected with the incremented step,
- * 1 - beta formed in double): p <- p - lr m^ / (sqrt(v^) + eps). */
+ * 1 - beta formed in double, 1 - beta^t as -expm1(t ln beta) in float;
+ * 0 < beta < 1): p <- p - lr m^ / (sqrt(v^) + eps). */
 typedef struct gs_ga_state {
     int n_cams;
     const float *intrinsics0;   /* DEVICE [n_cams,4] */

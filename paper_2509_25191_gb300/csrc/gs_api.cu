@@ -353,7 +353,7 @@ int gs_ga_step(const gs_ga_state *s, const gs_ga_problem *p, float *pair_sums, c
         !s->exp_avg_sq || !s->step || !s->intrinsics || !s->viewmats || p->intrinsics != s->intrinsics ||
         p->viewmats != s->viewmats)
         return GS_ERR_ARG;
-    if (!(s->beta1 >= 0.0 && s->beta1 < 1.0 && s->beta2 >= 0.0 && s->beta2 < 1.0 && s->eps >= 0.0)) return GS_ERR_ARG;
+    if (!(s->beta1 > 0.0 && s->beta1 < 1.0 && s->beta2 > 0.0 && s->beta2 < 1.0 && s->eps >= 0.0)) return GS_ERR_ARG;
     if (p->n_cams < 1 || p->n_cams > GS_GA_MAX_CAMS || p->n_pairs < 0 || p->n_matches < 0 || !loss ||
         2 * p->n_pairs > 0x7fffffffLL)
         return GS_ERR_ARG;

@@ -5,7 +5,8 @@
 // statistics (Eq. 4) of the initial distances.
 //
 // The per-iteration work is k_ga_pairs (one block per image pair, 20 bytes
-// per match streamed once, HBM-bound) followed by the tiny k_ga_cams. The
+// per match streamed once with four loads in flight per thread, HBM-bound)
+// followed by the tiny k_ga_total and k_ga_cams. The
 // distance is evaluated in normalised coordinates, s = x^'^T E x^ with
 // x^ = K_i^-1 x, x^' = K_j^-1 x', which is x'^T F x without forming F, and
 // the gradient is accumulated per pair as G^ = sum_k a^_k x^_k^T with
@@ -17,7 +18,7 @@
 
 namespace gsk {
 
-constexpr int GA_THREADS = 256;
+constexpr int GA_THREADS = 128;
 constexpr int GA_CAM_THREADS = 128;
 constexpr int GA_SEL_THREADS = 1024;
 constexpr int GA_RADIX_BINS = 2048;
@@ -112,7 +113,6 @@ __device__ __forceinline__ void ga_match(const GaPairGeom &g, float4 q, float w,
 }
 
 constexpr int GA_UNROLL = 4;
-
 template <bool WRITE_DIST>
 __global__ void __launch_bounds__(GA_THREADS) k_ga_pairs(const gs_ga_problem P, float *__restrict__ dist,
                                                          float *__restrict__ pair_sums, int32_t *status) {
@@ -204,16 +204,52 @@ __device__ __forceinline__ void block_sum_cam(float (&v)[NV], float (*s_red)[NV]
 }
 
 // ---------------------------------------------------------------------------
+// Totals over all pairs in a fixed order (one block): the loss
+// sum w e / sum w, and 1 / sum w for the camera gradients (stored in the pad
+// slot of pair 0's partial sums).
+// ---------------------------------------------------------------------------
+constexpr int GA_TOTAL_THREADS = 1024;
+
+__global__ void __launch_bounds__(GA_TOTAL_THREADS) k_ga_total(long long n_pairs, float *pair_sums, float *loss) {
+    __shared__ float s_we[GA_TOTAL_THREADS / 32], s_w[GA_TOTAL_THREADS / 32];
+    float we = 0.f, w = 0.f;
+    for (long long m = threadIdx.x; m < n_pairs; m += GA_TOTAL_THREADS) {
+        we += pair_sums[m * GS_GA_PAIR_FLOATS + 9];
+        w += pair_sums[m * GS_GA_PAIR_FLOATS + 10];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        we += __shfl_xor_sync(0xffffffffu, we, o);
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_we[threadIdx.x >> 5] = we;
+        s_w[threadIdx.x >> 5] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.f, b = 0.f;
+        for (int k = 0; k < GA_TOTAL_THREADS / 32; ++k) {
+            a += s_we[k];
+            b += s_w[k];
+        }
+        const float inv = b > 0.f ? 1.f / b : 0.f;
+        loss[0] = a * inv;
+        if (n_pairs > 0) pair_sums[GS_GA_PAIR_FLOATS - 1] = inv;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Per camera: chain every incident pair's G^ to (fx, fy, cx, cy, R, t),
-// reduce in a fixed order and divide by W = sum of all weights. Block 0 also
-// writes the loss.
+// reduce in a fixed order and divide by W = sum of all weights.
 // ---------------------------------------------------------------------------
 struct GaStepArgs {
     const float *intr0, *vm0;
     float *res, *m, *v, *d_res;
     const int32_t *step;
     float lr, eps;
-    double b1, b2;
+    float b1, b2, omb1, omb2;   // beta and 1 - beta (formed in double on the host)
+    float lnb1, lnb2;           // ln beta (double on the host)
     int focal;
 };
 
@@ -224,18 +260,9 @@ __global__ void __launch_bounds__(GA_CAM_THREADS) k_ga_cams(const gs_ga_problem 
                                                             const int32_t *__restrict__ cam_offsets,
                                                             const int32_t *__restrict__ cam_pairs, float *loss,
                                                             float *d_intr, float *d_vm, const GaStepArgs S) {
-    __shared__ float s_red2[GA_CAM_THREADS / 32][2];
     __shared__ float s_red16[GA_CAM_THREADS / 32][16];
-    float tot[2] = {0.f, 0.f};
-    for (long long m = threadIdx.x; m < P.n_pairs; m += GA_CAM_THREADS) {
-        tot[0] += pair_sums[m * GS_GA_PAIR_FLOATS + 9];
-        tot[1] += pair_sums[m * GS_GA_PAIR_FLOATS + 10];
-    }
-    block_sum_cam(tot, s_red2);
-    const float W = tot[1];
-    const float invW = W > 0.f ? 1.f / W : 0.f;
-    if (blockIdx.x == 0 && threadIdx.x == 0) loss[0] = tot[0] * invW;
-    if (!STEP && (!d_intr || !d_vm)) return;
+    // 1 / sum of all weights, left by k_ga_total in the pad slot of row 0
+    const float invW = P.n_pairs > 0 ? pair_sums[GS_GA_PAIR_FLOATS - 1] : 0.f;
     const int c = blockIdx.x;
     float g[16];
 #pragma unroll
@@ -428,16 +455,16 @@ __device__ void ga_residual_step(const GaStepArgs &S, int c, const float gI[4], 
 #pragma unroll
         for (int k = 0; k < 10; ++k) S.d_res[10 * c + k] = g[k];
     // Adam with the bias correction of the incremented step
-    const int t = S.step[0];
-    const float b1 = (float)S.b1, b2 = (float)S.b2;
-    const float omb1 = (float)(1.0 - S.b1), omb2 = (float)(1.0 - S.b2);
-    const float ibc1 = (float)(1.0 / (1.0 - pow(S.b1, (double)t)));
-    const float ibc2 = (float)(1.0 / (1.0 - pow(S.b2, (double)t)));
+    // 1 - beta^t = -expm1(t ln beta): accurate in float for every t (no
+    // cancellation at small t), and no FP64 on the device
+    const float t = (float)S.step[0];
+    const float ibc1 = -1.f / expm1f(t * S.lnb1);
+    const float ibc2 = -1.f / expm1f(t * S.lnb2);
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
         float m = S.m[10 * c + k], v = S.v[10 * c + k];
-        m = b1 * m + omb1 * g[k];
-        v = b2 * v + omb2 * g[k] * g[k];
+        m = S.b1 * m + S.omb1 * g[k];
+        v = S.b2 * v + S.omb2 * g[k] * g[k];
         S.m[10 * c + k] = m;
         S.v[10 * c + k] = v;
         res[k] -= S.lr * (m * ibc1) / (sqrtf(v * ibc2) + S.eps);
@@ -739,6 +766,11 @@ __global__ void k_ga_radix_pick(int shift, int bits, uint32_t *scratch, float *s
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// One block per pair (the hardware scheduler balances pairs of unequal size).
+static unsigned ga_pairs_grid(long long n_pairs) {
+    return (unsigned)(n_pairs < (1LL << 30) ? n_pairs : (1LL << 30));
+}
+
 int launch_ga_select(const float *vm, int n, float cos_thr, int32_t *pairs, long long capacity, long long *n_out,
                      int32_t *status, cudaStream_t st) {
     const size_t smem = sizeof(long long) * (size_t)(n + 1);
@@ -762,14 +794,16 @@ int launch_ga_epipolar(const gs_ga_problem &P, float *dist, float *pair_sums, co
                        const int32_t *cam_pairs, float *loss, float *d_intr, float *d_vm, int32_t *status,
                        cudaStream_t st) {
     if (P.n_pairs > 0) {
-        const long long grid = P.n_pairs < (1LL << 30) ? P.n_pairs : (1LL << 30);
-        if (dist) k_ga_pairs<true><<<(unsigned)grid, GA_THREADS, 0, st>>>(P, dist, pair_sums, status);
-        else k_ga_pairs<false><<<(unsigned)grid, GA_THREADS, 0, st>>>(P, dist, pair_sums, status);
+        const unsigned grid = ga_pairs_grid(P.n_pairs);
+        if (dist) k_ga_pairs<true><<<grid, GA_THREADS, 0, st>>>(P, dist, pair_sums, status);
+        else k_ga_pairs<false><<<grid, GA_THREADS, 0, st>>>(P, dist, pair_sums, status);
         if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
     }
-    const bool grads = d_intr && d_vm;
-    k_ga_cams<false><<<grads ? P.n_cams : 1, GA_CAM_THREADS, 0, st>>>(
-        P, pair_sums, cam_offsets, cam_pairs, loss, grads ? d_intr : nullptr, grads ? d_vm : nullptr, GaStepArgs{});
+    k_ga_total<<<1, GA_TOTAL_THREADS, 0, st>>>(P.n_pairs, pair_sums, loss);
+    if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
+    if (d_intr && d_vm)
+        k_ga_cams<false><<<P.n_cams, GA_CAM_THREADS, 0, st>>>(P, pair_sums, cam_offsets, cam_pairs, loss, d_intr,
+                                                               d_vm, GaStepArgs{});
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
@@ -785,16 +819,21 @@ int launch_ga_step(const gs_ga_state &s, const gs_ga_problem &P, float *pair_sum
     S.step = s.step;
     S.lr = s.lr;
     S.eps = (float)s.eps;
-    S.b1 = s.beta1;
-    S.b2 = s.beta2;
+    S.b1 = (float)s.beta1;
+    S.b2 = (float)s.beta2;
+    S.omb1 = (float)(1.0 - s.beta1);
+    S.omb2 = (float)(1.0 - s.beta2);
+    S.lnb1 = (float)log(s.beta1);
+    S.lnb2 = (float)log(s.beta2);
     S.focal = s.optimise_focal;
     k_ga_apply<<<(s.n_cams + 127) / 128, 128, 0, st>>>(S, s.n_cams, s.intrinsics, s.viewmats, s.step);
     if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
     if (P.n_pairs > 0) {
-        const long long grid = P.n_pairs < (1LL << 30) ? P.n_pairs : (1LL << 30);
-        k_ga_pairs<false><<<(unsigned)grid, GA_THREADS, 0, st>>>(P, nullptr, pair_sums, status);
+        k_ga_pairs<false><<<ga_pairs_grid(P.n_pairs), GA_THREADS, 0, st>>>(P, nullptr, pair_sums, status);
         if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
     }
+    k_ga_total<<<1, GA_TOTAL_THREADS, 0, st>>>(P.n_pairs, pair_sums, loss);
+    if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
     k_ga_cams<true><<<P.n_cams, GA_CAM_THREADS, 0, st>>>(P, pair_sums, cam_offsets, cam_pairs, loss, nullptr,
                                                           nullptr, S);
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
