@@ -294,6 +294,19 @@ def run_native(args, rank, world, local_rank):
         hbm = peaks["hbm_gbs"]
         roof = {"kernel": names[top], "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                 "traffic": None}
+    # the same step with the L1 + D-SSIM loss of Section 3.1 (fused kernel), and that kernel alone
+    dstep = GraphStep(g, views, target, tile=tile, loss="l1_dssim")
+    dssim = {"ms_per_step": round(_time_replays(dstep, 50), 4)}
+    dssim["mpix_s"] = round(P / dssim["ms_per_step"] / 1e3, 2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(20):
+        _lib.gs_l1_dssim_loss(views, dstep.image, dstep.target, dstep.loss, dstep.dimg, 0.2)
+    ev1.record()
+    torch.cuda.synchronize()
+    dssim["loss_kernel_ms"] = round(ev0.elapsed_time(ev1) / 20, 4)
+    dssim["loss"] = [round(float(v), 6) for v in dstep.loss.cpu()]
+    del dstep
     # test-time pose tuning (Gaussians frozen): the same step with the backward to the pose only
     pstep = GraphStep(g, views, target, tile=tile, want_gaussian_grads=False)
     pose_only = {"ms_per_step": round(_time_replays(pstep, 50), 4)}
@@ -322,6 +335,7 @@ def run_native(args, rank, world, local_rank):
         "autotune": tuning,
         "clocks": clocks,
         "pose_only_step": pose_only,
+        "l1_dssim_step": dssim,
         "batched_vs_plain": batched,
         "other_workloads": extra,
         "e2e": e2e,

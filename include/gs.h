@@ -241,6 +241,21 @@ typedef struct gs_adam_group {
 int gs_sgld_adam_step(const gs_adam_group *groups, int n_groups, int step, double beta1, double beta2, double eps,
                       const float *noise, float noise_scale, int noise_group, void *stream);
 
+/* Photometric loss with D-SSIM (Section 3.1: a weighted sum of an L1 and a
+ * D-SSIM term; weighting and SSIM settings of the cited 3DGS training):
+ *   L = (1 - lambda) mean|x - y| + lambda (1 - mean SSIM(x, y)),
+ * SSIM per channel of every view from local statistics under an 11x11
+ * Gaussian window (sigma 1.5, normalised) as a same-size correlation with
+ * zero padding, C1 = 0.01^2, C2 = 0.03^2, both means over all values of all
+ * views. image, target: DEVICE, views concatenated, each [3,H,W] (the layout
+ * of gs_render_fwd; only views->n_views, width, height are read). loss:
+ * DEVICE [3] = {L, mean L1, 1 - mean SSIM} (overwritten); dL_dimage: DEVICE,
+ * same layout (overwritten). 0 <= lambda <= 1. One fused forward+backward
+ * kernel over 32x32 tiles; the loss sums use atomics (the gradient is
+ * deterministic, the last bits of the loss are not). */
+int gs_l1_dssim_loss(const gs_views *views, const float *image, const float *target, float lambda, float *loss,
+                     float *dL_dimage, void *stream);
+
 /* ------------------------------------------------------------------------
  * Camera global alignment (paper Section 3.3, Eqs. 2-4).
  *

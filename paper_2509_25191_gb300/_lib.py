@@ -25,7 +25,7 @@ EXPORTED = ["gs_config_default", "gs_num_slots", "gs_slot_base", "gs_num_tiles",
             "gs_num_image_floats", "gs_pixel_base", "gs_pose_blocks", "gs_project", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version",
             "gs_project_bwd_noalloc", "gs_sgld_adam_step", "gs_ga_select_pairs", "gs_ga_incidence",
-            "gs_ga_epipolar", "gs_ga_weights_scratch_bytes", "gs_ga_weights", "gs_ga_step"]
+            "gs_ga_epipolar", "gs_ga_weights_scratch_bytes", "gs_ga_weights", "gs_ga_step", "gs_l1_dssim_loss"]
 GS_GA_MAX_CAMS = 8192
 GS_GA_PAIR_FLOATS = 12
 GS_GA_MAX_BINS = 16384
@@ -400,6 +400,13 @@ def pair_counts(bins: Bins):
 def gs_pose_grad(views: Views, pose_partials, n_blocks, dL_dviewmat, dL_dtwist=None, stream=None):
     _check(load().gs_pose_grad(ctypes.byref(views.c()), _ptr(pose_partials), int(n_blocks), _ptr(dL_dviewmat),
                                _ptr(dL_dtwist), _stream(stream)), "gs_pose_grad")
+
+
+def gs_l1_dssim_loss(views: Views, image, target, loss, dL_dimage, lam=0.2, stream=None):
+    """L1 + D-SSIM loss (loss [3] = total, mean L1, 1 - mean SSIM) and its
+    gradient, views concatenated [3,H,W] each."""
+    _check(load().gs_l1_dssim_loss(ctypes.byref(views.c()), _ptr(image), _ptr(target), ctypes.c_float(lam),
+                                   _ptr(loss), _ptr(dL_dimage), _stream(stream)), "gs_l1_dssim_loss")
 
 
 def gs_l1_loss(image, target, loss, dL_dimage, stream=None):

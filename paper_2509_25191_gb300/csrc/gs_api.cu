@@ -32,6 +32,8 @@ int launch_ga_epipolar(const gs_ga_problem &P, float *dist, float *pair_sums, co
                        cudaStream_t st);
 int launch_ga_weights(const float *e, long long n, int nb, double alpha, uint32_t *counts, float *w, float *stats,
                       uint32_t *scratch, cudaStream_t st);
+int launch_l1_dssim(const int *W, const int *H, int n_views, const float *image, const float *target, float lambda,
+                    float *loss, float *grad, cudaStream_t st);
 int launch_ga_step(const gs_ga_state &s, const gs_ga_problem &P, float *pair_sums, const int32_t *cam_offsets,
                    const int32_t *cam_pairs, float *loss, float *d_res, int32_t *status, cudaStream_t st);
 
@@ -312,6 +314,18 @@ int gs_sgld_adam_step(const gs_adam_group *groups, int n_groups, int step, doubl
     if (noise && (noise_group < 0 || noise_group >= n_groups)) return GS_ERR_ARG;
     return launch_adam_sgld(groups, n_groups, step, beta1, beta2, eps, noise, noise_scale, noise_group,
                             (cudaStream_t)stream);
+}
+
+int gs_l1_dssim_loss(const gs_views *views, const float *image, const float *target, float lambda, float *loss,
+                     float *dL_dimage, void *stream) {
+    if (!views || views->n_views < 1 || views->n_views > GS_MAX_VIEWS || !views->width || !views->height ||
+        !image || !target || !loss || !dL_dimage || !(lambda >= 0.f && lambda <= 1.f))
+        return GS_ERR_ARG;
+    for (int v = 0; v < views->n_views; ++v)
+        if (views->width[v] < 1 || views->height[v] < 1 || (long long)views->width[v] * views->height[v] > (1LL << 40))
+            return GS_ERR_ARG;
+    return launch_l1_dssim(views->width, views->height, views->n_views, image, target, lambda, loss, dL_dimage,
+                           (cudaStream_t)stream);
 }
 
 int gs_ga_select_pairs(const float *viewmats, int n_cams, double max_angle_deg, int32_t *pairs, int64_t capacity,

@@ -1,7 +1,7 @@
 """One training step of the rasterizer, captured as a CUDA graph.
 
 A step over a batch of views is: gs_project -> gs_bin_sort -> gs_render_fwd
--> gs_l1_loss (against the step's target images) -> gs_rasterize_bwd ->
+-> gs_l1_loss or gs_l1_dssim_loss (against the step's target images) -> gs_rasterize_bwd ->
 gs_project_bwd -> gs_pose_grad, i.e. the photometric supervision of
 Section 3.1 with gradients to every Gaussian parameter and to every view's
 pose (Section 3.4). All buffers are allocated once; the tile-instance
@@ -30,9 +30,12 @@ class GraphStep:
     KERNELS_PER_STEP = 11   # project 1, bin/sort 5, render 1, loss 1, raster bwd 1, projection bwd 1, pose 1
 
     def __init__(self, g: Gaussians, views: Views, target, tile=(16, 16), headroom=1.25, capture=True,
-                 want_gaussian_grads=True):
+                 want_gaussian_grads=True, loss="l1", lam=0.2):
         self.g, self.views, self.target = g, views, target
         self.want = want_gaussian_grads
+        if loss not in ("l1", "l1_dssim"):
+            raise ValueError(f"unknown loss {loss!r}")
+        self.loss_kind, self.lam = loss, float(lam)
         dev = g.means.device
         self.rast = Rasterizer(tile=tile)
         _, _ = self.rast.forward(g, views)
@@ -43,7 +46,8 @@ class GraphStep:
         self.proj = torch.empty(max(1, views.num_slots()), _lib.GS_RECORD_FLOATS, device=dev)
         self.image = torch.empty(views.num_image_floats(), device=dev)
         self.dimg = torch.empty_like(self.image)
-        self.loss = torch.empty(1, device=dev)
+        # l1: [mean L1]; l1_dssim: [total, mean L1, 1 - mean SSIM]
+        self.loss = torch.empty(1 if loss == "l1" else 3, device=dev)
         self.grads = Grads(g.n, g.sh_degree, views.num_slots(), views.n, dev, want_gaussian_grads)
         self.dviewmat = torch.empty(views.n, 12, device=dev)
         self.dtwist = torch.empty(views.n, 6, device=dev)
@@ -64,7 +68,10 @@ class GraphStep:
         rec()
         _lib.gs_render_fwd(v, cfg, self.proj, b, self.image, st)
         rec()
-        _lib.gs_l1_loss(self.image, self.target, self.loss, self.dimg)
+        if self.loss_kind == "l1":
+            _lib.gs_l1_loss(self.image, self.target, self.loss, self.dimg)
+        else:
+            _lib.gs_l1_dssim_loss(v, self.image, self.target, self.loss, self.dimg, self.lam)
         rec()
         _lib.gs_rasterize_bwd(v, cfg, self.proj, b, self.image, self.dimg, self.grads.grad2d, st)
         rec()
