@@ -43,6 +43,55 @@ __device__ __forceinline__ bool slot_rect(const Launch &L, const float4 *__restr
     return true;
 }
 
+// Warp-cooperative walk over the tiles of the 32 lanes' rectangles: the
+// lanes' tile counts are prefix-summed across the warp and the flattened
+// list of (lane, tile) items is processed 32 at a time, so every lane stays
+// busy whatever the mix of rectangle sizes (a per-lane loop over its own
+// rectangle leaves most lanes idle). For each item, f(tile index in the view,
+// the owner lane's payload words a, b) runs on the lane that took it. All 32
+// lanes must call this.
+template <typename F>
+__device__ __forceinline__ void warp_rect_walk(bool valid, int x0, int x1, int y0, int y1, int gx, unsigned int pa,
+                                               unsigned int pb, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const int w = valid ? x1 - x0 : 0;
+    const int n = valid ? w * (y1 - y0) : 0;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - n;
+    const float rw = w > 0 ? 1.f / (float)w : 0.f;
+    for (int base = 0; base < total; base += 32) {
+        const int fi = base + lane;
+        // owner = number of lanes whose inclusive count is <= fi
+        int own = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, own + step - 1);
+            if (v <= fi) own += step;
+        }
+        const int ox0 = __shfl_sync(0xffffffffu, x0, own);
+        const int oy0 = __shfl_sync(0xffffffffu, y0, own);
+        const int ow = __shfl_sync(0xffffffffu, w, own);
+        const int oex = __shfl_sync(0xffffffffu, excl, own);
+        const float orw = __shfl_sync(0xffffffffu, rw, own);
+        const unsigned int opa = __shfl_sync(0xffffffffu, pa, own);
+        const unsigned int opb = __shfl_sync(0xffffffffu, pb, own);
+        if (fi < total) {
+            const int local = fi - oex;
+            int dy = (int)(((float)local + 0.5f) * orw);   // exact after the correction below
+            if (dy * ow > local) --dy;
+            else if ((dy + 1) * ow <= local) ++dy;
+            const int dx = local - dy * ow;
+            f((oy0 + dy) * gx + ox0 + dx, opa, opb);
+        }
+    }
+}
+
 // next view segment [seg, seg_end) of a chunk that ends at c1
 __device__ __forceinline__ long long segment_end(const Launch &L, int v, long long c1) {
     const long long e = (v + 1 < L.n_views) ? L.v[v + 1].slot_base : L.n_slots;
@@ -64,14 +113,14 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_count(const Launch L, const
             for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) s_cnt[t] = 0;
             __syncthreads();
         }
-        for (long long p = seg + threadIdx.x; p < seg_end; p += BIN_THREADS) {
-            int x0, x1, y0, y1;
-            if (!slot_rect(L, proj, p, vd, x0, x1, y0, y1)) continue;
-            for (int ty = y0; ty < y1; ++ty)
-                for (int tx = x0; tx < x1; ++tx) {
-                    if (on_chip) atomicAdd(s_cnt + ty * vd.Gx + tx, 1);
-                    else atomicAdd(tile_count + vd.tile_base + ty * vd.Gx + tx, 1);
-                }
+        for (long long pb = seg; pb < seg_end; pb += BIN_THREADS) {   // uniform trip count: whole warps walk
+            const long long p = pb + threadIdx.x;
+            int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+            const bool valid = p < seg_end && slot_rect(L, proj, p, vd, x0, x1, y0, y1);
+            warp_rect_walk(valid, x0, x1, y0, y1, vd.Gx, 0u, 0u, [&](int t, unsigned int, unsigned int) {
+                if (on_chip) atomicAdd(s_cnt + t, 1);
+                else atomicAdd(tile_count + vd.tile_base + t, 1);
+            });
         }
         if (on_chip) {
             __syncthreads();
@@ -194,11 +243,12 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, con
         if (on_chip) {
             for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) s_cnt[t] = 0;
             __syncthreads();
-            for (long long p = seg + threadIdx.x; p < seg_end; p += BIN_THREADS) {
-                int x0, x1, y0, y1;
-                if (!slot_rect(L, proj, p, vd, x0, x1, y0, y1)) continue;
-                for (int ty = y0; ty < y1; ++ty)
-                    for (int tx = x0; tx < x1; ++tx) atomicAdd(s_cnt + ty * vd.Gx + tx, 1);
+            for (long long pb = seg; pb < seg_end; pb += BIN_THREADS) {
+                const long long p = pb + threadIdx.x;
+                int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+                const bool valid = p < seg_end && slot_rect(L, proj, p, vd, x0, x1, y0, y1);
+                warp_rect_walk(valid, x0, x1, y0, y1, vd.Gx, 0u, 0u,
+                               [&](int t, unsigned int, unsigned int) { atomicAdd(s_cnt + t, 1); });
             }
             __syncthreads();
             for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) {
@@ -207,18 +257,17 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, con
             }
             __syncthreads();
         }
-        for (long long p = seg + threadIdx.x; p < seg_end; p += BIN_THREADS) {
-            int x0, x1, y0, y1;
-            if (!slot_rect(L, proj, p, vd, x0, x1, y0, y1)) continue;
-            const float depth = proj[4 * p + 3].z;
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned long long)(unsigned int)p;
-            for (int ty = y0; ty < y1; ++ty)
-                for (int tx = x0; tx < x1; ++tx) {
-                    const int t = ty * vd.Gx + tx;
-                    const int pos = on_chip ? atomicAdd(s_cnt + t, 1) : atomicAdd(cursor + vd.tile_base + t, 1);
-                    keys[pos] = key;
-                }
+        for (long long pb = seg; pb < seg_end; pb += BIN_THREADS) {
+            const long long p = pb + threadIdx.x;
+            int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+            const bool valid = p < seg_end && slot_rect(L, proj, p, vd, x0, x1, y0, y1);
+            const unsigned int dbits = valid ? __float_as_uint(proj[4 * p + 3].z) : 0u;
+            const unsigned int pl = (unsigned int)p;
+            // payload: the owner's key = (depth bits << 32) | slot
+            warp_rect_walk(valid, x0, x1, y0, y1, vd.Gx, dbits, pl, [&](int t, unsigned int hi, unsigned int lo) {
+                const int pos = on_chip ? atomicAdd(s_cnt + t, 1) : atomicAdd(cursor + vd.tile_base + t, 1);
+                keys[pos] = ((unsigned long long)hi << 32) | lo;
+            });
         }
         if (on_chip) __syncthreads();
         seg = seg_end;
