@@ -211,7 +211,13 @@ def run_native(args, rank, world, local_rank):
         torch.cuda.synchronize()
         acc += [ev[i].elapsed_time(ev[i + 1]) for i in range(len(names))]
     stage_ms = acc / reps
+    # pixel-Gaussian pair counts of the raster backward: one extra eager step
+    # with counting switched on (the timed step does not count)
+    step.cfg.count_pairs = 1
+    step.run()
+    torch.cuda.synchronize()
     pairs = _lib.pair_counts(bins)
+    step.cfg.count_pairs = 0
     n_inst = int(bins.counters[0].item())
 
     graph = step.graph

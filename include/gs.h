@@ -70,6 +70,8 @@ typedef struct gs_config {
     float t_min;          /* [1e-4] stop before transmittance would fall below this */
     float fov_clamp;      /* [1.3] clamp x/z, y/z to +-fov_clamp*tan(half fov) inside J */
     float bg[3];          /* [0,0,0] background colour */
+    int count_pairs;      /* [0] if nonzero, the raster backward also counts the pixel-Gaussian pairs it
+                             evaluates and composites into bins->counters (diagnostics; costs time) */
 } gs_config;
 
 /* Gaussians (all DEVICE, float32, contiguous). Several scenes may be

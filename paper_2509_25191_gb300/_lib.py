@@ -42,7 +42,7 @@ class gs_config(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("pixel_gate", ctypes.c_int),
                 ("near_z", ctypes.c_float), ("dilation", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float), ("fov_clamp", ctypes.c_float),
-                ("bg", ctypes.c_float * 3)]
+                ("bg", ctypes.c_float * 3), ("count_pairs", ctypes.c_int)]
 
 
 class gs_gaussians(ctypes.Structure):
@@ -139,7 +139,7 @@ def _stream(stream):
 # ---------------------------------------------------------------------------
 
 def config(tile=(16, 16), pixel_gate=True, bg=(0.0, 0.0, 0.0), near=0.2, dilation=0.3,
-           alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, fov_clamp=1.3) -> gs_config:
+           alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, fov_clamp=1.3, count_pairs=False) -> gs_config:
     c = gs_config()
     load().gs_config_default(ctypes.byref(c))
     c.tile_w, c.tile_h = int(tile[0]), int(tile[1])
@@ -147,6 +147,7 @@ def config(tile=(16, 16), pixel_gate=True, bg=(0.0, 0.0, 0.0), near=0.2, dilatio
     c.near_z, c.dilation, c.alpha_min, c.alpha_max, c.t_min, c.fov_clamp = \
         near, dilation, alpha_min, alpha_max, t_min, fov_clamp
     c.bg = (ctypes.c_float * 3)(*bg)
+    c.count_pairs = int(bool(count_pairs))
     return c
 
 
@@ -392,7 +393,8 @@ def gs_ga_weights(dist, n_bins, alpha, counts, weights, stats, scratch, stream=N
 
 def pair_counts(bins: Bins):
     """(fwd evaluated, fwd composited, bwd evaluated, bwd composited) pixel-
-    Gaussian pairs of the last render calls (reads the device counters)."""
+    Gaussian pairs of the last render calls (reads the device counters; the
+    backward counts only when its config has count_pairs set)."""
     c = bins.counters.cpu().numpy().view(np.int64)
     return int(c[4]), int(c[5]), int(c[6]), int(c[7])
 

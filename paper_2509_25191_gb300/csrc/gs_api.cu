@@ -75,6 +75,7 @@ static int build_launch(const gs_views *vw, const gs_config *cfg, Launch &L) {
     L.t_min = cfg->t_min;
     L.fov_clamp = cfg->fov_clamp;
     L.bg[0] = cfg->bg[0]; L.bg[1] = cfg->bg[1]; L.bg[2] = cfg->bg[2];
+    L.count_pairs = cfg->count_pairs != 0;
     if (!(L.alpha_max > 0.f && L.alpha_max < 1.f) || !(L.t_min > 0.f)) return GS_ERR_ARG;
     long long slot = 0, pix = 0, tiles = 0;
     for (int v = 0; v < V; ++v) {
@@ -148,6 +149,7 @@ void gs_config_default(gs_config *cfg) {
     cfg->t_min = 1e-4f;
     cfg->fov_clamp = 1.3f;
     cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.0f;
+    cfg->count_pairs = 0;
 }
 
 int64_t gs_num_slots(const gs_views *vw) {

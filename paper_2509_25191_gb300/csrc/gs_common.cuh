@@ -35,6 +35,7 @@ struct Launch {
     long long n_threads;    // sum of scene sizes (per-Gaussian grids)
     int n_tiles;            // T
     int pixel_gate;
+    int count_pairs;        // the raster backward also counts pixel-Gaussian pairs
     float near_z, dilation, alpha_min, alpha_max, t_min, fov_clamp;
     float bg[3];
     ViewDesc v[GS_MAX_VIEWS];

@@ -305,14 +305,15 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
 // advancing the pixel's transmittance and colour sum exactly as the forward.
 // Returns 0 if the Gaussian was not evaluated at this pixel, 1 if its alpha
 // was evaluated but it was not composited, 2 if it was composited.
-__device__ __forceinline__ int pixel_grad(const float4 &xy, const float4 &con, const float4 &c, float pcx,
+__device__ __forceinline__ int pixel_grad(const float4 &xy, const float4 &con, const float4 &c, float2 ad, float pcx,
                                            float pcy, const Launch &L, float img0, float img1, float img2,
                                            float g0, float g1, float g2, float &T, float &C0, float &C1, float &C2,
                                            bool &done, float *gv) {
     float alpha, G = 0.f, dx, dy, u;
     bool clamped;
     if (!eval_alpha(xy, con, pcx, pcy, L.alpha_min, L.alpha_max, alpha, G, dx, dy, u, clamped)) return G > 0.f;
-    const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+    const float oma = __fsub_rn(1.f, alpha);
+    const float Tn = __fmul_rn(T, oma);
     if (Tn < L.t_min) {
         done = true;
         return 1;
@@ -324,9 +325,11 @@ __device__ __forceinline__ int pixel_grad(const float4 &xy, const float4 &con, c
     gv[6] += w * g0;
     gv[7] += w * g1;
     gv[8] += w * g2;
-    // colour behind this Gaussian: image - running sum
+    // colour behind this Gaussian: image - running sum; 1 - alpha >= 0.01, so
+    // the fast reciprocal's few-ulp error is far inside the gradient tolerance
     const float S0 = img0 - C0, S1 = img1 - C1, S2 = img2 - C2;
-    const float dL_dalpha = T * (c.x * g0 + c.y * g1 + c.z * g2) - (S0 * g0 + S1 * g1 + S2 * g2) / (1.f - alpha);
+    const float dL_dalpha =
+        T * (c.x * g0 + c.y * g1 + c.z * g2) - __fdividef(S0 * g0 + S1 * g1 + S2 * g2, oma);
     if (!clamped) {
         // alpha = o G, G = exp(power), power = -1/2 d^T Q d with Q the conic
         // (inverse of the covariance Sigma' = (a, b, c)), d = pixel - mean.
@@ -334,24 +337,24 @@ __device__ __forceinline__ int pixel_grad(const float4 &xy, const float4 &con, c
         // d power / d mean = v and d power / d Sigma' = v v^T / 2, i.e.
         // (v0^2/2, v0 v1, v1^2/2) for (a, b, c): summing these well-scaled
         // terms over pixels avoids the ill-conditioned conic -> covariance
-        // conversion of summed conic gradients for elongated Gaussians.
+        // conversion of summed conic gradients for elongated Gaussians. The
+        // halves of gv[2] and gv[4] are applied once, to the sums.
         gv[5] += dL_dalpha * G;
         const float dp = dL_dalpha * alpha;
-        const float A = con.x * (-2.f * LN2), D = con.z * (-2.f * LN2);
-        const float v0 = A * u;
-        const float v1 = v0 * con.y + D * dy;
+        const float v0 = ad.x * u;
+        const float v1 = v0 * con.y + ad.y * dy;
         const float dv0 = dp * v0, dv1 = dp * v1;
         gv[0] += dv0;
         gv[1] += dv1;
-        gv[2] += 0.5f * dv0 * v0;
+        gv[2] += dv0 * v0;
         gv[3] += dv0 * v1;
-        gv[4] += 0.5f * dv1 * v1;
+        gv[4] += dv1 * v1;
     }
     T = Tn;
     return 2;
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool COUNT>
 __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, const float4 *__restrict__ proj,
                                                             const int2 *__restrict__ ranges,
                                                             const unsigned int *__restrict__ ids,
@@ -361,6 +364,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
                                                             float4 *__restrict__ grad2d) {
     constexpr int BS = TW * TH / 2, NB = TW * TH;
     __shared__ float4 s_xy[NB], s_con[NB], s_rgb[NB];
+    __shared__ float2 s_ad[NB];    // per staged Gaussian: the conic's A and D (natural-log units)
     __shared__ unsigned int s_mask[NB];
     __shared__ float s_g[NB][9];   // per staged Gaussian: summed gradient (odd stride: no bank conflicts)
     __shared__ int s_item;
@@ -402,6 +406,12 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
             if (__syncthreads_count(done[0] && done[1]) == BS) break;
             stage_batch<TW, TH>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = threadIdx.x + h * BS;
+                if (b0 + k < r.y)
+                    s_ad[k] = make_float2(s_con[k].x * (-2.f * LN2), s_con[k].z * (-2.f * LN2));
+            }
             __syncthreads();
             const int nb = min(NB, r.y - b0);
             for (int k = 0; k < nb; ++k) {
@@ -412,15 +422,18 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
                 for (int c = 0; c < 9; ++c) gv[c] = 0.f;
                 bool hit = false;
                 const float4 xy = s_xy[k], con = s_con[k], c = s_rgb[k];
+                const float2 ad = s_ad[k];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     if (done[h]) continue;
-                    const int res = pixel_grad(xy, con, c, ti.pcx, ti.pcy0 + 4.f * h, L, im[h][0], im[h][1],
+                    const int res = pixel_grad(xy, con, c, ad, ti.pcx, ti.pcy0 + 4.f * h, L, im[h][0], im[h][1],
                                                im[h][2], gg[h][0], gg[h][1], gg[h][2], T[h], C[h][0], C[h][1],
                                                C[h][2], done[h], gv);
                     hit |= res == 2;
-                    n_eval += res > 0;
-                    n_comp += res == 2;
+                    if (COUNT) {
+                        n_eval += res > 0;
+                        n_comp += res == 2;
+                    }
                 }
                 if (__any_sync(0xffffffffu, hit)) {
                     const float sum = warp_reduce_scatter9(gv, lane);
@@ -433,7 +446,8 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
             for (int h = 0; h < 2; ++h) {
                 const int k = threadIdx.x + h * BS;
                 if (k < nb) {
-                    const float a0 = s_g[k][0], a1 = s_g[k][1], a2 = s_g[k][2], a3 = s_g[k][3], a4 = s_g[k][4];
+                    const float a0 = s_g[k][0], a1 = s_g[k][1], a2 = 0.5f * s_g[k][2], a3 = s_g[k][3];
+                    const float a4 = 0.5f * s_g[k][4];
                     const float a5 = s_g[k][5], a6 = s_g[k][6], a7 = s_g[k][7], a8 = s_g[k][8];
                     if (a0 != 0.f || a1 != 0.f || a2 != 0.f || a3 != 0.f || a4 != 0.f || a5 != 0.f || a6 != 0.f ||
                         a7 != 0.f || a8 != 0.f) {
@@ -448,7 +462,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
                 }
             }
         }
-        count_pairs(counters, 12, n_eval, n_comp);
+        if (COUNT) count_pairs(counters, 12, n_eval, n_comp);
     }
 }
 
@@ -469,22 +483,30 @@ static int launch_fwd_t(const Launch &L, const float *proj, const gs_bins *b, fl
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
-template <int TW, int TH>
-static int launch_bwd_t(const Launch &L, const float *proj, const gs_bins *b, const float *image,
+template <int TW, int TH, bool COUNT>
+static int launch_bwd_c(const Launch &L, const float *proj, const gs_bins *b, const float *image,
                         const float *dL_dimage, float *grad2d, cudaStream_t st) {
     static int blocks_per_sm = 0;
     if (!blocks_per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_bwd<TW, TH>, TW * TH / 2, 0) !=
-                cudaSuccess || blocks_per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_bwd<TW, TH, COUNT>, TW * TH / 2,
+                                                          0) != cudaSuccess ||
+            blocks_per_sm < 1)
             blocks_per_sm = 1;
     }
     const int grid = min(num_sms() * blocks_per_sm, max(1, L.n_tiles));
     if (cudaMemsetAsync(b->counters + CNT_Q_BWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
-    k_render_bwd<TW, TH><<<grid, TW * TH / 2, 0, st>>>(L, reinterpret_cast<const float4 *>(proj),
-                                                       reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
-                                                       b->tile_order, b->counters, image, dL_dimage,
-                                                       reinterpret_cast<float4 *>(grad2d));
+    k_render_bwd<TW, TH, COUNT><<<grid, TW * TH / 2, 0, st>>>(L, reinterpret_cast<const float4 *>(proj),
+                                                              reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
+                                                              b->tile_order, b->counters, image, dL_dimage,
+                                                              reinterpret_cast<float4 *>(grad2d));
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+template <int TW, int TH>
+static int launch_bwd_t(const Launch &L, const float *proj, const gs_bins *b, const float *image,
+                        const float *dL_dimage, float *grad2d, cudaStream_t st) {
+    return L.count_pairs ? launch_bwd_c<TW, TH, true>(L, proj, b, image, dL_dimage, grad2d, st)
+                         : launch_bwd_c<TW, TH, false>(L, proj, b, image, dL_dimage, grad2d, st);
 }
 
 int launch_render_fwd(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st) {
