@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
     __shared__ int s_item;
     const bool abort = counters[CNT_ABORT] != 0;
     const unsigned int wbit = 1u << (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counters + CNT_Q_FWD, 1);
         __syncthreads();
@@ -249,37 +250,44 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
             stage_batch<TW, TH>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
             __syncthreads();
             const int nb = min(NB, r.y - b0);
-            for (int k = 0; k < nb && !(done0 && done1); ++k) {
-                if (!(s_mask[k] & wbit)) continue;
-                const float4 xy = s_xy[k], con = s_con[k];
-                float alpha, G, dx, dy, u;
-                bool clamped;
-                if (!done0 && eval_alpha(xy, con, ti.pcx, ti.pcy0, L.alpha_min, L.alpha_max, alpha, G, dx, dy, u,
-                                         clamped)) {
-                    const float Tn = __fmul_rn(T0, __fsub_rn(1.f, alpha));
-                    if (Tn < L.t_min) {
-                        done0 = true;
-                    } else {
-                        const float w = __fmul_rn(alpha, T0);
-                        const float4 c = s_rgb[k];
-                        C00 = __fmaf_rn(c.x, w, C00);
-                        C01 = __fmaf_rn(c.y, w, C01);
-                        C02 = __fmaf_rn(c.z, w, C02);
-                        T0 = Tn;
+            // the warp walks only the staged Gaussians that may reach its patch:
+            // 32 masks per ballot, then the set bits in order
+            for (int k0 = 0; k0 < nb; k0 += 32) {
+                if (__all_sync(0xffffffffu, done0 && done1)) break;
+                unsigned int hits = __ballot_sync(0xffffffffu, k0 + lane < nb && (s_mask[k0 + lane] & wbit));
+                while (hits) {
+                    const int k = k0 + __ffs(hits) - 1;
+                    hits &= hits - 1;
+                    const float4 xy = s_xy[k], con = s_con[k];
+                    float alpha, G, dx, dy, u;
+                    bool clamped;
+                    if (!done0 && eval_alpha(xy, con, ti.pcx, ti.pcy0, L.alpha_min, L.alpha_max, alpha, G, dx, dy, u,
+                                             clamped)) {
+                        const float Tn = __fmul_rn(T0, __fsub_rn(1.f, alpha));
+                        if (Tn < L.t_min) {
+                            done0 = true;
+                        } else {
+                            const float w = __fmul_rn(alpha, T0);
+                            const float4 c = s_rgb[k];
+                            C00 = __fmaf_rn(c.x, w, C00);
+                            C01 = __fmaf_rn(c.y, w, C01);
+                            C02 = __fmaf_rn(c.z, w, C02);
+                            T0 = Tn;
+                        }
                     }
-                }
-                if (!done1 && eval_alpha(xy, con, ti.pcx, pcy1, L.alpha_min, L.alpha_max, alpha, G, dx, dy, u,
-                                         clamped)) {
-                    const float Tn = __fmul_rn(T1, __fsub_rn(1.f, alpha));
-                    if (Tn < L.t_min) {
-                        done1 = true;
-                    } else {
-                        const float w = __fmul_rn(alpha, T1);
-                        const float4 c = s_rgb[k];
-                        C10 = __fmaf_rn(c.x, w, C10);
-                        C11 = __fmaf_rn(c.y, w, C11);
-                        C12 = __fmaf_rn(c.z, w, C12);
-                        T1 = Tn;
+                    if (!done1 && eval_alpha(xy, con, ti.pcx, pcy1, L.alpha_min, L.alpha_max, alpha, G, dx, dy, u,
+                                             clamped)) {
+                        const float Tn = __fmul_rn(T1, __fsub_rn(1.f, alpha));
+                        if (Tn < L.t_min) {
+                            done1 = true;
+                        } else {
+                            const float w = __fmul_rn(alpha, T1);
+                            const float4 c = s_rgb[k];
+                            C10 = __fmaf_rn(c.x, w, C10);
+                            C11 = __fmaf_rn(c.y, w, C11);
+                            C12 = __fmaf_rn(c.z, w, C12);
+                            T1 = Tn;
+                        }
                     }
                 }
             }
@@ -414,30 +422,35 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
             }
             __syncthreads();
             const int nb = min(NB, r.y - b0);
-            for (int k = 0; k < nb; ++k) {
-                if (!(s_mask[k] & wbit)) continue;   // warp-uniform: no lane of this warp can be hit
-                // gradient of this thread's pixels w.r.t. (x, y, a, b, c, o, r, g, b) of Gaussian k
-                float gv[9];
+            for (int k0 = 0; k0 < nb; k0 += 32) {
+                // only the staged Gaussians that may reach this warp's patch, in order
+                unsigned int hits = __ballot_sync(0xffffffffu, k0 + lane < nb && (s_mask[k0 + lane] & wbit));
+                while (hits) {
+                    const int k = k0 + __ffs(hits) - 1;
+                    hits &= hits - 1;
+                    // gradient of this thread's pixels w.r.t. (x, y, a, b, c, o, r, g, b) of Gaussian k
+                    float gv[9];
 #pragma unroll
-                for (int c = 0; c < 9; ++c) gv[c] = 0.f;
-                bool hit = false;
-                const float4 xy = s_xy[k], con = s_con[k], c = s_rgb[k];
-                const float2 ad = s_ad[k];
+                    for (int c = 0; c < 9; ++c) gv[c] = 0.f;
+                    bool hit = false;
+                    const float4 xy = s_xy[k], con = s_con[k], c = s_rgb[k];
+                    const float2 ad = s_ad[k];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (done[h]) continue;
-                    const int res = pixel_grad(xy, con, c, ad, ti.pcx, ti.pcy0 + 4.f * h, L, im[h][0], im[h][1],
-                                               im[h][2], gg[h][0], gg[h][1], gg[h][2], T[h], C[h][0], C[h][1],
-                                               C[h][2], done[h], gv);
-                    hit |= res == 2;
-                    if (COUNT) {
-                        n_eval += res > 0;
-                        n_comp += res == 2;
+                    for (int h = 0; h < 2; ++h) {
+                        if (done[h]) continue;
+                        const int res = pixel_grad(xy, con, c, ad, ti.pcx, ti.pcy0 + 4.f * h, L, im[h][0], im[h][1],
+                                                   im[h][2], gg[h][0], gg[h][1], gg[h][2], T[h], C[h][0], C[h][1],
+                                                   C[h][2], done[h], gv);
+                        hit |= res == 2;
+                        if (COUNT) {
+                            n_eval += res > 0;
+                            n_comp += res == 2;
+                        }
                     }
-                }
-                if (__any_sync(0xffffffffu, hit)) {
-                    const float sum = warp_reduce_scatter9(gv, lane);
-                    if (red_own) atomicAdd(&s_g[k][red_idx], sum);
+                    if (__any_sync(0xffffffffu, hit)) {
+                        const float sum = warp_reduce_scatter9(gv, lane);
+                        if (red_own) atomicAdd(&s_g[k][red_idx], sum);
+                    }
                 }
             }
             __syncthreads();
