@@ -59,17 +59,19 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ proj, unsigned 
     rgb = make_float4(r2.x, r2.y, r2.z, __uint_as_float(slot));
 }
 
-// alpha of a staged Gaussian at pixel centre (pcx, pcy), block-relative.
-// Returns false if the Gaussian is skipped at this pixel.
-__device__ __forceinline__ bool eval_alpha(const float4 &xy, const float4 &con, float pcx, float pcy,
-                                           float alpha_min, float alpha_max, float &alpha, float &G, float &dx,
-                                           float &dy, float &u, bool &clamped) {
-    dx = __fsub_rn(pcx, xy.x);
+// alpha of a staged Gaussian at a pixel whose column offset dx = pcx - x has
+// already passed the gate |dx| <= ext_x (a thread's two pixels share their
+// column, so the caller tests it once for both). Returns false if the
+// Gaussian is skipped at this pixel. The base-2 exponent
+// p2 = Ah u^2 + Dh dy^2 is never positive (Ah, Dh < 0 for every staged,
+// positive-definite conic), so it needs no guard.
+__device__ __forceinline__ bool eval_alpha_row(const float4 &xy, const float4 &con, float dx, float pcy,
+                                               float alpha_min, float alpha_max, float &alpha, float &G, float &dy,
+                                               float &u, bool &clamped) {
     dy = __fsub_rn(pcy, xy.y);
-    if (fabsf(dx) > xy.z || fabsf(dy) > xy.w) return false;
+    if (fabsf(dy) > xy.w) return false;
     u = __fmaf_rn(con.y, dy, dx);
     const float p2 = __fmaf_rn(con.x, __fmul_rn(u, u), __fmul_rn(con.z, __fmul_rn(dy, dy)));
-    if (p2 > 0.f) return false;
     G = ex2_approx(p2);
     const float oG = __fmul_rn(con.w, G);
     clamped = oG > alpha_max;
@@ -259,10 +261,12 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
                     const int k = k0 + __ffs(hits) - 1;
                     hits &= hits - 1;
                     const float4 xy = s_xy[k], con = s_con[k];
-                    float alpha, G, dx, dy, u;
+                    const float dx = __fsub_rn(ti.pcx, xy.x);
+                    if (fabsf(dx) > xy.z) continue;   // the column gate, shared by both pixels
+                    float alpha, G, dy, u;
                     bool clamped;
-                    if (!done0 && eval_alpha(xy, con, ti.pcx, ti.pcy0, L.alpha_min, L.alpha_max, alpha, G, dx, dy, u,
-                                             clamped)) {
+                    if (!done0 && eval_alpha_row(xy, con, dx, ti.pcy0, L.alpha_min, L.alpha_max, alpha, G, dy, u,
+                                                 clamped)) {
                         const float Tn = __fmul_rn(T0, __fsub_rn(1.f, alpha));
                         if (Tn < L.t_min) {
                             done0 = true;
@@ -275,8 +279,8 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
                             T0 = Tn;
                         }
                     }
-                    if (!done1 && eval_alpha(xy, con, ti.pcx, pcy1, L.alpha_min, L.alpha_max, alpha, G, dx, dy, u,
-                                             clamped)) {
+                    if (!done1 && eval_alpha_row(xy, con, dx, pcy1, L.alpha_min, L.alpha_max, alpha, G, dy, u,
+                                                 clamped)) {
                         const float Tn = __fmul_rn(T1, __fsub_rn(1.f, alpha));
                         if (Tn < L.t_min) {
                             done1 = true;
@@ -313,13 +317,13 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
 // advancing the pixel's transmittance and colour sum exactly as the forward.
 // Returns 0 if the Gaussian was not evaluated at this pixel, 1 if its alpha
 // was evaluated but it was not composited, 2 if it was composited.
-__device__ __forceinline__ int pixel_grad(const float4 &xy, const float4 &con, const float4 &c, float2 ad, float pcx,
+__device__ __forceinline__ int pixel_grad(const float4 &xy, const float4 &con, const float4 &c, float2 ad, float dx,
                                            float pcy, const Launch &L, float img0, float img1, float img2,
                                            float g0, float g1, float g2, float &T, float &C0, float &C1, float &C2,
                                            bool &done, float *gv) {
-    float alpha, G = 0.f, dx, dy, u;
+    float alpha, G = 0.f, dy, u;
     bool clamped;
-    if (!eval_alpha(xy, con, pcx, pcy, L.alpha_min, L.alpha_max, alpha, G, dx, dy, u, clamped)) return G > 0.f;
+    if (!eval_alpha_row(xy, con, dx, pcy, L.alpha_min, L.alpha_max, alpha, G, dy, u, clamped)) return G > 0.f;
     const float oma = __fsub_rn(1.f, alpha);
     const float Tn = __fmul_rn(T, oma);
     if (Tn < L.t_min) {
@@ -435,10 +439,12 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
                     bool hit = false;
                     const float4 xy = s_xy[k], con = s_con[k], c = s_rgb[k];
                     const float2 ad = s_ad[k];
+                    const float dx = __fsub_rn(ti.pcx, xy.x);
+                    const bool col = fabsf(dx) <= xy.z;   // the column gate, shared by both pixels
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        if (done[h]) continue;
-                        const int res = pixel_grad(xy, con, c, ad, ti.pcx, ti.pcy0 + 4.f * h, L, im[h][0], im[h][1],
+                        if (done[h] || !col) continue;
+                        const int res = pixel_grad(xy, con, c, ad, dx, ti.pcy0 + 4.f * h, L, im[h][0], im[h][1],
                                                    im[h][2], gg[h][0], gg[h][1], gg[h][2], T[h], C[h][0], C[h][1],
                                                    C[h][2], done[h], gv);
                         hit |= res == 2;
