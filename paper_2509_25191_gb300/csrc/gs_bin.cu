@@ -367,14 +367,9 @@ __device__ void radix_sort_tile(SortSmem &S, unsigned long long *__restrict__ ke
         for (int e = threadIdx.x; e < 256 * nwa; e += SORT_THREADS) S.hist[e / nwa][e % nwa] = 0;
         __syncthreads();
         if (wid < nwa) {
-            for (int b = s0; b < s1; b += 32) {
-                const int i = b + lane;
-                const bool act = i < s1;
-                const unsigned int d = act ? ((S.key[cur][i] - kmin) >> dshift) & 255u : 256u + lane;
-                const unsigned int peers = __match_any_sync(0xffffffffu, d);
-                if (act && lane == __ffs(peers) - 1) S.hist[d][wid] += __popc(peers);
-                __syncwarp();
-            }
+            // counts only: order does not matter, plain shared atomics
+            for (int i = s0 + lane; i < s1; i += 32)
+                atomicAdd(&S.hist[((S.key[cur][i] - kmin) >> dshift) & 255u][wid], 1u);
         }
         __syncthreads();
         scan_hist(S, nwa);
@@ -382,14 +377,21 @@ __device__ void radix_sort_tile(SortSmem &S, unsigned long long *__restrict__ ke
             for (int b = s0; b < s1; b += 32) {
                 const int i = b + lane;
                 const bool act = i < s1;
-                const unsigned int d = act ? ((S.key[cur][i] - kmin) >> dshift) & 255u : 256u + lane;
-                const unsigned int peers = __match_any_sync(0xffffffffu, d);
+                const unsigned int key = act ? S.key[cur][i] : 0u;
+                const unsigned int d = ((key - kmin) >> dshift) & 255u;
+                // lanes holding the same digit, from one ballot per digit bit
+                unsigned int peers = __ballot_sync(0xffffffffu, act);
+#pragma unroll
+                for (int bit = 0; bit < 8; ++bit) {
+                    const unsigned int ones = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+                    peers &= ((d >> bit) & 1u) ? ones : ~ones;
+                }
                 unsigned int pos = 0;
                 if (act) pos = S.hist[d][wid] + __popc(peers & lt_mask);
                 __syncwarp();
                 if (act && lane == __ffs(peers) - 1) S.hist[d][wid] += __popc(peers);
                 if (act) {
-                    S.key[cur ^ 1][pos] = S.key[cur][i];
+                    S.key[cur ^ 1][pos] = key;
                     S.val[cur ^ 1][pos] = S.val[cur][i];
                 }
                 __syncwarp();
