@@ -295,14 +295,14 @@ struct SortSmem {
     int item;
 };
 
-// exclusive scan of the (digit, warp)-ordered counts hist[d][w], w < nwa
+// exclusive scan of the (digit, warp)-ordered counts hist[d][w], w < nwa:
+// thread d owns digit d (SORT_THREADS == 256 digits), sums its row, the block
+// scans the 256 row sums, and each row is rewritten as running offsets
+static_assert(SORT_THREADS == 256, "one thread per 8-bit digit");
 __device__ __forceinline__ void scan_hist(SortSmem &S, int nwa) {
-    const int E = 256 * nwa;
-    const int per = (E + SORT_THREADS - 1) / SORT_THREADS;
-    const int e0 = min(E, (int)threadIdx.x * per), e1 = min(E, e0 + per);
+    const int d = threadIdx.x;
     unsigned int sum = 0;
-    for (int e = e0; e < e1; ++e) sum += S.hist[e / nwa][e % nwa];
-    // block exclusive scan of the per-thread sums
+    for (int w = 0; w < nwa; ++w) sum += S.hist[d][w];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned int incl = sum;
 #pragma unroll
@@ -323,10 +323,9 @@ __device__ __forceinline__ void scan_hist(SortSmem &S, int nwa) {
     }
     __syncthreads();
     unsigned int run = S.part[wid] + incl - sum;
-    for (int e = e0; e < e1; ++e) {
-        unsigned int &h = S.hist[e / nwa][e % nwa];
-        const unsigned int c = h;
-        h = run;
+    for (int w = 0; w < nwa; ++w) {
+        const unsigned int c = S.hist[d][w];
+        S.hist[d][w] = run;
         run += c;
     }
     __syncthreads();
@@ -364,7 +363,7 @@ __device__ void radix_sort_tile(SortSmem &S, unsigned long long *__restrict__ ke
     int cur = 0;
     for (int pass = 0; pass < passes; ++pass) {
         const int dshift = shift + 8 * pass;
-        for (int e = threadIdx.x; e < 256 * nwa; e += SORT_THREADS) S.hist[e / nwa][e % nwa] = 0;
+        for (int w = 0; w < nwa; ++w) S.hist[threadIdx.x][w] = 0;
         __syncthreads();
         if (wid < nwa) {
             // counts only: order does not matter, plain shared atomics
