@@ -17,7 +17,7 @@
 //   k_bin_scatter  writes keys: one global reservation per (block, tile),
 //                  placement inside it by shared-memory atomics
 //   k_sort_tiles   persistent, largest tiles first; radix sort on chip
-//                  (chunks + merge path for tiles above 2048 instances)
+//                  (chunks + merge path for tiles above 4096 instances)
 #include "gs_common.cuh"
 
 namespace gsk {
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, con
 // ---------------------------------------------------------------------------
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr int SORT_CAP = 2048;      // ~42 KB of shared memory: 5 blocks per SM
+constexpr int SORT_CAP = 4096;      // ~74 KB of shared memory: 3 blocks per SM
 constexpr int SORT_SEG_MIN = 128;   // at least this many keys per active warp
 
 struct SortSmem {
@@ -509,14 +509,18 @@ int launch_bin_sort(const Launch &L, const float *proj, const gs_bins *b, int32_
         k_bin_scatter<<<nb, BIN_THREADS, bin_smem, st>>>(L, p, b->tile_scratch,
                                                          reinterpret_cast<unsigned long long *>(b->keys), b->counters,
                                                          smem_tiles);
-    static int smem_set = 0;
+    static int sort_blocks = 0;
     const int smem = (int)sizeof(SortSmem);
-    if (!smem_set) {
+    if (!sort_blocks) {
         if (cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
             return GS_ERR_CUDA;
-        smem_set = 1;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_tiles, SORT_THREADS, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        sort_blocks = per_sm * num_sms();
     }
-    k_sort_tiles<<<5 * num_sms(), SORT_THREADS, smem, st>>>(
+    k_sort_tiles<<<sort_blocks, SORT_THREADS, smem, st>>>(
         L, reinterpret_cast<const int2 *>(b->tile_ranges), b->tile_order,
         reinterpret_cast<unsigned long long *>(b->keys), reinterpret_cast<unsigned long long *>(b->keys_tmp),
         b->ids, b->counters);
