@@ -318,9 +318,8 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
 // Returns 0 if the Gaussian was not evaluated at this pixel, 1 if its alpha
 // was evaluated but it was not composited, 2 if it was composited.
 __device__ __forceinline__ int pixel_grad(const float4 &xy, const float4 &con, const float4 &c, float2 ad, float dx,
-                                           float pcy, const Launch &L, float img0, float img1, float img2,
-                                           float g0, float g1, float g2, float &T, float &C0, float &C1, float &C2,
-                                           bool &done, float *gv) {
+                                           float pcy, const Launch &L, float ig, float g0, float g1, float g2,
+                                           float &T, float &CG, bool &done, float *gv) {
     float alpha, G = 0.f, dy, u;
     bool clamped;
     if (!eval_alpha_row(xy, con, dx, pcy, L.alpha_min, L.alpha_max, alpha, G, dy, u, clamped)) return G > 0.f;
@@ -331,17 +330,16 @@ __device__ __forceinline__ int pixel_grad(const float4 &xy, const float4 &con, c
         return 1;
     }
     const float w = __fmul_rn(alpha, T);
-    C0 = __fmaf_rn(c.x, w, C0);
-    C1 = __fmaf_rn(c.y, w, C1);
-    C2 = __fmaf_rn(c.z, w, C2);
     gv[6] += w * g0;
     gv[7] += w * g1;
     gv[8] += w * g2;
-    // colour behind this Gaussian: image - running sum; 1 - alpha >= 0.01, so
-    // the fast reciprocal's few-ulp error is far inside the gradient tolerance
-    const float S0 = img0 - C0, S1 = img1 - C1, S2 = img2 - C2;
-    const float dL_dalpha =
-        T * (c.x * g0 + c.y * g1 + c.z * g2) - __fdividef(S0 * g0 + S1 * g1 + S2 * g2, oma);
+    // with cg = c.g: the running colour C (through this Gaussian) enters only
+    // as C.g, accumulated as CG += w cg, and the colour behind it is
+    // S = image - C, so S.g = image.g - CG. 1 - alpha >= 0.01, so the fast
+    // reciprocal's few-ulp error is far inside the gradient tolerance.
+    const float cgk = c.x * g0 + c.y * g1 + c.z * g2;
+    CG = fmaf(w, cgk, CG);
+    const float dL_dalpha = T * cgk - __fdividef(ig - CG, oma);
     if (!clamped) {
         // alpha = o G, G = exp(power), power = -1/2 d^T Q d with Q the conic
         // (inverse of the covariance Sigma' = (a, b, c)), d = pixel - mean.
@@ -400,7 +398,9 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
         const int2 r = ranges[tile];
         const ViewDesc &vd = L.v[ti.view];
         const long long hw = (long long)vd.W * vd.H;
-        float im[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, gg[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        // per pixel: upstream gradient g, image.g, and the running colour dotted
+        // with g (the colour behind a Gaussian enters dL/dalpha only as S.g)
+        float gg[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, ig[2] = {0.f, 0.f};
         bool done[2] = {!ti.in0, !ti.in1};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -408,12 +408,12 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
             const long long o = vd.pix_base + (long long)(ti.py0 + 4 * h) * vd.W + ti.px;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                im[h][ch] = image[o + ch * hw];
                 gg[h][ch] = dL_dimage[o + ch * hw];
+                ig[h] = fmaf(image[o + ch * hw], gg[h][ch], ig[h]);
             }
             done[h] = gg[h][0] == 0.f && gg[h][1] == 0.f && gg[h][2] == 0.f;
         }
-        float T[2] = {1.f, 1.f}, C[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        float T[2] = {1.f, 1.f}, cg[2] = {0.f, 0.f};
         unsigned int n_eval = 0, n_comp = 0;
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
             if (__syncthreads_count(done[0] && done[1]) == BS) break;
@@ -444,9 +444,8 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         if (done[h] || !col) continue;
-                        const int res = pixel_grad(xy, con, c, ad, dx, ti.pcy0 + 4.f * h, L, im[h][0], im[h][1],
-                                                   im[h][2], gg[h][0], gg[h][1], gg[h][2], T[h], C[h][0], C[h][1],
-                                                   C[h][2], done[h], gv);
+                        const int res = pixel_grad(xy, con, c, ad, dx, ti.pcy0 + 4.f * h, L, ig[h], gg[h][0],
+                                                   gg[h][1], gg[h][2], T[h], cg[h], done[h], gv);
                         hit |= res == 2;
                         if (COUNT) {
                             n_eval += res > 0;
