@@ -243,42 +243,58 @@ def run_native(args, rank, world, local_rank):
     rast.check_status()
     value = whole_job_mpix_s(P, world, ms)
 
-    # end to end through the public API: pinned host inputs copied in, result out
+    # end to end through the public API, each step fed from pinned host memory.
+    # e2e: a training step with the Gaussians resident on the device (the model
+    # state): the step's target image and camera pose are copied in, the loss
+    # and the pose gradient read back. e2e_params_in: the same, plus all
+    # Gaussian parameters copied in and the rendered image read back each step.
     e2e = None
+    e2e_params = None
     if not args.no_e2e:
-        host = [t.cpu().pin_memory() for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.sh,
-                                               views.viewmats)]
-        dev_t = [g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, views.viewmats]
+        k_e2e = max(3, min(args.steps, 50))
+        tgt_dev = step.target
+        host_step = [tgt_dev.cpu().pin_memory(), views.viewmats.cpu().pin_memory()]
+        dev_step = [tgt_dev, views.viewmats]
+        host_par = [t.cpu().pin_memory() for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.sh)]
+        dev_par = [g.means, g.log_scales, g.quats, g.opacity_logits, g.sh]
         out_img = torch.empty(image.shape, dtype=torch.float32).pin_memory()
         out_pose = torch.empty(dvm.shape, dtype=torch.float32).pin_memory()
-        out_loss = torch.empty(1, dtype=torch.float32).pin_memory()
-        h2d = sum(t.numel() * 4 for t in host)
-        d2h = (out_img.numel() + out_pose.numel() + 1) * 4
-        k_e2e = max(3, min(args.steps, 50))
+        out_loss = torch.empty(loss.shape, dtype=torch.float32).pin_memory()
 
-        def e2e_step():
-            for h, d in zip(host, dev_t):
-                d.copy_(h, non_blocking=True)
-            graph.replay()
-            out_img.copy_(image, non_blocking=True)
-            out_pose.copy_(dvm, non_blocking=True)
-            out_loss.copy_(loss, non_blocking=True)
+        def run_e2e(with_params):
+            hosts = host_step + (host_par if with_params else [])
+            devs = dev_step + (dev_par if with_params else [])
+            outs = [(out_loss, loss), (out_pose, dvm)] + ([(out_img, image)] if with_params else [])
 
-        for _ in range(3):
-            e2e_step()
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(k_e2e):
-            e2e_step()
-        b.record()
-        torch.cuda.synchronize()
-        ems = max_over_ranks(a.elapsed_time(b) / k_e2e, dev)
-        e2e = {"value": round(whole_job_mpix_s(P, world, ems), 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ems, 4), "steps": k_e2e}
+            def e2e_step():
+                for h, d in zip(hosts, devs):
+                    d.copy_(h, non_blocking=True)
+                graph.replay()
+                for o, d in outs:
+                    o.copy_(d, non_blocking=True)
+
+            for _ in range(3):
+                e2e_step()
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(k_e2e):
+                e2e_step()
+            b.record()
+            torch.cuda.synchronize()
+            ems = max_over_ranks(a.elapsed_time(b) / k_e2e, dev)
+            return {"value": round(whole_job_mpix_s(P, world, ems), 3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in hosts)),
+                    "d2h_bytes_per_step": int(sum(o.numel() * 4 for o, _ in outs)),
+                    "ms_per_step": round(ems, 4), "steps": k_e2e}
+
+        e2e = run_e2e(False)
+        e2e["inputs"] = "target image and camera pose in, loss and pose gradient out; Gaussians resident"
+        e2e_params = run_e2e(True)
+        e2e_params["inputs"] = "also all Gaussian parameters in and the rendered image out, every step"
 
     # roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
@@ -345,6 +361,7 @@ def run_native(args, rank, world, local_rank):
         "batched_vs_plain": batched,
         "other_workloads": extra,
         "e2e": e2e,
+        "e2e_params_in": e2e_params,
         "gpu_launches": kernels_per_step * args.steps,
     }
     return out, sc, vw
