@@ -50,6 +50,25 @@ BWD_OPS_EVAL, BWD_OPS_COMP = 10, 50
 FP32_LANES_PER_SM = 128
 
 
+# DRAM traffic per launch of the raster backward (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean of three launches of one ncu capture; command
+# and figures in profiles/k_render_bwd_single_view_1m.md). It holds only for
+# the kernel source it was measured on (hash of its two source files) and for
+# the default workload and tile; otherwise the bench reports null.
+RASTER_BWD_TRAFFIC = {"bytes": 53_812_000, "sources_sha256_16": "4bb47fb6f23914a2", "n": 1_000_000,
+                      "tile": (16, 16)}
+
+
+def raster_bwd_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2509_25191_gb300", "csrc")
+    for f in ("gs_render.cu", "gs_common.cuh"):
+        with open(os.path.join(here, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,6 +316,9 @@ def run_native(args, rank, world, local_rank):
         e2e_params["inputs"] = "also all Gaussian parameters in and the rendered image out, every step"
 
     # roofline of the dominant kernel
+    rt = RASTER_BWD_TRAFFIC
+    raster_traffic = rt["bytes"] if (args.n == rt["n"] and tuple(tile) == rt["tile"] and
+                                     raster_bwd_sources_hash() == rt["sources_sha256_16"]) else None
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     top = int(np.argmax(stage_ms))
@@ -308,7 +330,7 @@ def run_native(args, rank, world, local_rank):
         peak = sms * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         achieved = ops / t_top / 1e12
         roof = {"kernel": names[top], "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": raster_traffic,
                 "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz"
                                f" ({peak_src} max clock)",
                 "units": {"pairs_evaluated": ev_, "pairs_composited": co_, "fp32_ops": int(ops)}}
