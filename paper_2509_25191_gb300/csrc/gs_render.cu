@@ -263,15 +263,23 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
                     const float4 xy = s_xy[k], con = s_con[k];
                     const float dx = __fsub_rn(ti.pcx, xy.x);
                     if (fabsf(dx) > xy.z) continue;   // the column gate, shared by both pixels
-                    float alpha, G, dy, u;
-                    bool clamped;
-                    if (!done0 && eval_alpha_row(xy, con, dx, ti.pcy0, L.alpha_min, L.alpha_max, alpha, G, dy, u,
-                                                 clamped)) {
-                        const float Tn = __fmul_rn(T0, __fsub_rn(1.f, alpha));
+                    // both pixels' alphas first (two independent chains), then the
+                    // order-dependent updates; the arithmetic is eval_alpha_row's
+                    const float dy0 = __fsub_rn(ti.pcy0, xy.y), dy1 = __fsub_rn(pcy1, xy.y);
+                    const float u0 = __fmaf_rn(con.y, dy0, dx), u1 = __fmaf_rn(con.y, dy1, dx);
+                    const float p0 = __fmaf_rn(con.x, __fmul_rn(u0, u0), __fmul_rn(con.z, __fmul_rn(dy0, dy0)));
+                    const float p1 = __fmaf_rn(con.x, __fmul_rn(u1, u1), __fmul_rn(con.z, __fmul_rn(dy1, dy1)));
+                    const float oG0 = __fmul_rn(con.w, ex2_approx(p0)), oG1 = __fmul_rn(con.w, ex2_approx(p1));
+                    const float a0 = oG0 > L.alpha_max ? L.alpha_max : oG0;
+                    const float a1 = oG1 > L.alpha_max ? L.alpha_max : oG1;
+                    const bool ok0 = !done0 && fabsf(dy0) <= xy.w && a0 >= L.alpha_min;
+                    const bool ok1 = !done1 && fabsf(dy1) <= xy.w && a1 >= L.alpha_min;
+                    if (ok0) {
+                        const float Tn = __fmul_rn(T0, __fsub_rn(1.f, a0));
                         if (Tn < L.t_min) {
                             done0 = true;
                         } else {
-                            const float w = __fmul_rn(alpha, T0);
+                            const float w = __fmul_rn(a0, T0);
                             const float4 c = s_rgb[k];
                             C00 = __fmaf_rn(c.x, w, C00);
                             C01 = __fmaf_rn(c.y, w, C01);
@@ -279,8 +287,8 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
                             T0 = Tn;
                         }
                     }
-                    if (!done1 && eval_alpha_row(xy, con, dx, pcy1, L.alpha_min, L.alpha_max, alpha, G, dy, u,
-                                                 clamped)) {
+                    if (ok1) {
+                        const float alpha = a1;
                         const float Tn = __fmul_rn(T1, __fsub_rn(1.f, alpha));
                         if (Tn < L.t_min) {
                             done1 = true;
