@@ -59,25 +59,15 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ proj, unsigned 
     rgb = make_float4(r2.x, r2.y, r2.z, __uint_as_float(slot));
 }
 
-// alpha of a staged Gaussian at a pixel whose column offset dx = pcx - x has
-// already passed the gate |dx| <= ext_x (a thread's two pixels share their
-// column, so the caller tests it once for both). Returns false if the
-// Gaussian is skipped at this pixel. The base-2 exponent
-// p2 = Ah u^2 + Dh dy^2 is never positive (Ah, Dh < 0 for every staged,
-// positive-definite conic), so it needs no guard.
-__device__ __forceinline__ bool eval_alpha_row(const float4 &xy, const float4 &con, float dx, float pcy,
-                                               float alpha_min, float alpha_max, float &alpha, float &G, float &dy,
-                                               float &u, bool &clamped) {
-    dy = __fsub_rn(pcy, xy.y);
-    if (fabsf(dy) > xy.w) return false;
-    u = __fmaf_rn(con.y, dy, dx);
-    const float p2 = __fmaf_rn(con.x, __fmul_rn(u, u), __fmul_rn(con.z, __fmul_rn(dy, dy)));
-    G = ex2_approx(p2);
-    const float oG = __fmul_rn(con.w, G);
-    clamped = oG > alpha_max;
-    alpha = clamped ? alpha_max : oG;
-    return alpha >= alpha_min;
-}
+// alpha of a staged Gaussian at a pixel (the forward and the backward share
+// this arithmetic and so take identical decisions): with dx = pcx - x,
+// dy = pcy - y (block-relative pixel centre minus mean),
+//   gate   |dx| <= ext_x and |dy| <= ext_y (the column test is shared by a
+//          thread's two pixels, which lie in one column),
+//   u = dx + beta dy, p2 = Ah u^2 + Dh dy^2 (base 2; never positive: Ah, Dh < 0
+//          for every staged, positive-definite conic, so no guard),
+//   G = 2^p2, alpha = min(alpha_max, o G) ("clamped" if o G > alpha_max),
+//   skipped if alpha < alpha_min.
 
 struct TileInfo {
     int view;
@@ -264,7 +254,7 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
                     const float dx = __fsub_rn(ti.pcx, xy.x);
                     if (fabsf(dx) > xy.z) continue;   // the column gate, shared by both pixels
                     // both pixels' alphas first (two independent chains), then the
-                    // order-dependent updates; the arithmetic is eval_alpha_row's
+                    // order-dependent updates
                     const float dy0 = __fsub_rn(ti.pcy0, xy.y), dy1 = __fsub_rn(pcy1, xy.y);
                     const float u0 = __fmaf_rn(con.y, dy0, dx), u1 = __fmaf_rn(con.y, dy1, dx);
                     const float p0 = __fmaf_rn(con.x, __fmul_rn(u0, u0), __fmul_rn(con.z, __fmul_rn(dy0, dy0)));
@@ -325,12 +315,12 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
 // advancing the pixel's transmittance and colour sum exactly as the forward.
 // Returns 0 if the Gaussian was not evaluated at this pixel, 1 if its alpha
 // was evaluated but it was not composited, 2 if it was composited.
-__device__ __forceinline__ int pixel_grad(const float4 &xy, const float4 &con, const float4 &c, float2 ad, float dx,
-                                           float pcy, const Launch &L, float ig, float g0, float g1, float g2,
-                                           float &T, float &CG, bool &done, float *gv) {
-    float alpha, G = 0.f, dy, u;
-    bool clamped;
-    if (!eval_alpha_row(xy, con, dx, pcy, L.alpha_min, L.alpha_max, alpha, G, dy, u, clamped)) return G > 0.f;
+// Gradient contribution of one staged Gaussian at one pixel whose alpha
+// (>= alpha_min) was already formed: 1 if the pixel stops before it (T would
+// fall below t_min), 2 if it was composited.
+__device__ __forceinline__ int pixel_grad(const float4 &c, const float4 &con, float2 ad, float alpha, float G,
+                                           float dy, float u, bool clamped, const Launch &L, float ig, float g0,
+                                           float g1, float g2, float &T, float &CG, bool &done, float *gv) {
     const float oma = __fsub_rn(1.f, alpha);
     const float Tn = __fmul_rn(T, oma);
     if (Tn < L.t_min) {
@@ -448,16 +438,37 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
                     const float4 xy = s_xy[k], con = s_con[k], c = s_rgb[k];
                     const float2 ad = s_ad[k];
                     const float dx = __fsub_rn(ti.pcx, xy.x);
-                    const bool col = fabsf(dx) <= xy.z;   // the column gate, shared by both pixels
+                    if (fabsf(dx) <= xy.z) {   // the column gate, shared by both pixels
+                        // both pixels' alphas first (two independent chains, the
+                        // forward's arithmetic and decisions), then the gradients
+                        float dyh[2], uh[2], Gh[2], ah[2];
+                        bool clh[2], evh[2], okh[2];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        if (done[h] || !col) continue;
-                        const int res = pixel_grad(xy, con, c, ad, dx, ti.pcy0 + 4.f * h, L, ig[h], gg[h][0],
-                                                   gg[h][1], gg[h][2], T[h], cg[h], done[h], gv);
-                        hit |= res == 2;
-                        if (COUNT) {
-                            n_eval += res > 0;
-                            n_comp += res == 2;
+                        for (int h = 0; h < 2; ++h) {
+                            dyh[h] = __fsub_rn(ti.pcy0 + 4.f * h, xy.y);
+                            uh[h] = __fmaf_rn(con.y, dyh[h], dx);
+                            const float p2 = __fmaf_rn(con.x, __fmul_rn(uh[h], uh[h]),
+                                                       __fmul_rn(con.z, __fmul_rn(dyh[h], dyh[h])));
+                            Gh[h] = ex2_approx(p2);
+                            const float oG = __fmul_rn(con.w, Gh[h]);
+                            clh[h] = oG > L.alpha_max;
+                            ah[h] = clh[h] ? L.alpha_max : oG;
+                            evh[h] = !done[h] && fabsf(dyh[h]) <= xy.w;
+                            okh[h] = evh[h] && ah[h] >= L.alpha_min;
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (!okh[h]) {
+                                if (COUNT) n_eval += evh[h];
+                                continue;
+                            }
+                            const int res = pixel_grad(c, con, ad, ah[h], Gh[h], dyh[h], uh[h], clh[h], L, ig[h],
+                                                       gg[h][0], gg[h][1], gg[h][2], T[h], cg[h], done[h], gv);
+                            hit |= res == 2;
+                            if (COUNT) {
+                                n_eval += 1;
+                                n_comp += res == 2;
+                            }
                         }
                     }
                     if (__any_sync(0xffffffffu, hit)) {
