@@ -156,8 +156,13 @@ int gs_pose_blocks(int64_t n);
  *                       sqrt(k Sigma'_xx)) (and yy) with k = 2 ln(o /
  *                       alpha_min), the bounding box of the ellipse where
  *                       alpha >= alpha_min (culled if k <= 0),
- *   {a, b, c, o}        dilated 2D covariance Sigma' (b off-diagonal; its
- *                       inverse is the conic) and opacity,
+ *   {Ah, beta, Dh, o}   the conic (inverse of the dilated 2D covariance
+ *                       Sigma' = [[a, b], [b, c]]) in the form the raster
+ *                       kernels evaluate, and the opacity: with det =
+ *                       a c - b^2, A = c / det, beta = -b / c, D = 1 / c,
+ *                       Ah = -A / (2 ln 2), Dh = -D / (2 ln 2), the Gaussian
+ *                       at offset (dx, dy) from the mean is
+ *                       2^(Ah u^2 + Dh dy^2) with u = dx + beta dy,
  *   {r, g, b, radius}   colour (SH evaluated, +0.5, clamped at 0) and the
  *                       integer radius ceil(3 sqrt(lambda_max)) (0 = culled),
  *   {x_lo, y_lo, depth, clamp_bits}  low parts of the mean (x + x_lo is the

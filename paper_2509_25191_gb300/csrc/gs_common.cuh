@@ -94,6 +94,9 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float LN2 = 0.69314718055994531f;
+
 struct ff { float hi, lo; };   // unevaluated sum hi + lo
 
 __device__ __forceinline__ ff two_sum(float a, float b) {

@@ -149,7 +149,13 @@ __global__ void __launch_bounds__(128) k_project_fwd(const Launch L, const float
             const float ex = fminf(radius, sqrtf(kext * ca) * grow);
             const float ey = fminf(radius, sqrtf(kext * cc) * grow);
             out[0] = make_float4(PX.hi, PY.hi, ex, ey);
-            out[1] = make_float4(ca, cb, cc, opac);
+            // the conic in the form the rasterizer evaluates (see gs.h): with
+            // det = a c - b^2 (b^2 carried exactly), A = c / det, beta = -b / c,
+            // D = 1 / c, base-2 exponent Ah u^2 + Dh dy^2, u = dx + beta dy
+            const ff bb = two_prod(cb, cb);
+            const float cdet = __fsub_rn(__fmaf_rn(ca, cc, -bb.hi), bb.lo);
+            const float A = __fdiv_rn(cc, cdet), beta = __fdiv_rn(-cb, cc), D = __fdiv_rn(1.f, cc);
+            out[1] = make_float4(__fmul_rn(A, -0.5f * LOG2E), beta, __fmul_rn(D, -0.5f * LOG2E), opac);
             out[2] = make_float4(rgb[0], rgb[1], rgb[2], radius);
             out[3] = make_float4(PX.lo, PY.lo, z, __int_as_float(clamp_bits));
         } else {

@@ -27,8 +27,6 @@
 
 namespace gsk {
 
-constexpr float LOG2E = 1.4426950408889634f;
-constexpr float LN2 = 0.69314718055994531f;
 
 // Staged instance: xy = mean relative to the block origin and the reach
 // half-extents (ext_x, ext_y <= radius, so the test |dx| <= ext_x, |dy| <=
@@ -49,13 +47,7 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ proj, unsigned 
     const float4 r2 = proj[4ull * slot + 2];
     const float4 r3 = proj[4ull * slot + 3];
     xy = make_float4(__fadd_rn(__fsub_rn(r0.x, ox), r3.x), __fadd_rn(__fsub_rn(r0.y, oy), r3.y), r0.z, r0.w);
-    // det = a c - b^2 with b^2 carried exactly
-    const ff bb = two_prod(r1.y, r1.y);
-    const float det = __fsub_rn(__fmaf_rn(r1.x, r1.z, -bb.hi), bb.lo);
-    const float A = __fdiv_rn(r1.z, det);
-    const float beta = __fdiv_rn(-r1.y, r1.z);
-    const float D = __fdiv_rn(1.f, r1.z);
-    con = make_float4(__fmul_rn(A, -0.5f * LOG2E), beta, __fmul_rn(D, -0.5f * LOG2E), r1.w);
+    con = r1;   // the conic in the staged form, written by the projection
     rgb = make_float4(r2.x, r2.y, r2.z, __uint_as_float(slot));
 }
 

@@ -114,7 +114,14 @@ def test_projection_parity(case):
         y = rec[:, 1].astype(np.float64) + rec[:, 13]
         assert np.abs(x - ref["xy"][:, 0])[both].max() < 2e-5 * max(1.0, np.abs(ref["xy"][both]).max())
         assert np.abs(y - ref["xy"][:, 1])[both].max() < 2e-5 * max(1.0, np.abs(ref["xy"][both]).max())
-        cov = rec[:, 4:7][both]
+        # the record holds the conic in the staged form; map it back to the
+        # covariance (a well-conditioned direction) in FP64
+        Ah, beta, Dh = (rec[:, 4:7][both].astype(np.float64)).T
+        c = -1.0 / (2.0 * np.log(2.0) * Dh)
+        A = -2.0 * np.log(2.0) * Ah
+        b = -beta * c
+        a = 1.0 / A + b * b / c
+        cov = np.stack([a, b, c], 1)
         rc = ref["cov"][both]
         scale = np.abs(rc).max(axis=1, keepdims=True)
         assert (np.abs(cov - rc) / scale).max() < 1e-5
