@@ -280,17 +280,41 @@ def run_native(args, rank, world, local_rank):
         out_pose = torch.empty(dvm.shape, dtype=torch.float32).pin_memory()
         out_loss = torch.empty(loss.shape, dtype=torch.float32).pin_memory()
 
+        # the large per-step input (the target image) is uploaded for step k+1
+        # on a copy stream while step k computes (two device staging buffers,
+        # a device-to-device copy into the captured input at the step start)
+        copy_stream = torch.cuda.Stream(device=dev)
+        staging = [torch.empty_like(tgt_dev) for _ in range(2)]
+        ready = [torch.cuda.Event() for _ in range(2)]
+        consumed = [torch.cuda.Event() for _ in range(2)]
+        main = torch.cuda.current_stream(dev)
+
         def run_e2e(with_params):
-            hosts = host_step + (host_par if with_params else [])
-            devs = dev_step + (dev_par if with_params else [])
+            hosts = host_step[1:] + (host_par if with_params else [])
+            devs = dev_step[1:] + (dev_par if with_params else [])
             outs = [(out_loss, loss), (out_pose, dvm)] + ([(out_img, image)] if with_params else [])
+            state = {"k": 0}
+
+            def upload(k):
+                with torch.cuda.stream(copy_stream):
+                    copy_stream.wait_event(consumed[k % 2])
+                    staging[k % 2].copy_(host_step[0], non_blocking=True)
+                    ready[k % 2].record(copy_stream)
+
+            upload(0)
 
             def e2e_step():
+                k = state["k"]
+                main.wait_event(ready[k % 2])
+                tgt_dev.copy_(staging[k % 2], non_blocking=True)
+                consumed[k % 2].record(main)
+                upload(k + 1)
                 for h, d in zip(hosts, devs):
                     d.copy_(h, non_blocking=True)
                 graph.replay()
                 for o, d in outs:
                     o.copy_(d, non_blocking=True)
+                state["k"] = k + 1
 
             for _ in range(3):
                 e2e_step()
@@ -306,12 +330,13 @@ def run_native(args, rank, world, local_rank):
             torch.cuda.synchronize()
             ems = max_over_ranks(a.elapsed_time(b) / k_e2e, dev)
             return {"value": round(whole_job_mpix_s(P, world, ems), 3), "unit": UNIT,
-                    "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in hosts)),
+                    "h2d_bytes_per_step": int(host_step[0].numel() * 4 + sum(h.numel() * 4 for h in hosts)),
                     "d2h_bytes_per_step": int(sum(o.numel() * 4 for o, _ in outs)),
                     "ms_per_step": round(ems, 4), "steps": k_e2e}
 
         e2e = run_e2e(False)
-        e2e["inputs"] = "target image and camera pose in, loss and pose gradient out; Gaussians resident"
+        e2e["inputs"] = ("target image and camera pose in, loss and pose gradient out; Gaussians resident; "
+                         "the next step's target uploads on a copy stream during the current step")
         e2e_params = run_e2e(True)
         e2e_params["inputs"] = "also all Gaussian parameters in and the rendered image out, every step"
 
@@ -665,9 +690,21 @@ def cpu_baseline(sc, vw):
     t = time.perf_counter()
     npx = oracle_step(sc, vw, 1.0, 7)
     dt = time.perf_counter() - t
-    return {"value": round(npx / dt / 1e6, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full step: all {npx} pixels of the same workload, FP64 C oracle, single thread",
-            "seconds": round(dt, 2)}
+    out = {"value": round(npx / dt / 1e6, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"one full step: all {npx} pixels of the same workload, FP64 C oracle, single thread",
+           "seconds": round(dt, 2)}
+    # the small 2,000-Gaussian 128x128 case as well (full step, single thread)
+    from paper_2509_25191_gb300 import synth
+    ssc, svw = synth.single_view_small()
+    t = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t < 1.0:
+        spx = oracle_step(ssc, svw, 1.0, 7 + reps)
+        reps += 1
+    sdt = (time.perf_counter() - t) / reps
+    out["small_case"] = {"workload": "2,000 SH0 Gaussians, one 128x128 view", "mpix_s": round(spx / sdt / 1e6, 6),
+                         "ms_per_step": round(sdt * 1e3, 3)}
+    return out
 
 
 _WORKER = {}
