@@ -283,17 +283,20 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, con
 // ---------------------------------------------------------------------------
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr int SORT_CAP = 4096;      // ~74 KB of shared memory: 3 blocks per SM
+constexpr int SORT_CAP = 4096;      // ~74 KB of shared memory: 3 blocks per SM (228 KB with the per-block reserve)
 constexpr int SORT_SEG_MIN = 128;   // at least this many keys per active warp
 
 struct SortSmem {
     unsigned int key[2][SORT_CAP];
     unsigned int val[2][SORT_CAP];
     unsigned int hist[256][SORT_WARPS + 1];   // [digit][warp] counts, then running offsets (odd pitch)
-    unsigned int part[SORT_THREADS];
+    unsigned int part[SORT_WARPS];   // per-warp partial sums of the histogram scan
     unsigned int kmin, kmax;
     int item;
+    unsigned int moff[257];          // large tiles: bin offsets within the tile
 };
+// (the per-bin counts and cursors of a large tile's partition pass live in
+// hist, unused until the segments are sorted)
 
 // exclusive scan of the (digit, warp)-ordered counts hist[d][w], w < nwa:
 // thread d owns digit d (SORT_THREADS == 256 digits), sums its row, the block
@@ -331,15 +334,16 @@ __device__ __forceinline__ void scan_hist(SortSmem &S, int nwa) {
     __syncthreads();
 }
 
-// sort keys[st .. st+n) (n <= SORT_CAP) in place by (depth, slot)
-__device__ void radix_sort_tile(SortSmem &S, unsigned long long *__restrict__ keys, unsigned int *__restrict__ ids,
-                                int st, int n, bool write_ids) {
+// sort src[st .. st+n) (n <= SORT_CAP) by (depth, slot) into keys[st ..]
+// (src may be keys itself)
+__device__ void radix_sort_tile(SortSmem &S, const unsigned long long *src, unsigned long long *keys,
+                                unsigned int *__restrict__ ids, int st, int n, bool write_ids) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) { S.kmin = 0xffffffffu; S.kmax = 0u; }
     __syncthreads();
     unsigned int lmin = 0xffffffffu, lmax = 0u;
     for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
-        const unsigned long long k = keys[st + i];
+        const unsigned long long k = src[st + i];
         const unsigned int d = (unsigned int)(k >> 32);
         S.key[0][i] = d;
         S.val[0][i] = (unsigned int)(k & 0xffffffffu);
@@ -448,6 +452,32 @@ __device__ void block_merge(const unsigned long long *a, int na, const unsigned 
     }
 }
 
+// Sort a segment longer than SORT_CAP whose keys are in tmp[st .. st+n):
+// chunks of SORT_CAP sorted on chip into keys, then pairwise merges
+// (ping-pong between keys and tmp over the same index range); the result,
+// with its ids, ends in keys.
+__device__ void sort_segment_merge(SortSmem &S, unsigned long long *keys, unsigned long long *tmp,
+                                   unsigned int *__restrict__ ids, int st, int n) {
+    for (int c = 0; c < n; c += SORT_CAP) radix_sort_tile(S, tmp, keys, ids, st + c, min(SORT_CAP, n - c), false);
+    unsigned long long *src = keys + st, *dst = tmp + st;
+    for (int w = SORT_CAP; w < n; w <<= 1) {
+        for (int m = 0; m < n; m += 2 * w) {
+            const int na = min(w, n - m), nb = max(0, min(w, n - m - w));
+            block_merge(src + m, na, src + m + na, nb, dst + m);
+        }
+        __syncthreads();
+        unsigned long long *t = src;
+        src = dst;
+        dst = t;
+    }
+    for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
+        const unsigned long long k = src[i];
+        if (src != keys + st) keys[st + i] = k;
+        ids[st + i] = (unsigned int)(k & 0xffffffffu);
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_tiles(const Launch L, const int2 *__restrict__ ranges,
                                                              const int *__restrict__ order,
                                                              unsigned long long *__restrict__ keys,
@@ -470,26 +500,71 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_tiles(const Launch L, con
             continue;
         }
         if (n <= SORT_CAP) {
-            radix_sort_tile(S, keys, ids, r.x, n, true);
+            radix_sort_tile(S, keys, keys, ids, r.x, n, true);
             continue;
         }
-        for (int c = 0; c < n; c += SORT_CAP) radix_sort_tile(S, keys, ids, r.x + c, min(SORT_CAP, n - c), false);
-        // pairwise merges of sorted runs, ping-pong between keys and keys_tmp
-        unsigned long long *src = keys + r.x, *dst = keys_tmp + r.x;
-        for (int w = SORT_CAP; w < n; w <<= 1) {
-            for (int m = 0; m < n; m += 2 * w) {
-                const int na = min(w, n - m), nb = max(0, min(w, n - m - w));
-                block_merge(src + m, na, src + m + na, nb, dst + m);
-            }
-            __syncthreads();
-            unsigned long long *t = src; src = dst; dst = t;
+        // Large tile: one partition pass by the top 8 bits of (depth bits -
+        // tile minimum) into keys_tmp (bins in depth order), then runs of
+        // consecutive bins that fit on chip are sorted as one segment each
+        // into keys; a single bin larger than that takes the chunk-and-merge
+        // path. The result is the same (depth, slot) order.
+        if (threadIdx.x == 0) {
+            S.kmin = 0xffffffffu;
+            S.kmax = 0u;
         }
-        for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
-            const unsigned long long k = src[i];
-            if (src != keys + r.x) keys[r.x + i] = k;
-            ids[r.x + i] = (unsigned int)(k & 0xffffffffu);
+        unsigned int *mcnt = &S.hist[0][0];   // 256 counters, then cursors
+        for (int b = threadIdx.x; b < 256; b += SORT_THREADS) mcnt[b] = 0;
+        __syncthreads();
+        {
+            unsigned int lmin = 0xffffffffu, lmax = 0u;
+            for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
+                const unsigned int d = (unsigned int)(keys[r.x + i] >> 32);
+                lmin = min(lmin, d);
+                lmax = max(lmax, d);
+            }
+            atomicMin(&S.kmin, lmin);
+            atomicMax(&S.kmax, lmax);
         }
         __syncthreads();
+        const unsigned int kmin = S.kmin, range = S.kmax - S.kmin;
+        const int nbits = range ? 32 - __clz(range) : 0;
+        const int mshift = nbits > 8 ? nbits - 8 : 0;
+        for (int i = threadIdx.x; i < n; i += SORT_THREADS)
+            atomicAdd(&mcnt[(((unsigned int)(keys[r.x + i] >> 32)) - kmin) >> mshift], 1u);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned int acc = 0;
+            for (int b = 0; b < 256; ++b) {
+                S.moff[b] = acc;
+                acc += mcnt[b];
+                mcnt[b] = S.moff[b];   // becomes the scatter cursor
+            }
+            S.moff[256] = acc;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
+            const unsigned long long k = keys[r.x + i];
+            const unsigned int b = (((unsigned int)(k >> 32)) - kmin) >> mshift;
+            keys_tmp[r.x + atomicAdd(&mcnt[b], 1u)] = k;
+        }
+        __syncthreads();   // the block's global writes are visible to the block after the barrier
+        for (int b0 = 0; b0 < 256;) {
+            // the longest run of bins from b0 that fits on chip (at least one bin)
+            int b1 = b0 + 1;
+            while (b1 < 256 && S.moff[b1 + 1] - S.moff[b0] <= (unsigned int)SORT_CAP) ++b1;
+            const int s0 = (int)S.moff[b0], len = (int)(S.moff[b1] - S.moff[b0]);
+            if (len == 1 && threadIdx.x == 0) {
+                const unsigned long long k = keys_tmp[r.x + s0];
+                keys[r.x + s0] = k;
+                ids[r.x + s0] = (unsigned int)(k & 0xffffffffu);
+            } else if (len > 1 && len <= SORT_CAP) {
+                radix_sort_tile(S, keys_tmp, keys, ids, r.x + s0, len, true);
+            } else if (len > SORT_CAP) {
+                sort_segment_merge(S, keys, keys_tmp, ids, r.x + s0, len);
+            }
+            __syncthreads();
+            b0 = b1;
+        }
     }
 }
 
