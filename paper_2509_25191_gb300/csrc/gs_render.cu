@@ -417,6 +417,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
             __syncthreads();
             const int nb = min(NB, r.y - b0);
             for (int k0 = 0; k0 < nb; k0 += 32) {
+                if (__all_sync(0xffffffffu, done[0] && done[1])) break;   // the warp's pixels have all stopped
                 // only the staged Gaussians that may reach this warp's patch, in order
                 unsigned int hits = __ballot_sync(0xffffffffu, k0 + lane < nb && (s_mask[k0 + lane] & wbit));
                 while (hits) {
