@@ -55,7 +55,8 @@ typedef enum gs_status {
     GS_ERR_CAPACITY = 3,     /* device: instance capacity too small; detail = instances needed */
     GS_ERR_UNSUPPORTED = 4,  /* configuration not compiled in (tile shape, SH degree) */
     GS_ERR_OVERFLOW = 5,     /* device: more than 2^31-1 tile instances */
-    GS_ERR_TOO_LARGE = 6     /* exceeds the fixed scratch of gs_project_bwd_noalloc */
+    GS_ERR_TOO_LARGE = 6,    /* exceeds the fixed scratch of gs_project_bwd_noalloc */
+    GS_ERR_TIMEOUT = 7       /* device: a bounded wait for an asynchronous copy ran out */
 } gs_status;
 
 /* Rasterizer settings. gs_config_default() fills the defaults in brackets. */
@@ -169,7 +170,11 @@ int gs_pose_blocks(int64_t n);
  *                       position to ~1e-5 px), camera z, bit c set if colour
  *                       channel c was clamped.
  * Culled records are all zero.
- * proj: DEVICE [P,16]. status: DEVICE int32[4] (unused here, may be NULL). */
+ * proj: DEVICE [P,16], 16-byte aligned. status: DEVICE int32[4] or NULL;
+ * the degree-3 path stages each block's SH rows and records with tensor
+ * copies, and if a bounded wait for one runs out (a copy that never lands)
+ * it sets status = {GS_ERR_TIMEOUT, block} and leaves that block's records
+ * unwritten. */
 int gs_project(const gs_gaussians *g, const gs_views *views, const gs_config *cfg,
                float *proj, int32_t *status, void *stream);
 

@@ -15,7 +15,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgsplat_gb300.so")
 
-GS_OK, GS_ERR_ARG, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_UNSUPPORTED, GS_ERR_OVERFLOW, GS_ERR_TOO_LARGE = range(7)
+GS_OK, GS_ERR_ARG, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_UNSUPPORTED, GS_ERR_OVERFLOW, GS_ERR_TOO_LARGE, GS_ERR_TIMEOUT = range(8)
 GS_MAX_VIEWS = 64
 GS_RECORD_FLOATS = 16
 GS_GRAD2D_FLOATS = 12

@@ -9,7 +9,7 @@
 namespace gsk {
 
 int launch_project(const Launch &L, int deg, const gs_gaussians *g, const float *viewmats, const float *intr,
-                   float *proj, cudaStream_t st);
+                   float *proj, int32_t *status, cudaStream_t st);
 int launch_bin_sort(const Launch &L, const float *proj, const gs_bins *b, int32_t *status, cudaStream_t st);
 int launch_render_fwd(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st);
 int launch_render_bwd(const Launch &L, const float *proj, const gs_bins *b, const float *image,
@@ -47,6 +47,42 @@ int num_sms() {
         cached[dev] = n;
     }
     return cached[dev];
+}
+
+// cuTensorMapEncodeTiled, fetched from the driver once (the library links
+// only the static CUDA runtime)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+bool encode_tmap_2d(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
+                    uint32_t box_inner, uint32_t box_rows, CUtensorMapSwizzle swizzle) {
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn || rows == 0 || rows > 0x7fffffffULL) return false;
+    const cuuint64_t dims[2] = {inner, rows};
+    const cuuint64_t strides[1] = {row_bytes};
+    const cuuint32_t box[2] = {box_inner, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 static bool tile_supported(int tw, int th) {
@@ -197,14 +233,13 @@ int gs_pose_blocks(int64_t n) { return pose_blocks(n); }
 
 int gs_project(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, float *proj, int32_t *status,
                void *stream) {
-    (void)status;
     Launch L;
     int rc = build_launch(vw, cfg, L);
     if (rc) return rc;
     if ((rc = check_gaussians(g, vw))) return rc;
     if (!vw->viewmats || !vw->intrinsics || (L.n_slots > 0 && !proj)) return GS_ERR_ARG;
     if (!aligned16(proj)) return GS_ERR_ARG;
-    return launch_project(L, g->sh_degree, g, vw->viewmats, vw->intrinsics, proj, (cudaStream_t)stream);
+    return launch_project(L, g->sh_degree, g, vw->viewmats, vw->intrinsics, proj, status, (cudaStream_t)stream);
 }
 
 int gs_bin_sort(const gs_views *vw, const gs_config *cfg, const float *proj, const gs_bins *b, int32_t *status,
@@ -232,7 +267,6 @@ int gs_render_fwd(const gs_views *vw, const gs_config *cfg, const float *proj, c
 int gs_rasterize_bwd(const gs_views *vw, const gs_config *cfg, const float *proj, const gs_bins *b,
                      const float *image, const float *dL_dimage, float *grad2d, int32_t *status,
                      void *stream) {
-    (void)status;
     Launch L;
     int rc = build_launch(vw, cfg, L);
     if (rc) return rc;
@@ -249,7 +283,6 @@ int gs_rasterize_bwd(const gs_views *vw, const gs_config *cfg, const float *proj
 int gs_project_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, const float *proj,
                    const float *grad2d, const gs_grads *out, int want_gaussian_grads, int32_t *status,
                    void *stream) {
-    (void)status;
     Launch L;
     int rc = build_launch(vw, cfg, L);
     if (rc) return rc;

@@ -1,6 +1,7 @@
 // Internal definitions shared by the CUDA sources of libgsplat_gb300.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap and its enums (types only: the encoder is fetched from the driver at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -257,8 +258,78 @@ __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, flo
 }
 
 // ---------------------------------------------------------------------------
+// asynchronous bulk copies (TMA) with an mbarrier, PTX ISA "cp.async.bulk"
+// and "mbarrier". Every wait is bounded: it gives up after ~2^20 polls of
+// mbarrier.try_wait (each poll may suspend the thread for a while), so a
+// copy that never lands ends in an error status instead of a hang.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// true once the barrier's phase `parity` has completed; false if the bounded
+// number of polls ran out first
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (int it = 0; it < (1 << 20); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 2D tiled load of the box at (x, y) (x in elements, a multiple of 16 bytes)
+// into shared memory, completing on bar
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 2D tiled store of a shared-memory box to (x, y) (x = 0 here; rows outside
+// the tensor are not written), tracked by the issuing thread's bulk group
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of all committed bulk stores have been read
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// make this thread's generic shared-memory writes visible to bulk copies
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16-byte chunk c of row r of a box staged with the 128-byte swizzle (rows
+// of 128 bytes) or the 64-byte swizzle (rows of 64 bytes): the hardware XORs
+// the chunk index with address bits 7..9 (7..8), so a thread reading chunk c
+// of its own row hits a different bank group than its neighbours
+__device__ __forceinline__ int swz128(int r, int c) { return r * 8 + (c ^ (r & 7)); }
+__device__ __forceinline__ int swz64(int r, int c) { return r * 4 + (c ^ ((r >> 1) & 3)); }
+
+// ---------------------------------------------------------------------------
 // host-side launch helpers (defined in gs_api.cu)
 // ---------------------------------------------------------------------------
 int num_sms();
+// encode a 2D float32 tensor map: `rows` rows of `inner` floats, `row_bytes`
+// apart, box = box_inner x box_rows, with the given swizzle; false if the
+// driver's encoder is unavailable or rejects the description
+bool encode_tmap_2d(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
+                    uint32_t box_inner, uint32_t box_rows, CUtensorMapSwizzle swizzle);
 
 }  // namespace gsk

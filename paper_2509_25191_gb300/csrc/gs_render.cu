@@ -23,6 +23,9 @@
 // Per-Gaussian gradients (mean2D, 2D covariance, opacity, colour) are summed over a
 // warp with a 12-shuffle reduce-scatter, over the block in shared memory, and
 // added to the per-slot grad2d record with one vector atomic per float4.
+// The backward runs a thread's two pixels through packed float2 arithmetic
+// (f32x2 fma/mul/add, one instruction for both), branch-free: a pixel that
+// does not composite a Gaussian contributes zeros.
 #include "gs_common.cuh"
 
 namespace gsk {
@@ -60,6 +63,18 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ proj, unsigned 
 //          for every staged, positive-definite conic, so no guard),
 //   G = 2^p2, alpha = min(alpha_max, o G) ("clamped" if o G > alpha_max),
 //   skipped if alpha < alpha_min.
+
+// Packed pair arithmetic (sm_100+ f32x2): a thread's two pixels run through
+// one instruction stream, lane .x = pixel (px, py0), lane .y = pixel
+// (px, py0 + 4). Each lane of a packed operation is the IEEE-rounded scalar
+// operation, so the backward reproduces the forward's scalar alpha and
+// transmittance bit for bit.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 struct TileInfo {
     int view;
@@ -303,57 +318,6 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
     }
 }
 
-// One pixel's contribution to the gradient of Gaussian k (added into gv),
-// advancing the pixel's transmittance and colour sum exactly as the forward.
-// Returns 0 if the Gaussian was not evaluated at this pixel, 1 if its alpha
-// was evaluated but it was not composited, 2 if it was composited.
-// Gradient contribution of one staged Gaussian at one pixel whose alpha
-// (>= alpha_min) was already formed: 1 if the pixel stops before it (T would
-// fall below t_min), 2 if it was composited.
-__device__ __forceinline__ int pixel_grad(const float4 &c, const float4 &con, float2 ad, float alpha, float G,
-                                           float dy, float u, bool clamped, const Launch &L, float ig, float g0,
-                                           float g1, float g2, float &T, float &CG, bool &done, float *gv) {
-    const float oma = __fsub_rn(1.f, alpha);
-    const float Tn = __fmul_rn(T, oma);
-    if (Tn < L.t_min) {
-        done = true;
-        return 1;
-    }
-    const float w = __fmul_rn(alpha, T);
-    gv[6] += w * g0;
-    gv[7] += w * g1;
-    gv[8] += w * g2;
-    // with cg = c.g: the running colour C (through this Gaussian) enters only
-    // as C.g, accumulated as CG += w cg, and the colour behind it is
-    // S = image - C, so S.g = image.g - CG. 1 - alpha >= 0.01, so the fast
-    // reciprocal's few-ulp error is far inside the gradient tolerance.
-    const float cgk = c.x * g0 + c.y * g1 + c.z * g2;
-    CG = fmaf(w, cgk, CG);
-    const float dL_dalpha = T * cgk - __fdividef(ig - CG, oma);
-    if (!clamped) {
-        // alpha = o G, G = exp(power), power = -1/2 d^T Q d with Q the conic
-        // (inverse of the covariance Sigma' = (a, b, c)), d = pixel - mean.
-        // With v = Q d = (A u, A beta u + D dy) from the staged form,
-        // d power / d mean = v and d power / d Sigma' = v v^T / 2, i.e.
-        // (v0^2/2, v0 v1, v1^2/2) for (a, b, c): summing these well-scaled
-        // terms over pixels avoids the ill-conditioned conic -> covariance
-        // conversion of summed conic gradients for elongated Gaussians. The
-        // halves of gv[2] and gv[4] are applied once, to the sums.
-        gv[5] += dL_dalpha * G;
-        const float dp = dL_dalpha * alpha;
-        const float v0 = ad.x * u;
-        const float v1 = v0 * con.y + ad.y * dy;
-        const float dv0 = dp * v0, dv1 = dp * v1;
-        gv[0] += dv0;
-        gv[1] += dv1;
-        gv[2] += dv0 * v0;
-        gv[3] += dv0 * v1;
-        gv[4] += dv1 * v1;
-    }
-    T = Tn;
-    return 2;
-}
-
 template <int TW, int TH, bool COUNT>
 __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, const float4 *__restrict__ proj,
                                                             const int2 *__restrict__ ranges,
@@ -388,25 +352,30 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
         const int2 r = ranges[tile];
         const ViewDesc &vd = L.v[ti.view];
         const long long hw = (long long)vd.W * vd.H;
-        // per pixel: upstream gradient g, image.g, and the running colour dotted
-        // with g (the colour behind a Gaussian enters dL/dalpha only as S.g)
+        // per pixel: upstream gradient g (one pair per channel), -image.g, and
+        // the running colour dotted with g (the colour behind a Gaussian enters
+        // dL/dalpha only as S.g = image.g - C.g)
         float gg[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, ig[2] = {0.f, 0.f};
-        bool done[2] = {!ti.in0, !ti.in1};
+        bool done0 = !ti.in0, done1 = !ti.in1;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            if (done[h]) continue;
+            if (!(h ? ti.in1 : ti.in0)) continue;
             const long long o = vd.pix_base + (long long)(ti.py0 + 4 * h) * vd.W + ti.px;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 gg[h][ch] = dL_dimage[o + ch * hw];
                 ig[h] = fmaf(image[o + ch * hw], gg[h][ch], ig[h]);
             }
-            done[h] = gg[h][0] == 0.f && gg[h][1] == 0.f && gg[h][2] == 0.f;
         }
-        float T[2] = {1.f, 1.f}, cg[2] = {0.f, 0.f};
+        done0 = done0 || (gg[0][0] == 0.f && gg[0][1] == 0.f && gg[0][2] == 0.f);
+        done1 = done1 || (gg[1][0] == 0.f && gg[1][1] == 0.f && gg[1][2] == 0.f);
+        const float2 GR = make_float2(gg[0][0], gg[1][0]), GG = make_float2(gg[0][1], gg[1][1]),
+                     GB = make_float2(gg[0][2], gg[1][2]), NIG = make_float2(-ig[0], -ig[1]);
+        const float2 PCY = make_float2(ti.pcy0, ti.pcy0 + 4.f);
+        float2 T = f2(1.f), CG = f2(0.f);
         unsigned int n_eval = 0, n_comp = 0;
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
-            if (__syncthreads_count(done[0] && done[1]) == BS) break;
+            if (__syncthreads_count(done0 && done1) == BS) break;
             stage_batch<TW, TH>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -417,54 +386,70 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
             __syncthreads();
             const int nb = min(NB, r.y - b0);
             for (int k0 = 0; k0 < nb; k0 += 32) {
-                if (__all_sync(0xffffffffu, done[0] && done[1])) break;   // the warp's pixels have all stopped
+                if (__all_sync(0xffffffffu, done0 && done1)) break;   // the warp's pixels have all stopped
                 // only the staged Gaussians that may reach this warp's patch, in order
                 unsigned int hits = __ballot_sync(0xffffffffu, k0 + lane < nb && (s_mask[k0 + lane] & wbit));
                 while (hits) {
                     const int k = k0 + __ffs(hits) - 1;
                     hits &= hits - 1;
-                    // gradient of this thread's pixels w.r.t. (x, y, a, b, c, o, r, g, b) of Gaussian k
-                    float gv[9];
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) gv[c] = 0.f;
-                    bool hit = false;
-                    const float4 xy = s_xy[k], con = s_con[k], c = s_rgb[k];
-                    const float2 ad = s_ad[k];
+                    const float4 xy = s_xy[k], con = s_con[k];
+                    // both pixels' alphas, the forward's arithmetic and decisions
                     const float dx = __fsub_rn(ti.pcx, xy.x);
-                    if (fabsf(dx) <= xy.z) {   // the column gate, shared by both pixels
-                        // both pixels' alphas first (two independent chains, the
-                        // forward's arithmetic and decisions), then the gradients
-                        float dyh[2], uh[2], Gh[2], ah[2];
-                        bool clh[2], evh[2], okh[2];
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            dyh[h] = __fsub_rn(ti.pcy0 + 4.f * h, xy.y);
-                            uh[h] = __fmaf_rn(con.y, dyh[h], dx);
-                            const float p2 = __fmaf_rn(con.x, __fmul_rn(uh[h], uh[h]),
-                                                       __fmul_rn(con.z, __fmul_rn(dyh[h], dyh[h])));
-                            Gh[h] = ex2_approx(p2);
-                            const float oG = __fmul_rn(con.w, Gh[h]);
-                            clh[h] = oG > L.alpha_max;
-                            ah[h] = clh[h] ? L.alpha_max : oG;
-                            evh[h] = !done[h] && fabsf(dyh[h]) <= xy.w;
-                            okh[h] = evh[h] && ah[h] >= L.alpha_min;
-                        }
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            if (!okh[h]) {
-                                if (COUNT) n_eval += evh[h];
-                                continue;
-                            }
-                            const int res = pixel_grad(c, con, ad, ah[h], Gh[h], dyh[h], uh[h], clh[h], L, ig[h],
-                                                       gg[h][0], gg[h][1], gg[h][2], T[h], cg[h], done[h], gv);
-                            hit |= res == 2;
-                            if (COUNT) {
-                                n_eval += 1;
-                                n_comp += res == 2;
-                            }
-                        }
-                    }
-                    if (__any_sync(0xffffffffu, hit)) {
+                    const bool col = fabsf(dx) <= xy.z;   // the column gate, shared by both pixels
+                    const float2 dy = __fadd2_rn(PCY, f2(-xy.y));
+                    const float2 u = __ffma2_rn(f2(con.y), dy, f2(dx));
+                    const float2 p2 = __ffma2_rn(f2(con.x), __fmul2_rn(u, u), __fmul2_rn(f2(con.z), __fmul2_rn(dy, dy)));
+                    const float2 G = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
+                    const float2 oG = __fmul2_rn(f2(con.w), G);
+                    const bool cl0 = oG.x > L.alpha_max, cl1 = oG.y > L.alpha_max;
+                    const float a0 = cl0 ? L.alpha_max : oG.x, a1 = cl1 ? L.alpha_max : oG.y;
+                    const bool ev0 = col && !done0 && fabsf(dy.x) <= xy.w, ev1 = col && !done1 && fabsf(dy.y) <= xy.w;
+                    const bool ok0 = ev0 && a0 >= L.alpha_min, ok1 = ev1 && a1 >= L.alpha_min;
+                    if (COUNT) n_eval += (unsigned int)ev0 + (unsigned int)ev1;
+                    if (!__any_sync(0xffffffffu, ok0 || ok1)) continue;
+                    // transmittance: the pixel stops before a Gaussian that would
+                    // bring T below t_min; otherwise the Gaussian is composited
+                    const float2 oma = __fadd2_rn(f2(1.f), make_float2(-a0, -a1));
+                    const float2 Tn = __fmul2_rn(T, oma);
+                    const bool st0 = ok0 && Tn.x < L.t_min, st1 = ok1 && Tn.y < L.t_min;
+                    const bool cp0 = ok0 && !st0, cp1 = ok1 && !st1;
+                    done0 = done0 || st0;
+                    done1 = done1 || st1;
+                    if (COUNT) n_comp += (unsigned int)cp0 + (unsigned int)cp1;
+                    // gradients; a pixel that does not composite contributes zeros
+                    // (its weight and its alpha factors are zero)
+                    const float4 c = s_rgb[k];
+                    const float2 ad = s_ad[k];
+                    const float2 w = __fmul2_rn(make_float2(cp0 ? a0 : 0.f, cp1 ? a1 : 0.f), T);
+                    const float2 Told = T;
+                    T = make_float2(cp0 ? Tn.x : T.x, cp1 ? Tn.y : T.y);
+                    const float2 g6 = __fmul2_rn(w, GR), g7 = __fmul2_rn(w, GG), g8 = __fmul2_rn(w, GB);
+                    // c.g, and C.g accumulated through this Gaussian; S.g = image.g - C.g,
+                    // dL/dalpha = T (c.g) - (S.g) / (1 - alpha) (1 - alpha >= 0.01, so
+                    // the approximate reciprocal's few-ulp error is far inside the
+                    // gradient tolerance)
+                    const float2 cgk = __ffma2_rn(f2(c.z), GB, __ffma2_rn(f2(c.y), GG, __fmul2_rn(f2(c.x), GR)));
+                    CG = __ffma2_rn(w, cgk, CG);
+                    const float2 q = __fmul2_rn(__fadd2_rn(CG, NIG), make_float2(rcp_approx(oma.x), rcp_approx(oma.y)));
+                    const float2 dla = __ffma2_rn(Told, cgk, q);
+                    // alpha = o G unless clamped; G = exp(power), power = -1/2 d^T Q d,
+                    // Q the conic, d = pixel - mean. With v = Q d = (A u, A beta u + D dy)
+                    // from the staged form, d power / d mean = v and d power / d Sigma' =
+                    // v v^T / 2, i.e. (v0^2/2, v0 v1, v1^2/2) for (a, b, c); summing these
+                    // well-scaled terms avoids the ill-conditioned conic -> covariance
+                    // conversion of summed conic gradients. The halves of the (a) and (c)
+                    // sums are applied once, at the flush.
+                    const bool un0 = cp0 && !cl0, un1 = cp1 && !cl1;
+                    const float2 g5 = __fmul2_rn(dla, make_float2(un0 ? G.x : 0.f, un1 ? G.y : 0.f));
+                    const float2 dp = __fmul2_rn(dla, make_float2(un0 ? a0 : 0.f, un1 ? a1 : 0.f));
+                    const float2 v0 = __fmul2_rn(f2(ad.x), u);
+                    const float2 v1 = __ffma2_rn(v0, f2(con.y), __fmul2_rn(f2(ad.y), dy));
+                    const float2 g0 = __fmul2_rn(dp, v0), g1 = __fmul2_rn(dp, v1);
+                    const float2 g2 = __fmul2_rn(g0, v0), g3 = __fmul2_rn(g0, v1), g4 = __fmul2_rn(g1, v1);
+                    if (__any_sync(0xffffffffu, cp0 || cp1)) {
+                        // gradient of this thread's pixels w.r.t. (x, y, a, b, c, o, r, g, b)
+                        float gv[9] = {g0.x + g0.y, g1.x + g1.y, g2.x + g2.y, g3.x + g3.y, g4.x + g4.y,
+                                       g5.x + g5.y, g6.x + g6.y, g7.x + g7.y, g8.x + g8.y};
                         const float sum = warp_reduce_scatter9(gv, lane);
                         if (red_own) atomicAdd(&s_g[k][red_idx], sum);
                     }
