@@ -23,7 +23,7 @@
 // Per-Gaussian gradients (mean2D, 2D covariance, opacity, colour) are summed over a
 // warp with a 12-shuffle reduce-scatter, over the block in shared memory, and
 // added to the per-slot grad2d record with one vector atomic per float4.
-// The backward runs a thread's two pixels through packed float2 arithmetic
+// Both kernels run a thread's two pixels through packed float2 arithmetic
 // (f32x2 fma/mul/add, one instruction for both), branch-free: a pixel that
 // does not composite a Gaussian contributes zeros.
 #include "gs_common.cuh"
@@ -241,9 +241,10 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
         const int tile = order[item];
         const TileInfo ti = tile_info<TW, TH>(L, tile);
         const int2 r = abort ? make_int2(0, 0) : ranges[tile];
-        float T0 = 1.f, T1 = 1.f, C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
+        // lane .x = pixel (px, py0), lane .y = pixel (px, py0 + 4)
+        float2 T = f2(1.f), CR = f2(0.f), CG = f2(0.f), CB = f2(0.f);
         bool done0 = !ti.in0, done1 = !ti.in1;
-        const float pcy1 = ti.pcy0 + 4.f;
+        const float2 PCY = make_float2(ti.pcy0, ti.pcy0 + 4.f);
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
             if (__syncthreads_count(done0 && done1) == BS) break;
             stage_batch<TW, TH>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
@@ -259,48 +260,33 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
                     hits &= hits - 1;
                     const float4 xy = s_xy[k], con = s_con[k];
                     const float dx = __fsub_rn(ti.pcx, xy.x);
-                    if (fabsf(dx) > xy.z) continue;   // the column gate, shared by both pixels
-                    // both pixels' alphas first (two independent chains), then the
-                    // order-dependent updates
-                    const float dy0 = __fsub_rn(ti.pcy0, xy.y), dy1 = __fsub_rn(pcy1, xy.y);
-                    const float u0 = __fmaf_rn(con.y, dy0, dx), u1 = __fmaf_rn(con.y, dy1, dx);
-                    const float p0 = __fmaf_rn(con.x, __fmul_rn(u0, u0), __fmul_rn(con.z, __fmul_rn(dy0, dy0)));
-                    const float p1 = __fmaf_rn(con.x, __fmul_rn(u1, u1), __fmul_rn(con.z, __fmul_rn(dy1, dy1)));
-                    const float oG0 = __fmul_rn(con.w, ex2_approx(p0)), oG1 = __fmul_rn(con.w, ex2_approx(p1));
-                    const float a0 = oG0 > L.alpha_max ? L.alpha_max : oG0;
-                    const float a1 = oG1 > L.alpha_max ? L.alpha_max : oG1;
-                    const bool ok0 = !done0 && fabsf(dy0) <= xy.w && a0 >= L.alpha_min;
-                    const bool ok1 = !done1 && fabsf(dy1) <= xy.w && a1 >= L.alpha_min;
-                    if (ok0) {
-                        const float Tn = __fmul_rn(T0, __fsub_rn(1.f, a0));
-                        if (Tn < L.t_min) {
-                            done0 = true;
-                        } else {
-                            const float w = __fmul_rn(a0, T0);
-                            const float4 c = s_rgb[k];
-                            C00 = __fmaf_rn(c.x, w, C00);
-                            C01 = __fmaf_rn(c.y, w, C01);
-                            C02 = __fmaf_rn(c.z, w, C02);
-                            T0 = Tn;
-                        }
-                    }
-                    if (ok1) {
-                        const float alpha = a1;
-                        const float Tn = __fmul_rn(T1, __fsub_rn(1.f, alpha));
-                        if (Tn < L.t_min) {
-                            done1 = true;
-                        } else {
-                            const float w = __fmul_rn(alpha, T1);
-                            const float4 c = s_rgb[k];
-                            C10 = __fmaf_rn(c.x, w, C10);
-                            C11 = __fmaf_rn(c.y, w, C11);
-                            C12 = __fmaf_rn(c.z, w, C12);
-                            T1 = Tn;
-                        }
-                    }
+                    const bool col = fabsf(dx) <= xy.z;   // the column gate, shared by both pixels
+                    const float2 dy = __fadd2_rn(PCY, f2(-xy.y));
+                    const float2 u = __ffma2_rn(f2(con.y), dy, f2(dx));
+                    const float2 p2 = __ffma2_rn(f2(con.x), __fmul2_rn(u, u), __fmul2_rn(f2(con.z), __fmul2_rn(dy, dy)));
+                    const float2 oG = __fmul2_rn(f2(con.w), make_float2(ex2_approx(p2.x), ex2_approx(p2.y)));
+                    const float a0 = oG.x > L.alpha_max ? L.alpha_max : oG.x;
+                    const float a1 = oG.y > L.alpha_max ? L.alpha_max : oG.y;
+                    const bool ok0 = col && !done0 && fabsf(dy.x) <= xy.w && a0 >= L.alpha_min;
+                    const bool ok1 = col && !done1 && fabsf(dy.y) <= xy.w && a1 >= L.alpha_min;
+                    if (!__any_sync(0xffffffffu, ok0 || ok1)) continue;
+                    // the Gaussian that would bring T below t_min is not composited
+                    // and the pixel stops; otherwise C += c alpha T, T *= 1 - alpha
+                    const float2 Tn = __fmul2_rn(T, __fadd2_rn(f2(1.f), make_float2(-a0, -a1)));
+                    const bool st0 = ok0 && Tn.x < L.t_min, st1 = ok1 && Tn.y < L.t_min;
+                    const bool cp0 = ok0 && !st0, cp1 = ok1 && !st1;
+                    done0 = done0 || st0;
+                    done1 = done1 || st1;
+                    const float2 w = __fmul2_rn(make_float2(cp0 ? a0 : 0.f, cp1 ? a1 : 0.f), T);
+                    T = make_float2(cp0 ? Tn.x : T.x, cp1 ? Tn.y : T.y);
+                    const float4 c = s_rgb[k];
+                    CR = __ffma2_rn(f2(c.x), w, CR);
+                    CG = __ffma2_rn(f2(c.y), w, CG);
+                    CB = __ffma2_rn(f2(c.z), w, CB);
                 }
             }
         }
+        const float T0 = T.x, T1 = T.y, C00 = CR.x, C01 = CG.x, C02 = CB.x, C10 = CR.y, C11 = CG.y, C12 = CB.y;
         const ViewDesc &vd = L.v[ti.view];
         const long long hw = (long long)vd.W * vd.H;
         if (ti.in0) {
