@@ -16,7 +16,7 @@ int launch_render_bwd(const Launch &L, const float *proj, const gs_bins *b, cons
                       const float *dL_dimage, float *grad2d, cudaStream_t st);
 int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const float *viewmats, const float *intr,
                        const float *proj, const float *grad2d, const gs_grads *out, int want_gauss, int nblk,
-                       cudaStream_t st);
+                       int32_t *status, cudaStream_t st);
 int launch_pose_reduce(int n_views, const float *partials, int nblk, const float *viewmats, float *out_rt,
                        float *out_twist, cudaStream_t st);
 int launch_l1(const float *image, const float *target, long long n, float *loss, float *grad, cudaStream_t st);
@@ -309,7 +309,7 @@ int gs_project_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *c
         }
     }
     return launch_project_bwd(L, g->sh_degree, g, vw->viewmats, vw->intrinsics, proj, grad2d, out,
-                              want_gaussian_grads, pose_blocks(g->n), st);
+                              want_gaussian_grads, pose_blocks(g->n), status, st);
 }
 
 int gs_render_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, const float *proj,
@@ -476,7 +476,6 @@ extern "C" int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *vw,
                                       const float *proj, const float *grad2d, const gs_grads *grads,
                                       int want_gaussian_grads, float *dL_dviewmat, float *dL_dtwist,
                                       int32_t *status, void *stream) {
-    (void)status;
     Launch L;
     int rc = build_launch(vw, cfg, L);
     if (rc) return rc;
@@ -508,7 +507,7 @@ extern "C" int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *vw,
     gs_grads out = *grads;
     out.pose_partials = scratch;   // every partial the reduction reads is written first
     rc = launch_project_bwd(L, g->sh_degree, g, vw->viewmats, vw->intrinsics, proj, grad2d, &out,
-                            want_gaussian_grads, nblk, st);
+                            want_gaussian_grads, nblk, status, st);
     if (rc) return rc;
     return launch_pose_reduce(L.n_views, scratch, nblk, vw->viewmats, dL_dviewmat, dL_dtwist, st);
 }

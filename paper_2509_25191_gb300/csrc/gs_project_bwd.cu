@@ -16,31 +16,56 @@
 //   tangent), mean2D = f x / z + c, m = R_v mu + t_v, Sigma = M M^T with
 //   M = R(q) diag(exp l), q normalised, o = sigmoid, colour = max(0,
 //   sum f_k Y_k(d) + 0.5), d = normalise(mu - C_v), C_v = -R_v^T t_v.
+#include <stdlib.h>
+#include <string.h>
+
 #include "gs_common.cuh"
 
 namespace gsk {
 
-constexpr int PB_THREADS = 128;   // 128 registers and 38 KB shared: 4 blocks per SM, no spills
+constexpr int PB_THREADS = 128;   // 128 registers: 4 blocks per SM, no spills
 constexpr int PB_WARPS = PB_THREADS / 32;
 
-template <int DEG, bool GAUSS>
+// Staging of a block's 128 Gaussians on the degree-3 path: the SH rows arrive
+// by two tensor copies (a 32-float box with the 128-byte swizzle and a
+// 16-float box with the 64-byte swizzle: a thread reads its own row 16 bytes
+// at a time without bank conflicts), and the SH-coefficient gradients are
+// summed over views in the same layout and leave by two tensor stores.
+struct PbStage {
+    float4 shA[PB_THREADS * 8];
+    float4 shB[PB_THREADS * 4];
+    float4 gA[PB_THREADS * 8];
+    float4 gB[PB_THREADS * 4];
+    unsigned long long bar;
+};
+
+template <int DEG, bool GAUSS, bool TMA>
 __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
     const Launch L, const float *__restrict__ means, const float *__restrict__ log_scales,
     const float *__restrict__ quats, const float *__restrict__ logits, const float *__restrict__ sh,
     const float *__restrict__ viewmats, const float *__restrict__ intr, const float4 *__restrict__ proj,
     const float4 *__restrict__ grad2d, float *__restrict__ g_means, float *__restrict__ g_log_scales,
     float *__restrict__ g_quats, float *__restrict__ g_logits, float *__restrict__ g_sh,
-    float *__restrict__ pose_partials) {
+    float *__restrict__ pose_partials, const __grid_constant__ CUtensorMap tm_shA,
+    const __grid_constant__ CUtensorMap tm_shB, const __grid_constant__ CUtensorMap tm_gA,
+    const __grid_constant__ CUtensorMap tm_gB, int *__restrict__ status) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int GP = 3 * K + 1;   // odd row pitch: conflict-free column access
-    __shared__ float s_pose[PB_WARPS][GS_MAX_VIEWS][12];
+    static_assert(!TMA || DEG == 3, "the staged path is for 48-float SH rows");
+    // per-warp pose partials [PB_WARPS][n_views][12] (dynamic: sized by the launch)
+    extern __shared__ float s_pose[];
     // per-thread SH-coefficient gradients, summed over views here and written
-    // out by the whole block with coalesced stores
-    __shared__ float s_gf[GAUSS ? PB_THREADS * GP : 1];
-    __shared__ long long s_row[GAUSS ? PB_THREADS : 1];
+    // out by the whole block with coalesced stores (per-thread path)
+    __shared__ float s_gf[GAUSS && !TMA ? PB_THREADS * GP : 1];
+    __shared__ long long s_row[GAUSS && !TMA ? PB_THREADS : 1];
+    __shared__ __align__(1024) PbStage S[1];   // (removed by the compiler where unused)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < PB_WARPS * GS_MAX_VIEWS * 12; i += PB_THREADS) (&s_pose[0][0][0])[i] = 0.f;
+    const int nv = L.n_views;
+    for (int i = threadIdx.x; i < PB_WARPS * nv * 12; i += PB_THREADS) s_pose[i] = 0.f;
+    if (TMA && threadIdx.x == 0) mbar_init(&S[0].bar, 1);
     __syncthreads();
+    uint32_t phase = 0;
+    const int r = threadIdx.x;   // this thread's row of the staging boxes
 
     const long long stride = (long long)gridDim.x * PB_THREADS;
     for (long long base = (long long)blockIdx.x * PB_THREADS; base < L.n_threads; base += stride) {
@@ -52,9 +77,49 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
         const int vb = valid ? L.s[s].v_begin : 0x7fffffff, ve = valid ? L.s[s].v_end : 0;
         const int wvb = __reduce_min_sync(0xffffffffu, vb), wve = __reduce_max_sync(0xffffffffu, ve);
 
+        // a block iteration is "full" when its 128 threads are Gaussians of one
+        // scene: its SH rows (and gradient rows) are then contiguous boxes
+        bool full = false;
+        int row0 = 0;
+        if constexpr (TMA) {
+            const long long last = base + PB_THREADS - 1;
+            if (last < L.n_threads) {
+                const int s0 = scene_of_thread(L, base);
+                full = scene_of_thread(L, last) == s0 && (smem_u32(S[0].shA) & 1023u) == 0;
+                row0 = (int)(L.s[s0].g_begin + base - L.s[s0].thread_base);
+            }
+            if (threadIdx.x == 0) {
+                // the previous iteration's gradient stores have read the staging
+                if (GAUSS) bulk_wait_read_all();
+                if (full) {
+                    fence_async_smem();
+                    mbar_expect_tx(&S[0].bar, PB_THREADS * 48 * 4);
+                    tma_load_2d(S[0].shA, &tm_shA, 0, row0, &S[0].bar);
+                    tma_load_2d(S[0].shB, &tm_shB, 32, row0, &S[0].bar);
+                }
+            }
+            __syncthreads();
+            if (!full && valid) {
+                // a partial iteration stages its rows itself, in the same layout
+                const float4 *src = reinterpret_cast<const float4 *>(sh + 48LL * i);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) S[0].shA[swz128(r, c)] = src[c];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) S[0].shB[swz64(r, c)] = src[8 + c];
+            }
+            if (GAUSS) {
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) S[0].gA[swz128(r, c)] = z;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) S[0].gB[swz64(r, c)] = z;
+            }
+        }
+
         float mx = 0.f, my = 0.f, mz = 0.f, sc[3] = {0.f, 0.f, 0.f}, qn[4] = {1.f, 0.f, 0.f, 0.f}, qlen = 1.f;
         float Rq[9], M[9], S00 = 0, S01 = 0, S02 = 0, S11 = 0, S12 = 0, S22 = 0, opac = 0.f;
-        // SH coefficients are read per view where needed (L1-resident), not held in registers
+        // SH coefficients are read per view where needed (L1-resident or
+        // staged), not held in registers
         const float *f = sh + (long long)3 * K * (valid ? i : 0);
         if (valid) {
             mx = means[3 * i]; my = means[3 * i + 1]; mz = means[3 * i + 2];
@@ -81,11 +146,29 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
         // accumulators over views
         float gm[3] = {0.f, 0.f, 0.f}, go = 0.f;
         float GS00 = 0, GS01 = 0, GS02 = 0, GS11 = 0, GS12 = 0, GS22 = 0;   // full-matrix entries, symmetric
-        float *gf = s_gf + (GAUSS ? threadIdx.x * GP : 0);
-        if (GAUSS) {
+        float *gf = s_gf + (GAUSS && !TMA ? threadIdx.x * GP : 0);
+        if (GAUSS && !TMA) {
 #pragma unroll
             for (int k = 0; k < 3 * K; ++k) gf[k] = 0.f;
             s_row[threadIdx.x] = valid ? i : -1;
+        }
+        if constexpr (TMA) {
+            if (full) {
+                const bool ok = __syncthreads_and(mbar_wait(&S[0].bar, phase));
+                phase ^= 1;
+                if (!ok) {
+                    if (threadIdx.x == 0) {
+                        if (status) {
+                            atomicCAS(status, 0, GS_ERR_TIMEOUT);
+                            atomicExch(status + 1, (int)blockIdx.x);
+                        }
+                        mbar_wait(&S[0].bar, phase ^ 1);   // give the copy in flight (bounded) time to land
+                    }
+                    return;
+                }
+            } else {
+                __syncthreads();   // the partial iteration's rows are staged
+            }
         }
 
         for (int v = wvb; v < wve; ++v) {
@@ -150,7 +233,15 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                         float gY[16];
 #pragma unroll
                         for (int k = 0; k < K; ++k) gY[k] = 0.f;
-                        if (DEG == 1 || DEG == 3) {
+                        if (TMA) {
+#pragma unroll
+                            for (int j = 0; j < 12; ++j) {
+                                const float4 q4 = j < 8 ? S[0].shA[swz128(r, j)] : S[0].shB[swz64(r, j - 8)];
+                                const float fv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) gY[(4 * j + e) / 3] += fv[e] * graw[(4 * j + e) % 3];
+                            }
+                        } else if (DEG == 1 || DEG == 3) {
                             // 3K floats = 3K/4 float4 (rows are 16-byte aligned for these degrees)
                             const float4 *f4 = reinterpret_cast<const float4 *>(f);
 #pragma unroll
@@ -166,7 +257,18 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                                 gY[k] = __ldg(f + 3 * k) * graw[0] + __ldg(f + 3 * k + 1) * graw[1] +
                                         __ldg(f + 3 * k + 2) * graw[2];
                         }
-                        if (GAUSS) {
+                        if (GAUSS && TMA) {
+#pragma unroll
+                            for (int j = 0; j < 12; ++j) {
+                                float4 &gq = j < 8 ? S[0].gA[swz128(r, j)] : S[0].gB[swz64(r, j - 8)];
+                                float4 t = gq;
+                                t.x += Yb[(4 * j) / 3] * graw[(4 * j) % 3];
+                                t.y += Yb[(4 * j + 1) / 3] * graw[(4 * j + 1) % 3];
+                                t.z += Yb[(4 * j + 2) / 3] * graw[(4 * j + 2) % 3];
+                                t.w += Yb[(4 * j + 3) / 3] * graw[(4 * j + 3) % 3];
+                                gq = t;
+                            }
+                        } else if (GAUSS) {
 #pragma unroll
                             for (int k = 0; k < K; ++k) {
                                 gf[3 * k] += Yb[k] * graw[0];
@@ -260,7 +362,7 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                 }
                 if (lane == 0) {
 #pragma unroll
-                    for (int cc = 0; cc < 12; ++cc) s_pose[wid][v][cc] += pg[cc];
+                    for (int cc = 0; cc < 12; ++cc) s_pose[(wid * nv + v) * 12 + cc] += pg[cc];
                 }
             }
         }
@@ -298,23 +400,46 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
             g_means[3 * i + 2] = gm[2];
             g_logits[i] = go * opac * (1.f - opac);
         }
-        if (GAUSS) {
+        if constexpr (GAUSS && TMA) {
+            if (full) {
+                // the block's SH-coefficient gradient rows leave as two boxes
+                fence_async_smem();
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    tma_store_2d(&tm_gA, S[0].gA, 0, row0);
+                    tma_store_2d(&tm_gB, S[0].gB, 32, row0);
+                    bulk_commit();
+                }
+            } else {
+                if (valid) {
+                    float4 *dst = reinterpret_cast<float4 *>(g_sh + 48LL * i);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) dst[c] = S[0].gA[swz128(r, c)];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) dst[8 + c] = S[0].gB[swz64(r, c)];
+                }
+                __syncthreads();
+            }
+        } else if constexpr (GAUSS) {
             // the block's SH-coefficient gradients: row r goes to Gaussian s_row[r]
             __syncthreads();
             for (int e = threadIdx.x; e < PB_THREADS * 3 * K; e += PB_THREADS) {
-                const int r = e / (3 * K), c = e % (3 * K);
-                const long long row = s_row[r];
-                if (row >= 0) g_sh[row * 3 * K + c] = s_gf[r * GP + c];
+                const int rr = e / (3 * K), c = e % (3 * K);
+                const long long row = s_row[rr];
+                if (row >= 0) g_sh[row * 3 * K + c] = s_gf[rr * GP + c];
             }
             __syncthreads();
+        } else if constexpr (TMA) {
+            __syncthreads();   // the staged SH rows are free for the next iteration
         }
     }
+    if (TMA && GAUSS && threadIdx.x == 0) bulk_wait_read_all();
     __syncthreads();
-    for (int e = threadIdx.x; e < L.n_views * 12; e += PB_THREADS) {
+    for (int e = threadIdx.x; e < nv * 12; e += PB_THREADS) {
         const int v = e / 12, cc = e % 12;
         float acc = 0.f;
 #pragma unroll
-        for (int ww = 0; ww < PB_WARPS; ++ww) acc += s_pose[ww][v][cc];
+        for (int ww = 0; ww < PB_WARPS; ++ww) acc += s_pose[(ww * nv + v) * 12 + cc];
         pose_partials[((long long)v * gridDim.x + blockIdx.x) * 12 + cc] = acc;
     }
 }
@@ -329,27 +454,41 @@ int pose_blocks(long long n) {
 
 int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const float *viewmats, const float *intr,
                        const float *proj, const float *grad2d, const gs_grads *out, int want_gauss, int nblk,
-                       cudaStream_t st) {
+                       int32_t *status, cudaStream_t st) {
     const float4 *p = reinterpret_cast<const float4 *>(proj);
     const float4 *g2 = reinterpret_cast<const float4 *>(grad2d);
-#define GS_PB(D, G)                                                                                              \
-    k_project_bwd<D, G><<<nblk, PB_THREADS, 0, st>>>(L, g->means, g->log_scales, g->quats, g->opacity_logits,  \
-                                                     g->sh, viewmats, intr, p, g2, out->means, out->log_scales, \
-                                                     out->quats, out->opacity_logits, out->sh, out->pose_partials)
+    const size_t dyn = (size_t)PB_WARPS * L.n_views * 12 * sizeof(float);
+    CUtensorMap ma, mb, ga, gb;
+    memset(&ma, 0, sizeof ma); memset(&mb, 0, sizeof mb); memset(&ga, 0, sizeof ga); memset(&gb, 0, sizeof gb);
+    // degree 3 with 16-byte aligned SH rows (and gradient rows): the staged
+    // path, unless the environment sets GS_DISABLE_TMA=1
+    const char *no_tma = getenv("GS_DISABLE_TMA");
+    bool tma = deg == 3 && !(no_tma && no_tma[0] == '1') && ((uintptr_t)g->sh & 15u) == 0 &&
+               g->n < 0x7fffffffLL &&
+               encode_tmap_2d(&ma, g->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
+               encode_tmap_2d(&mb, g->sh, 48, (uint64_t)g->n, 192, 16, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_64B);
+    if (tma && want_gauss)
+        tma = ((uintptr_t)out->sh & 15u) == 0 &&
+              encode_tmap_2d(&ga, out->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
+              encode_tmap_2d(&gb, out->sh, 48, (uint64_t)g->n, 192, 16, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_64B);
+#define GS_PB(D, G, T)                                                                                             \
+    k_project_bwd<D, G, T><<<nblk, PB_THREADS, dyn, st>>>(                                                         \
+        L, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, viewmats, intr, p, g2, out->means,        \
+        out->log_scales, out->quats, out->opacity_logits, out->sh, out->pose_partials, ma, mb, ga, gb, status)
     if (want_gauss) {
         switch (deg) {
-        case 0: GS_PB(0, true); break;
-        case 1: GS_PB(1, true); break;
-        case 2: GS_PB(2, true); break;
-        case 3: GS_PB(3, true); break;
+        case 0: GS_PB(0, true, false); break;
+        case 1: GS_PB(1, true, false); break;
+        case 2: GS_PB(2, true, false); break;
+        case 3: if (tma) GS_PB(3, true, true); else GS_PB(3, true, false); break;
         default: return GS_ERR_UNSUPPORTED;
         }
     } else {
         switch (deg) {
-        case 0: GS_PB(0, false); break;
-        case 1: GS_PB(1, false); break;
-        case 2: GS_PB(2, false); break;
-        case 3: GS_PB(3, false); break;
+        case 0: GS_PB(0, false, false); break;
+        case 1: GS_PB(1, false, false); break;
+        case 2: GS_PB(2, false, false); break;
+        case 3: if (tma) GS_PB(3, false, true); else GS_PB(3, false, false); break;
         default: return GS_ERR_UNSUPPORTED;
         }
     }

@@ -21,8 +21,9 @@
 //   S_i = sum_{j>i} c_j alpha_j T_j + T_final bg = image - sum_{j<=i} c_j alpha_j T_j,
 // so that dL/dalpha_i = T_i (c_i . g) - (S_i . g) / (1 - alpha_i).
 // Per-Gaussian gradients (mean2D, 2D covariance, opacity, colour) are summed over a
-// warp with a 12-shuffle reduce-scatter, over the block in shared memory, and
-// added to the per-slot grad2d record with one vector atomic per float4.
+// warp through a shared-memory transpose (each of 27 lanes adds one value over
+// a third of the warp), over the block in shared memory, and added to the
+// per-slot grad2d record with one vector atomic per float4.
 // Both kernels run a thread's two pixels through packed float2 arithmetic
 // (f32x2 fma/mul/add, one instruction for both), branch-free: a pixel that
 // does not composite a Gaussian contributes zeros.
@@ -152,42 +153,6 @@ __device__ __forceinline__ unsigned int warp_mask(const float4 &xy, const float4
     return m;
 }
 
-// Sum 9 per-lane values over the warp by recursive halving (a reduce-scatter):
-// each exchange keeps one part of the current values and sends the other,
-// splitting 9+1 -> 5, 5+1 -> 3, 3+1 -> 2, 2 -> 1 over lane bits 16, 8, 4, 2
-// (one zero pad where the count is odd), and the last exchange over bit 0
-// completes the 32-lane sum. Lane l then holds the sum of value
-// idx(l) = 5 [l&16] + 3 [l&8] + q(l), q(l) = 2 [l&4] + [l&2]; the value is
-// real (not a pad) for q <= 2, 3 [l&8] + q <= 4 and idx <= 8. 12 shuffles
-// instead of 5 per value.
-__device__ __forceinline__ float warp_reduce_scatter9(float (&v)[9], int lane) {
-    const unsigned int F = 0xffffffffu;
-    bool up = (lane & 16) != 0;
-    float a[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const float hi = k + 5 < 9 ? v[k + 5] : 0.f;
-        a[k] = (up ? hi : v[k]) + __shfl_xor_sync(F, up ? v[k] : hi, 16);
-    }
-    up = (lane & 8) != 0;
-    float b[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float hi = k + 3 < 5 ? a[k + 3] : 0.f;
-        b[k] = (up ? hi : a[k]) + __shfl_xor_sync(F, up ? a[k] : hi, 8);
-    }
-    up = (lane & 4) != 0;
-    float c[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float hi = k + 2 < 3 ? b[k + 2] : 0.f;
-        c[k] = (up ? hi : b[k]) + __shfl_xor_sync(F, up ? b[k] : hi, 4);
-    }
-    up = (lane & 2) != 0;
-    const float d = (up ? c[1] : c[0]) + __shfl_xor_sync(F, up ? c[0] : c[1], 2);
-    return d + __shfl_xor_sync(F, d, 1);
-}
-
 // add a thread's pair counts to the 64-bit counters at counters + at (one atomic per warp)
 __device__ __forceinline__ void count_pairs(int *counters, int at, unsigned int n_eval, unsigned int n_comp) {
 #pragma unroll
@@ -265,8 +230,7 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
                     const float2 u = __ffma2_rn(f2(con.y), dy, f2(dx));
                     const float2 p2 = __ffma2_rn(f2(con.x), __fmul2_rn(u, u), __fmul2_rn(f2(con.z), __fmul2_rn(dy, dy)));
                     const float2 oG = __fmul2_rn(f2(con.w), make_float2(ex2_approx(p2.x), ex2_approx(p2.y)));
-                    const float a0 = oG.x > L.alpha_max ? L.alpha_max : oG.x;
-                    const float a1 = oG.y > L.alpha_max ? L.alpha_max : oG.y;
+                    const float a0 = fminf(oG.x, L.alpha_max), a1 = fminf(oG.y, L.alpha_max);
                     const bool ok0 = col && !done0 && fabsf(dy.x) <= xy.w && a0 >= L.alpha_min;
                     const bool ok1 = col && !done1 && fabsf(dy.y) <= xy.w && a1 >= L.alpha_min;
                     if (!__any_sync(0xffffffffu, ok0 || ok1)) continue;
@@ -317,14 +281,16 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
     __shared__ float2 s_ad[NB];    // per staged Gaussian: the conic's A and D (natural-log units)
     __shared__ unsigned int s_mask[NB];
     __shared__ float s_g[NB][9];   // per staged Gaussian: summed gradient (odd stride: no bank conflicts)
+    __shared__ float s_red[BS / 32][32 * 9];   // per warp: the lanes' 9 values, pitch 9
     __shared__ int s_item;
     if (counters[CNT_ABORT]) return;
     const int lane = threadIdx.x & 31;
     const unsigned int wbit = 1u << (threadIdx.x >> 5);
-    const int red_q = ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
-    const int red_p = ((lane & 8) ? 3 : 0) + red_q;
-    const int red_idx = ((lane & 16) ? 5 : 0) + red_p;
-    const bool red_own = !(lane & 1) && red_q <= 2 && red_p <= 4 && red_idx <= 8;   // lanes holding a real sum
+    float *rb = s_red[threadIdx.x >> 5];
+    // the warp sum of value j: lane 9p + j (p < 3) adds lanes p, p + 3, ...,
+    // then lanes j + 9 and j + 18 hand their parts to lane j (the pitch-9 rows
+    // put the 27 reading lanes on 27 different banks at every step)
+    const int red_j = lane % 9, red_p = lane / 9;
     for (int k = threadIdx.x; k < NB; k += BS)
         for (int c = 0; c < 9; ++c) s_g[k][c] = 0.f;
     for (;;) {
@@ -436,8 +402,19 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
                         // gradient of this thread's pixels w.r.t. (x, y, a, b, c, o, r, g, b)
                         float gv[9] = {g0.x + g0.y, g1.x + g1.y, g2.x + g2.y, g3.x + g3.y, g4.x + g4.y,
                                        g5.x + g5.y, g6.x + g6.y, g7.x + g7.y, g8.x + g8.y};
-                        const float sum = warp_reduce_scatter9(gv, lane);
-                        if (red_own) atomicAdd(&s_g[k][red_idx], sum);
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) rb[lane * 9 + c] = gv[c];
+                        __syncwarp();
+                        float acc = 0.f;
+                        if (lane < 27) {
+#pragma unroll
+                            for (int i = 0; i < 11; ++i)
+                                if (red_p + 3 * i < 32) acc += rb[(red_p + 3 * i) * 9 + red_j];
+                        }
+                        const float t1 = __shfl_sync(0xffffffffu, acc, (lane + 9) & 31);
+                        const float t2 = __shfl_sync(0xffffffffu, acc, (lane + 18) & 31);
+                        if (lane < 9) atomicAdd(&s_g[k][lane], acc + t1 + t2);
+                        __syncwarp();   // the buffer is free for the next Gaussian
                     }
                 }
             }

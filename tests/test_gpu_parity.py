@@ -330,6 +330,38 @@ def test_backward_parity(case):
     check_grad(dtw.cpu().numpy(), tw, "twist")
 
 
+@pytest.mark.parametrize("case", ["clustered_sh3", "orbit_4views", "uneven_3scenes"])
+def test_projection_backward_staged_path_equals_per_thread_path(case, monkeypatch):
+    """The degree-3 projection backward stages SH rows in and SH gradients
+    out with tensor copies for full blocks; partial blocks and the fallback
+    go per thread. Same arithmetic in the same order: the raw-parameter
+    gradients and the pose partials agree bit for bit."""
+    sc, vw = CASES[case]()
+    rast, g, views, image, proj = gpu_forward(sc, vw)
+    up = torch.randn(views.num_image_floats(), device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    cfg = rast.cfg
+    n_slots = int(np.sum(vw.gauss_count))
+    # one set of 2D gradients for both (their float atomics make repeated
+    # raster backward runs differ in the last bits)
+    grad2d = torch.empty(max(1, n_slots), _lib.GS_GRAD2D_FLOATS, device="cuda")
+    status = _lib.new_status()
+    _lib.gs_rasterize_bwd(views, cfg, proj, rast.bins, image, up, grad2d, status)
+    outs = []
+    for no_tma in ("0", "1"):
+        monkeypatch.setenv("GS_DISABLE_TMA", no_tma)
+        gr = _lib.Grads(g.n, g.sh_degree, n_slots, vw.n)
+        gr.grad2d = grad2d
+        for t in (gr.means, gr.log_scales, gr.quats, gr.opacity_logits, gr.sh, gr.pose_partials):
+            t.fill_(float("nan"))
+        _lib.gs_project_bwd(g, views, cfg, proj, gr, True, status)
+        torch.cuda.synchronize()
+        assert int(status[0].item()) == 0
+        outs.append([t.cpu().numpy() for t in (gr.means, gr.log_scales, gr.quats, gr.opacity_logits, gr.sh,
+                                               gr.pose_partials)])
+    for a, b in zip(*outs):
+        assert not np.isnan(a).any() and np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
 def test_pose_only_backward_matches_full():
     sc, vw = CASES["orbit_4views"]()
     rast, g, views, image, proj = gpu_forward(sc, vw)
