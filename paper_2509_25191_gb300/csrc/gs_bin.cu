@@ -98,11 +98,18 @@ __device__ __forceinline__ long long segment_end(const Launch &L, int v, long lo
     return e < c1 ? e : c1;
 }
 
+// With a reservation table (table != nullptr), the block also keeps the
+// value each (block, tile) atomic returned: the start of the block's range
+// inside the tile, relative to the tile's first instance. The scatter then
+// places its instances without counting again. Row blockIdx.x of the table
+// holds the on-chip segments of the block's chunk one after another.
 __global__ void __launch_bounds__(BIN_THREADS) k_bin_count(const Launch L, const float4 *__restrict__ proj,
-                                                           int *__restrict__ tile_count, int smem_tiles) {
+                                                           int *__restrict__ tile_count, int smem_tiles,
+                                                           int *__restrict__ table, int table_row) {
     extern __shared__ int s_cnt[];
     const long long c0 = (long long)blockIdx.x * BIN_CHUNK;
     const long long c1 = c0 + BIN_CHUNK < L.n_slots ? c0 + BIN_CHUNK : L.n_slots;
+    int *trow = table ? table + (long long)blockIdx.x * table_row : nullptr;
     for (long long seg = c0; seg < c1;) {
         const int v = view_of_slot(L, seg);
         const long long seg_end = segment_end(L, v, c1);
@@ -126,8 +133,12 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_count(const Launch L, const
             __syncthreads();
             for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) {
                 const int c = s_cnt[t];
-                if (c) atomicAdd(tile_count + vd.tile_base + t, c);
+                if (c) {
+                    const int at = atomicAdd(tile_count + vd.tile_base + t, c);
+                    if (trow) trow[t] = at;
+                }
             }
+            if (trow) trow += Tv;
             __syncthreads();
         }
         seg = seg_end;
@@ -223,24 +234,33 @@ __global__ void __launch_bounds__(1024) k_bin_scan(const Launch L, long long cap
     }
 }
 
-// Same chunking as k_bin_count: each block reserves one contiguous range per
-// (block, tile) with a single global atomic, then places its instances inside
-// the range with shared-memory atomics.
+// Same chunking as k_bin_count: each block owns one contiguous range per
+// (block, tile), taken from the count kernel's reservation table or (without
+// one) reserved here by counting again and one global atomic per (block,
+// tile); it places its instances inside the range with shared-memory atomics.
 __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, const float4 *__restrict__ proj,
                                                              int *__restrict__ cursor,
                                                              unsigned long long *__restrict__ keys,
-                                                             const int *__restrict__ counters, int smem_tiles) {
+                                                             const int *__restrict__ counters, int smem_tiles,
+                                                             const int *__restrict__ table, int table_row) {
     extern __shared__ int s_cnt[];
     if (counters[CNT_ABORT]) return;
     const long long c0 = (long long)blockIdx.x * BIN_CHUNK;
     const long long c1 = c0 + BIN_CHUNK < L.n_slots ? c0 + BIN_CHUNK : L.n_slots;
+    const int *trow = table ? table + (long long)blockIdx.x * table_row : nullptr;
     for (long long seg = c0; seg < c1;) {
         const int v = view_of_slot(L, seg);
         const long long seg_end = segment_end(L, v, c1);
         const ViewDesc &vd = L.v[v];
         const int Tv = vd.Gx * vd.Gy;
         const bool on_chip = Tv <= smem_tiles;
-        if (on_chip) {
+        if (on_chip && trow) {
+            // the block's range in each tile, reserved by the count kernel
+            // (entries of tiles the block does not touch are never read back)
+            for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) s_cnt[t] = cursor[vd.tile_base + t] + trow[t];
+            trow += Tv;
+            __syncthreads();
+        } else if (on_chip) {
             for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) s_cnt[t] = 0;
             __syncthreads();
             for (long long pb = seg; pb < seg_end; pb += BIN_THREADS) {
@@ -577,13 +597,33 @@ int launch_bin_sort(const Launch &L, const float *proj, const gs_bins *b, int32_
     for (int v = 0; v < L.n_views; ++v) smem_tiles = max(smem_tiles, L.v[v].Gx * L.v[v].Gy);
     smem_tiles = min(smem_tiles, BIN_SMEM_TILES);
     const size_t bin_smem = sizeof(int) * (size_t)max(smem_tiles, 1);
-    if (nb > 0) k_bin_count<<<nb, BIN_THREADS, bin_smem, st>>>(L, p, b->tile_scratch, smem_tiles);
+    // reservation table in keys_tmp (free until the sort): one row per block
+    // covering the on-chip view segments of its chunk, if it fits
+    long long row = 0;
+    for (int v = 0; v < L.n_views; ++v) {
+        // the chunk that holds the view's first slot may also hold the ends
+        // of earlier views and the starts of later ones
+        const long long c0 = (L.v[v].slot_base / BIN_CHUNK) * BIN_CHUNK, c1 = c0 + BIN_CHUNK;
+        long long sum = 0;
+        for (int u = 0; u < L.n_views; ++u) {
+            const long long u0 = L.v[u].slot_base, u1 = u0 + L.v[u].g_count;
+            const int Tu = L.v[u].Gx * L.v[u].Gy;
+            if (u1 > c0 && u0 < c1 && Tu <= smem_tiles) sum += Tu;
+        }
+        row = max(row, sum);
+    }
+    int *table = nullptr;
+    if (nb > 0 && row > 0 && row < 0x7fffffffLL && (unsigned long long)nb * (unsigned long long)row * 4ULL <=
+                                                    (unsigned long long)b->capacity * 8ULL)
+        table = reinterpret_cast<int *>(b->keys_tmp);
+    const int table_row = table ? (int)row : 0;
+    if (nb > 0) k_bin_count<<<nb, BIN_THREADS, bin_smem, st>>>(L, p, b->tile_scratch, smem_tiles, table, table_row);
     k_bin_scan<<<1, 1024, 0, st>>>(L, b->capacity, b->tile_scratch, reinterpret_cast<int2 *>(b->tile_ranges),
                                    b->tile_order, b->counters, status);
     if (nb > 0)
         k_bin_scatter<<<nb, BIN_THREADS, bin_smem, st>>>(L, p, b->tile_scratch,
                                                          reinterpret_cast<unsigned long long *>(b->keys), b->counters,
-                                                         smem_tiles);
+                                                         smem_tiles, table, table_row);
     static int sort_blocks = 0;
     const int smem = (int)sizeof(SortSmem);
     if (!sort_blocks) {
