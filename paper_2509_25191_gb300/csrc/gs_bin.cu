@@ -35,12 +35,16 @@ constexpr int BIN_SMEM_TILES = 12288;   // at most 48 KB of int counters, sized 
 
 // The first float4 of a record holds everything binning needs (one sector);
 // culled records are all zero, valid ones have positive extents.
-__device__ __forceinline__ bool slot_rect(const Launch &L, const float4 *__restrict__ proj, long long p,
-                                          const ViewDesc &vd, int &x0, int &x1, int &y0, int &y1) {
-    const float4 r0 = proj[4 * p];
+__device__ __forceinline__ bool slot_rect(const Launch &L, const float4 &r0, const ViewDesc &vd, int &x0, int &x1,
+                                          int &y0, int &y1) {
     if (!(r0.z > 0.f)) return false;
     tile_rect(r0.x, r0.y, r0.z, r0.w, 1.f / (float)L.tw, 1.f / (float)L.th, vd.Gx, vd.Gy, x0, x1, y0, y1);
     return true;
+}
+
+// a slot's binning record (zeros past the segment end)
+__device__ __forceinline__ float4 slot_head(const float4 *__restrict__ proj, long long p, long long end) {
+    return p < end ? proj[4 * p] : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Warp-cooperative walk over the tiles of the 32 lanes' rectangles: the
@@ -120,10 +124,14 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_count(const Launch L, const
             for (int t = threadIdx.x; t < Tv; t += BIN_THREADS) s_cnt[t] = 0;
             __syncthreads();
         }
-        for (long long pb = seg; pb < seg_end; pb += BIN_THREADS) {   // uniform trip count: whole warps walk
-            const long long p = pb + threadIdx.x;
+        // uniform trip count: whole warps walk; the next slot's record is
+        // loaded while the current one's tiles are walked
+        float4 rec = slot_head(proj, seg + threadIdx.x, seg_end);
+        for (long long pb = seg; pb < seg_end; pb += BIN_THREADS) {
+            const float4 cur = rec;
+            rec = slot_head(proj, pb + BIN_THREADS + threadIdx.x, seg_end);
             int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-            const bool valid = p < seg_end && slot_rect(L, proj, p, vd, x0, x1, y0, y1);
+            const bool valid = slot_rect(L, cur, vd, x0, x1, y0, y1);
             warp_rect_walk(valid, x0, x1, y0, y1, vd.Gx, 0u, 0u, [&](int t, unsigned int, unsigned int) {
                 if (on_chip) atomicAdd(s_cnt + t, 1);
                 else atomicAdd(tile_count + vd.tile_base + t, 1);
@@ -266,7 +274,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, con
             for (long long pb = seg; pb < seg_end; pb += BIN_THREADS) {
                 const long long p = pb + threadIdx.x;
                 int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-                const bool valid = p < seg_end && slot_rect(L, proj, p, vd, x0, x1, y0, y1);
+                const bool valid = slot_rect(L, slot_head(proj, p, seg_end), vd, x0, x1, y0, y1);
                 warp_rect_walk(valid, x0, x1, y0, y1, vd.Gx, 0u, 0u,
                                [&](int t, unsigned int, unsigned int) { atomicAdd(s_cnt + t, 1); });
             }
@@ -277,11 +285,20 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const Launch L, con
             }
             __syncthreads();
         }
+        // the next slot's record and depth are loaded while the current
+        // one's instances are written
+        float4 rec = slot_head(proj, seg + threadIdx.x, seg_end);
+        float dep = seg + threadIdx.x < seg_end ? proj[4 * (seg + threadIdx.x) + 3].z : 0.f;
         for (long long pb = seg; pb < seg_end; pb += BIN_THREADS) {
             const long long p = pb + threadIdx.x;
+            const float4 cur = rec;
+            const float cdep = dep;
+            const long long pn = p + BIN_THREADS;
+            rec = slot_head(proj, pn, seg_end);
+            dep = pn < seg_end ? proj[4 * pn + 3].z : 0.f;
             int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-            const bool valid = p < seg_end && slot_rect(L, proj, p, vd, x0, x1, y0, y1);
-            const unsigned int dbits = valid ? __float_as_uint(proj[4 * p + 3].z) : 0u;
+            const bool valid = slot_rect(L, cur, vd, x0, x1, y0, y1);
+            const unsigned int dbits = valid ? __float_as_uint(cdep) : 0u;
             const unsigned int pl = (unsigned int)p;
             // payload: the owner's key = (depth bits << 32) | slot
             warp_rect_walk(valid, x0, x1, y0, y1, vd.Gx, dbits, pl, [&](int t, unsigned int hi, unsigned int lo) {
