@@ -36,6 +36,7 @@ struct PbStage {
     float4 shB[PB_THREADS * 4];
     float4 gA[PB_THREADS * 8];
     float4 gB[PB_THREADS * 4];
+    float4 g2d[PB_THREADS * 3];   // the first view's 2D-gradient rows (48-byte rows: conflict-free)
     unsigned long long bar;
 };
 
@@ -48,7 +49,8 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
     float *__restrict__ g_quats, float *__restrict__ g_logits, float *__restrict__ g_sh,
     float *__restrict__ pose_partials, const __grid_constant__ CUtensorMap tm_shA,
     const __grid_constant__ CUtensorMap tm_shB, const __grid_constant__ CUtensorMap tm_gA,
-    const __grid_constant__ CUtensorMap tm_gB, int *__restrict__ status) {
+    const __grid_constant__ CUtensorMap tm_gB, const __grid_constant__ CUtensorMap tm_g2d,
+    int *__restrict__ status) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int GP = 3 * K + 1;   // odd row pitch: conflict-free column access
     static_assert(!TMA || DEG == 3, "the staged path is for 48-float SH rows");
@@ -80,22 +82,25 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
         // a block iteration is "full" when its 128 threads are Gaussians of one
         // scene: its SH rows (and gradient rows) are then contiguous boxes
         bool full = false;
-        int row0 = 0;
+        int row0 = 0, v_first = -1;
         if constexpr (TMA) {
             const long long last = base + PB_THREADS - 1;
             if (last < L.n_threads) {
                 const int s0 = scene_of_thread(L, base);
                 full = scene_of_thread(L, last) == s0 && (smem_u32(S[0].shA) & 1023u) == 0;
                 row0 = (int)(L.s[s0].g_begin + base - L.s[s0].thread_base);
+                v_first = L.s[s0].v_begin;
             }
             if (threadIdx.x == 0) {
                 // the previous iteration's gradient stores have read the staging
                 if (GAUSS) bulk_wait_read_all();
                 if (full) {
                     fence_async_smem();
-                    mbar_expect_tx(&S[0].bar, PB_THREADS * 48 * 4);
+                    mbar_expect_tx(&S[0].bar, PB_THREADS * (48 + 12) * 4);
                     tma_load_2d(S[0].shA, &tm_shA, 0, row0, &S[0].bar);
                     tma_load_2d(S[0].shB, &tm_shB, 32, row0, &S[0].bar);
+                    const int srow = (int)(L.v[v_first].slot_base + base - L.s[scene_of_thread(L, base)].thread_base);
+                    tma_load_2d(S[0].g2d, &tm_g2d, 0, srow, &S[0].bar);
                 }
             }
             __syncthreads();
@@ -178,7 +183,10 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
             bool contrib = false;
             if (v >= vb && v < ve) {
                 const long long slot = L.v[v].slot_base + li;
-                const float4 ga4 = grad2d[3 * slot], gb4 = grad2d[3 * slot + 1], gc4 = grad2d[3 * slot + 2];
+                const bool staged = TMA && full && v == v_first;
+                const float4 ga4 = staged ? S[0].g2d[3 * r] : grad2d[3 * slot];
+                const float4 gb4 = staged ? S[0].g2d[3 * r + 1] : grad2d[3 * slot + 1];
+                const float4 gc4 = staged ? S[0].g2d[3 * r + 2] : grad2d[3 * slot + 2];
                 contrib = ga4.x != 0.f || ga4.y != 0.f || ga4.z != 0.f || ga4.w != 0.f || gb4.x != 0.f ||
                           gb4.y != 0.f || gb4.z != 0.f || gb4.w != 0.f || gc4.x != 0.f;
                 if (contrib) {
@@ -458,8 +466,9 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
     const float4 *p = reinterpret_cast<const float4 *>(proj);
     const float4 *g2 = reinterpret_cast<const float4 *>(grad2d);
     const size_t dyn = (size_t)PB_WARPS * L.n_views * 12 * sizeof(float);
-    CUtensorMap ma, mb, ga, gb;
+    CUtensorMap ma, mb, ga, gb, m2;
     memset(&ma, 0, sizeof ma); memset(&mb, 0, sizeof mb); memset(&ga, 0, sizeof ga); memset(&gb, 0, sizeof gb);
+    memset(&m2, 0, sizeof m2);
     // degree 3 with 16-byte aligned SH rows and gradient rows: the staged
     // path, unless the environment sets GS_DISABLE_TMA=1. The pose-only
     // backward reads SH rows only for Gaussians with a nonzero 2D gradient,
@@ -470,6 +479,9 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
                g->n < 0x7fffffffLL &&
                encode_tmap_2d(&ma, g->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
                encode_tmap_2d(&mb, g->sh, 48, (uint64_t)g->n, 192, 16, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_64B);
+    if (tma)
+        tma = L.n_slots < 0x7fffffffLL &&
+              encode_tmap_2d(&m2, grad2d, 12, (uint64_t)L.n_slots, 48, 12, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_NONE);
     if (tma && want_gauss)
         tma = ((uintptr_t)out->sh & 15u) == 0 &&
               encode_tmap_2d(&ga, out->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
@@ -477,7 +489,7 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
 #define GS_PB(D, G, T)                                                                                             \
     k_project_bwd<D, G, T><<<nblk, PB_THREADS, dyn, st>>>(                                                         \
         L, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, viewmats, intr, p, g2, out->means,        \
-        out->log_scales, out->quats, out->opacity_logits, out->sh, out->pose_partials, ma, mb, ga, gb, status)
+        out->log_scales, out->quats, out->opacity_logits, out->sh, out->pose_partials, ma, mb, ga, gb, m2, status)
     if (want_gauss) {
         switch (deg) {
         case 0: GS_PB(0, true, false); break;

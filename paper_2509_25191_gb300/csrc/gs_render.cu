@@ -241,8 +241,11 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
                     const bool cp0 = ok0 && !st0, cp1 = ok1 && !st1;
                     done0 = done0 || st0;
                     done1 = done1 || st1;
-                    const float2 w = __fmul2_rn(make_float2(cp0 ? a0 : 0.f, cp1 ? a1 : 0.f), T);
-                    T = make_float2(cp0 ? Tn.x : T.x, cp1 ? Tn.y : T.y);
+                    // weight and transmittance through a 0/1 mask (T (1 - alpha M) is
+                    // T (1 - alpha) bit for bit when M = 1, T when M = 0)
+                    const float2 Mcp = make_float2(cp0 ? 1.f : 0.f, cp1 ? 1.f : 0.f);
+                    const float2 w = __fmul2_rn(__fmul2_rn(make_float2(a0, a1), Mcp), T);
+                    T = __fmul2_rn(T, __ffma2_rn(make_float2(-a0, -a1), Mcp, f2(1.f)));
                     const float4 c = s_rgb[k];
                     CR = __ffma2_rn(f2(c.x), w, CR);
                     CG = __ffma2_rn(f2(c.y), w, CG);
