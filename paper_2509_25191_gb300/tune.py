@@ -58,8 +58,9 @@ def autotune(g: Gaussians, views: Views, target, candidates=CANDIDATES, reps=10,
         return a.elapsed_time(b) / n
 
     # round 1: every candidate once; round 2: the two fastest, re-timed in
-    # alternation (best of three) so that clock ramp-up and the order of the
-    # candidates do not decide between near-equal shapes
+    # alternation (median of three) so that clock ramp-up, the order of the
+    # candidates and a single outlying measurement do not decide between
+    # near-equal shapes
     times = {}
     for tile in candidates:
         step = GraphStep(g, views, target, tile=tile)
@@ -79,9 +80,12 @@ def autotune(g: Gaussians, views: Views, target, candidates=CANDIDATES, reps=10,
             for _ in range(3):
                 st.replay()
         torch.cuda.synchronize()
+        again = {t: [] for t in finalists}
         for _ in range(3):
             for t, st in steps.items():
-                times[t] = min(times[t], time_step(st, 2 * reps))
+                again[t].append(time_step(st, 2 * reps))
+        for t in finalists:
+            times[t] = sorted(again[t])[1]
         del steps
         torch.cuda.empty_cache()
     best = min(times, key=times.get)
