@@ -167,15 +167,15 @@ __device__ __forceinline__ void count_pairs(int *counters, int at, unsigned int 
     }
 }
 
-// Stage instances [b0, min(b0 + 2 BS, end)) of a tile: two per thread.
-template <int TW, int TH>
+// Stage instances [b0, min(b0 + PER BS, end)) of a tile: PER per thread.
+template <int TW, int TH, int PER>
 __device__ __forceinline__ void stage_batch(const Launch &L, const float4 *__restrict__ proj,
                                             const unsigned int *__restrict__ ids, int b0, int end,
                                             const TileInfo &ti, float4 *s_xy, float4 *s_con, float4 *s_rgb,
                                             unsigned int *s_mask) {
     constexpr int BS = TW * TH / 2;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < PER; ++h) {
         const int k = threadIdx.x + h * BS;
         if (b0 + k < end) {
             stage(proj, ids[b0 + k], ti.ox, ti.oy, s_xy[k], s_con[k], s_rgb[k]);
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
         const float2 PCY = make_float2(ti.pcy0, ti.pcy0 + 4.f);
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
             if (__syncthreads_count(done0 && done1) == BS) break;
-            stage_batch<TW, TH>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
+            stage_batch<TW, TH, 2>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
             __syncthreads();
             const int nb = min(NB, r.y - b0);
             // the warp walks only the staged Gaussians that may reach its patch:
@@ -279,7 +279,9 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
                                                             const float *__restrict__ image,
                                                             const float *__restrict__ dL_dimage,
                                                             float4 *__restrict__ grad2d) {
-    constexpr int BS = TW * TH / 2, NB = TW * TH;
+    // one staged Gaussian per thread and batch: the smaller shared-memory
+    // footprint (17 KB) lets 9 blocks share an SM
+    constexpr int BS = TW * TH / 2, NB = BS;
     __shared__ float4 s_xy[NB], s_con[NB], s_rgb[NB];
     __shared__ float2 s_ad[NB];    // per staged Gaussian: the conic's A and D (natural-log units)
     __shared__ unsigned int s_mask[NB];
@@ -331,9 +333,9 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
         unsigned int n_eval = 0, n_comp = 0;
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
             if (__syncthreads_count(done0 && done1) == BS) break;
-            stage_batch<TW, TH>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
+            stage_batch<TW, TH, 1>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < 1; ++h) {
                 const int k = threadIdx.x + h * BS;
                 if (b0 + k < r.y)
                     s_ad[k] = make_float2(s_con[k].x * (-2.f * LN2), s_con[k].z * (-2.f * LN2));
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, c
             __syncthreads();
             // flush this batch's per-Gaussian sums
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < 1; ++h) {
                 const int k = threadIdx.x + h * BS;
                 if (k < nb) {
                     const float a0 = s_g[k][0], a1 = s_g[k][1], a2 = 0.5f * s_g[k][2], a3 = s_g[k][3];

@@ -212,6 +212,33 @@ def test_binning_bit_exact(case, tile):
         inst_base += len(ii)
 
 
+def test_binning_without_reservation_table_bit_exact():
+    """A sparse view on a large tile grid with an exact-size instance buffer:
+    the count kernel's reservation table (kept in keys_tmp) does not fit, so
+    the scatter counts again and reserves per (block, tile) itself. Same
+    bit-exact result."""
+    sc, _ = synth.single_view_small(seed=3, n=300)
+    vw = _eye_view(300, 1024, 1024, 150.0, 512.0, 512.0)
+    recs = _records_from_oracle(sc, vw)
+    ref, r = recs[0]
+    tile = (16, 16)
+    rr, kk, ii = O.bin_view(r[:, 0], r[:, 1], ref["radius"], r[:, 14], 1024, 1024, *tile, ext=r[:, 2:4])
+    n_inst = len(ii)
+    n_tiles = (1024 // 16) ** 2
+    assert 0 < n_inst and n_inst * 8 < n_tiles * 4   # the one-block table would need n_tiles ints
+    proj = torch.as_tensor(r).cuda()
+    views = _lib.Views.from_synth(vw)
+    cfg = _lib.config(tile=tile)
+    bins = _lib.Bins(views.num_tiles(cfg), n_inst)
+    status = _lib.new_status()
+    _lib.gs_bin_sort(views, cfg, proj, bins, status)
+    torch.cuda.synchronize()
+    assert status[0].item() == 0 and bins.counters[0].item() == n_inst
+    assert np.array_equal(bins.tile_ranges.cpu().numpy().reshape(-1, 2).astype(np.int64), rr)
+    assert np.array_equal(bins.ids.cpu().numpy().view(np.uint32).astype(np.int64), ii.astype(np.int64))
+    assert np.array_equal(bins.keys.cpu().numpy().view(np.uint64), kk)
+
+
 def test_binning_large_tiles_bit_exact():
     """Tiles of > 2047 and > 16384 instances take the large-tile sort and
     the merge path; the result must still equal the oracle's."""
