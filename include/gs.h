@@ -28,7 +28,13 @@
  *     enqueued; a failed launch returns GS_ERR_CUDA. Conditions found on the
  *     device (instance capacity exceeded) are written to the caller's DEVICE
  *     status word int32[4] = {code, detail_lo, detail_hi, 0}; the caller reads
- *     it at a point of its choosing. Kernels never trap and never spin.
+ *     it at a point of its choosing. Kernels never trap; the only waits
+ *     are the projection kernels' bounded waits for their own tensor copies
+ *     (GS_ERR_TIMEOUT if one runs out).
+ *   - The enqueued work also depends on the environment variable
+ *     GS_DISABLE_TMA, read at each call: "1" makes the projection kernels
+ *     read and write per thread instead of staging through tensor copies
+ *     (the same results, bit for bit; the tests compare the two).
  *   - float32 everywhere. Quaternions are (w,x,y,z). Cameras are
  *     world->camera rigid transforms with OpenCV axes (x right, y down,
  *     z forward); a pixel (u,v) has its centre at (u+0.5, v+0.5).
@@ -208,7 +214,11 @@ int gs_render_bwd(const gs_gaussians *g, const gs_views *views, const gs_config 
 /* The two stages of gs_render_bwd, callable separately (same arguments and
  * semantics as there). gs_rasterize_bwd zeroes grad2d [P,12] and adds the
  * per-slot 2D gradients (layout as gs_grads.grad2d); gs_project_bwd chains
- * grad2d to the raw parameters and the pose partials. */
+ * grad2d to the raw parameters and the pose partials. With degree-3 SH and
+ * want_gaussian_grads, gs_project_bwd stages each block's SH rows, first-view
+ * 2D-gradient rows and SH-gradient rows by tensor copies (grads->sh must then
+ * be 16-byte aligned, else the per-thread path runs); a bounded wait for one
+ * that runs out sets status = {GS_ERR_TIMEOUT, block}. */
 int gs_rasterize_bwd(const gs_views *views, const gs_config *cfg, const float *proj, const gs_bins *bins,
                      const float *image, const float *dL_dimage, float *grad2d, int32_t *status,
                      void *stream);
