@@ -33,6 +33,11 @@ CASES = {
     "orbit_4views": lambda: synth.orbit_views(0, 20000, 4, 200, 112, 1000.0 * 200 / 979.0),
     "uneven_3scenes": lambda: synth.uneven_scenes(seeds=(1, 2, 3), sizes=(3000, 6000, 9000), views_per_scene=2,
                                                   resolutions=((96, 64), (150, 90), (77, 131)), focal=150.0),
+    # the view sees Gaussians [37, 11939) of 12,000: the first 37 and last 61
+    # get zero gradients, and the staged projection blocks start mid-array
+    "subset_view": lambda: (synth.cluster_scene(4, 12000),
+                            synth._views(synth.look_at((0.0, 0.0, -6.0)), 1000.0 * 300 / 1237.0, 300, 200, 37,
+                                         12000 - 37 - 61)),
 }
 
 
@@ -135,7 +140,7 @@ def test_projection_parity(case):
         assert (ext >= rext * (1 - 1e-6)).all() and (ext <= rext * (1 + 2e-4) + 1e-5).all()
 
 
-@pytest.mark.parametrize("case", ["clustered_sh3", "orbit_4views", "uneven_3scenes"])
+@pytest.mark.parametrize("case", ["clustered_sh3", "orbit_4views", "uneven_3scenes", "subset_view"])
 def test_projection_staged_path_equals_per_thread_path(case, monkeypatch):
     """Degree 3 stages each full block's SH rows and records with tensor
     copies (swizzled boxes); blocks that straddle scenes, the tail block and
@@ -357,7 +362,7 @@ def test_backward_parity(case):
     check_grad(dtw.cpu().numpy(), tw, "twist")
 
 
-@pytest.mark.parametrize("case", ["clustered_sh3", "orbit_4views", "uneven_3scenes"])
+@pytest.mark.parametrize("case", ["clustered_sh3", "orbit_4views", "uneven_3scenes", "subset_view"])
 def test_projection_backward_staged_path_equals_per_thread_path(case, monkeypatch):
     """The degree-3 projection backward stages SH rows in and SH gradients
     out with tensor copies for full blocks; partial blocks and the fallback
