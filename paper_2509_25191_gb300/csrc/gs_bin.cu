@@ -371,6 +371,43 @@ __device__ __forceinline__ void scan_hist(SortSmem &S, int nwa) {
     __syncthreads();
 }
 
+constexpr int FIX_RUN = 32;   // longest run of equal compressed keys one thread orders alone
+static_assert(2 * (SORT_CAP / (FIX_RUN + 1)) + 1 <= 256 * (SORT_WARPS + 1), "the long-run list fits the histogram");
+
+// Order key[0..L), val[0..L) (shared memory) by (key, val) with the whole
+// block: a sorting network of ascending compare-exchanges over the next power
+// of two P >= L (each merge of two sorted halves starts with the mirrored
+// pairs i, size-1-i and continues with half-cleaners), so positions >= L act
+// as +infinity and are never touched.
+__device__ void block_sort_run(unsigned int *key, unsigned int *val, int L) {
+    int P = 1;
+    while (P < L) P <<= 1;
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < (P >> 1); t += SORT_THREADS) {
+                int i, j;
+                if (stride == (size >> 1)) {   // mirrored pairs of the two halves
+                    const int blk = t / stride, off = t % stride;
+                    i = blk * size + off;
+                    j = blk * size + size - 1 - off;
+                } else {
+                    const int blk = t / stride, off = t % stride;
+                    i = blk * 2 * stride + off;
+                    j = i + stride;
+                }
+                if (j < L) {
+                    const unsigned int ki = key[i], kj = key[j], vi = val[i], vj = val[j];
+                    if (ki > kj || (ki == kj && vi > vj)) {
+                        key[i] = kj; key[j] = ki;
+                        val[i] = vj; val[j] = vi;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // sort src[st .. st+n) (n <= SORT_CAP) by (depth, slot) into keys[st ..]
 // (src may be keys itself)
 __device__ void radix_sort_tile(SortSmem &S, const unsigned long long *src, unsigned long long *keys,
@@ -440,13 +477,26 @@ __device__ void radix_sort_tile(SortSmem &S, const unsigned long long *src, unsi
         __syncthreads();
         cur ^= 1;
     }
-    // runs of equal compressed key: insertion sort by (depth bits, slot)
+    // runs of equal compressed key: up to FIX_RUN keys are ordered by
+    // (depth bits, slot) by the thread that finds the run (insertion sort);
+    // a longer run (many equal or nearly equal depths) is recorded and then
+    // sorted by the whole block, so no thread sorts thousands of keys alone
+    // (the histogram is free after the passes and holds the list)
+    unsigned int *nlong = &S.hist[0][0], *lrun = &S.hist[0][1];
+    if (threadIdx.x == 0) *nlong = 0;
+    __syncthreads();
     for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
         const unsigned int c = (S.key[cur][i] - kmin) >> shift;
         if ((i == 0 || ((S.key[cur][i - 1] - kmin) >> shift) != c) && i + 1 < n &&
             ((S.key[cur][i + 1] - kmin) >> shift) == c) {
             int e = i + 1;
             while (e < n && ((S.key[cur][e] - kmin) >> shift) == c) ++e;
+            if (e - i > FIX_RUN) {
+                const unsigned int q = atomicAdd(nlong, 1u);   // at most n / (FIX_RUN + 1) runs
+                lrun[2 * q] = (unsigned int)i;
+                lrun[2 * q + 1] = (unsigned int)(e - i);
+                continue;
+            }
             for (int a = i + 1; a < e; ++a) {
                 const unsigned int ka = S.key[cur][a], va = S.val[cur][a];
                 int b = a - 1;
@@ -460,6 +510,10 @@ __device__ void radix_sort_tile(SortSmem &S, const unsigned long long *src, unsi
             }
         }
     }
+    __syncthreads();
+    const unsigned int n_long = *nlong;
+    for (unsigned int q = 0; q < n_long; ++q)
+        block_sort_run(S.key[cur] + lrun[2 * q], S.val[cur] + lrun[2 * q], (int)lrun[2 * q + 1]);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
         const unsigned int v = S.val[cur][i];
