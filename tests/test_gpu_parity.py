@@ -273,7 +273,7 @@ def test_binning_equal_depths_bit_exact(n):
     assert np.array_equal(bins.ids.cpu().numpy().view(np.uint32).astype(np.int64), ii.astype(np.int64))
     assert np.array_equal(bins.keys.cpu().numpy().view(np.uint64), kk)
     print(f"equal depths: {len(ii)} instances, largest tile {counts.max()}, bin+sort {dt * 1e3:.2f} ms")
-    assert dt < 2.0   # a sanity bound (one thread sorting a whole tile alone took tens of ms)
+    assert dt < 2.0   # a sanity bound only
 
 
 def test_binning_large_tiles_bit_exact():
