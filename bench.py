@@ -535,7 +535,9 @@ def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
         return vm
 
     vm = load(0)
-    step = GraphStep(g, views, tgt_static)
+    from paper_2509_25191_gb300.tune import autotune
+    tile, _ = autotune(g, views, tgt_static, reps=3)
+    step = GraphStep(g, views, tgt_static, tile=tile)
     # Eq. 1 update state: Adam moments per group, a pool of exploration noise
     gp = [g.means, g.log_scales, g.quats, g.opacity_logits, g.sh]
     gg = [step.grads.means, step.grads.log_scales, step.grads.quats, step.grads.opacity_logits, step.grads.sh]
@@ -593,7 +595,7 @@ def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
             "ms_per_step": round(ms, 3), "mpix_s": round(px / ms / 1e3, 2), "pixels_per_step": px,
             "sgld_adam_update": opt,
             "pose_grad_norm_last_step": round(last["pose_grad_norm"], 6),
-            "instances": int(step.bins.counters[0].item())}
+            "tile": list(tile), "instances": int(step.bins.counters[0].item())}
 
 
 def _rel_rot_err_deg(vm_a, vm_b, pairs):

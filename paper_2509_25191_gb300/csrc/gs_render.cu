@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
 }
 
 template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(TW * TH / 2, 8) k_render_bwd(const Launch L, const float4 *__restrict__ proj,
+__global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bwd(const Launch L, const float4 *__restrict__ proj,
                                                             const int2 *__restrict__ ranges,
                                                             const unsigned int *__restrict__ ids,
                                                             const int *__restrict__ order, int *__restrict__ counters,
