@@ -67,7 +67,7 @@ typedef enum gs_status {
 
 /* Rasterizer settings. gs_config_default() fills the defaults in brackets. */
 typedef struct gs_config {
-    int tile_w, tile_h;   /* tile in pixels [16,16]; supported: 16x16, 8x8, 16x8, 32x8, 32x16 */
+    int tile_w, tile_h;   /* tile in pixels [16,16]; supported: 16x16, 8x8, 16x8, 32x8, 32x16, 32x32 */
     int pixel_gate;       /* [1] evaluate a Gaussian at a pixel only if |dx|,|dy| <= radius
                              (the only supported value: it makes images tile-size invariant) */
     float near_z;         /* [0.2] cull if camera-space z <= near_z */

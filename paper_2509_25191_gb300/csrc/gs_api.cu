@@ -87,7 +87,7 @@ bool encode_tmap_2d(CUtensorMap *map, const void *base, uint64_t inner, uint64_t
 
 static bool tile_supported(int tw, int th) {
     return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 16 && th == 8) || (tw == 32 && th == 8) ||
-           (tw == 32 && th == 16);
+           (tw == 32 && th == 16) || (tw == 32 && th == 32);
 }
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }

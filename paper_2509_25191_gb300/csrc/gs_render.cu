@@ -499,6 +499,7 @@ int launch_render_fwd(const Launch &L, const float *proj, const gs_bins *b, floa
     if (L.tw == 16 && L.th == 8) return GS_CALL_FWD(16, 8);
     if (L.tw == 32 && L.th == 8) return GS_CALL_FWD(32, 8);
     if (L.tw == 32 && L.th == 16) return GS_CALL_FWD(32, 16);
+    if (L.tw == 32 && L.th == 32) return GS_CALL_FWD(32, 32);
     return GS_ERR_UNSUPPORTED;
 #undef GS_CALL_FWD
 }
@@ -511,6 +512,7 @@ int launch_render_bwd(const Launch &L, const float *proj, const gs_bins *b, cons
     if (L.tw == 16 && L.th == 8) return GS_CALL_BWD(16, 8);
     if (L.tw == 32 && L.th == 8) return GS_CALL_BWD(32, 8);
     if (L.tw == 32 && L.th == 16) return GS_CALL_BWD(32, 16);
+    if (L.tw == 32 && L.th == 32) return GS_CALL_BWD(32, 32);
     return GS_ERR_UNSUPPORTED;
 #undef GS_CALL_BWD
 }

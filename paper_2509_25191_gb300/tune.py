@@ -21,7 +21,7 @@ import torch
 from ._lib import Gaussians, Views
 from .step import GraphStep
 
-CANDIDATES = ((16, 16), (32, 8), (16, 8), (8, 8), (32, 16))
+CANDIDATES = ((16, 16), (32, 8), (16, 8), (8, 8), (32, 16), (32, 32))
 
 
 def signature(g: Gaussians, views: Views) -> str:

@@ -362,7 +362,7 @@ def test_permutation_invariance_bit_exact():
 
 def test_tile_size_invariance_bit_exact():
     sc, vw = _reduced_c2(n=8000, W=170, H=90)
-    imgs = [gpu_forward(sc, vw, tile=t)[3].cpu().numpy() for t in [(16, 16), (8, 8), (16, 8), (32, 8), (32, 16)]]
+    imgs = [gpu_forward(sc, vw, tile=t)[3].cpu().numpy() for t in [(16, 16), (8, 8), (16, 8), (32, 8), (32, 16), (32, 32)]]
     for im in imgs[1:]:
         assert np.array_equal(imgs[0], im)
 
