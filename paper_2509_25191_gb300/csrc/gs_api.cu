@@ -49,7 +49,7 @@ int num_sms() {
     return cached[dev];
 }
 
-// cuTensorMapEncodeTiled, fetched from the driver once (the library links
+// cuTensorMapEncodeTiled, fetched from the CUDA driver once (the library links
 // only the static CUDA runtime)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,

@@ -1,7 +1,7 @@
 // Internal definitions shared by the CUDA sources of libgsplat_gb300.
 #pragma once
 
-#include <cuda.h>   // CUtensorMap and its enums (types only: the encoder is fetched from the driver at run time)
+#include <cuda.h>   // CUtensorMap and its enums (types only: the encoder is fetched from the CUDA driver at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 

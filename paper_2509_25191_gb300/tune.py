@@ -57,7 +57,7 @@ def autotune(g: Gaussians, views: Views, target, candidates=CANDIDATES, reps=10,
         torch.cuda.synchronize()
         return a.elapsed_time(b) / n
 
-    # round 1: every candidate once; round 2: the two fastest, re-timed in
+    # pass 1: every candidate once; pass 2: the two fastest, re-timed in
     # alternation (median of three) so that clock ramp-up, the order of the
     # candidates and a single outlying measurement do not decide between
     # near-equal shapes
