@@ -212,7 +212,9 @@ def run_native(args, rank, world, local_rank):
     else:
         tile = tuple(int(x) for x in args.tile.split("x"))
 
-    step = GraphStep(g, views, target, tile=tile)
+    # two input slots (target, view matrices): the end-to-end loop below
+    # uploads step k+1's inputs into one while step k runs on the other
+    step = GraphStep(g, views, target, tile=tile, slots=2)
     rast, cfg, bins = step.rast, step.cfg, step.bins
     image, dvm, loss = step.image, step.dviewmat, step.loss
     kernels_per_step = GraphStep.KERNELS_PER_STEP
@@ -273,45 +275,45 @@ def run_native(args, rank, world, local_rank):
         k_e2e = max(3, min(args.steps, 50))
         tgt_dev = step.target
         host_step = [tgt_dev.cpu().pin_memory(), views.viewmats.cpu().pin_memory()]
-        dev_step = [tgt_dev, views.viewmats]
         host_par = [t.cpu().pin_memory() for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.sh)]
         dev_par = [g.means, g.log_scales, g.quats, g.opacity_logits, g.sh]
         out_img = torch.empty(image.shape, dtype=torch.float32).pin_memory()
         out_pose = torch.empty(dvm.shape, dtype=torch.float32).pin_memory()
         out_loss = torch.empty(loss.shape, dtype=torch.float32).pin_memory()
 
-        # the large per-step input (the target image) is uploaded for step k+1
-        # on a copy stream while step k computes (two device staging buffers,
-        # a device-to-device copy into the captured input at the step start)
+        # step k+1's inputs (the target image and the view matrices) are
+        # uploaded on a copy stream into the step's other input slot while
+        # step k computes; each step's graph reads its own slot
         copy_stream = torch.cuda.Stream(device=dev)
-        staging = [torch.empty_like(tgt_dev) for _ in range(2)]
         ready = [torch.cuda.Event() for _ in range(2)]
         consumed = [torch.cuda.Event() for _ in range(2)]
         main = torch.cuda.current_stream(dev)
 
         def run_e2e(with_params):
-            hosts = host_step[1:] + (host_par if with_params else [])
-            devs = dev_step[1:] + (dev_par if with_params else [])
+            hosts = host_par if with_params else []
+            devs = dev_par if with_params else []
             outs = [(out_loss, loss), (out_pose, dvm)] + ([(out_img, image)] if with_params else [])
             state = {"k": 0}
 
             def upload(k):
+                sl = k % 2
                 with torch.cuda.stream(copy_stream):
-                    copy_stream.wait_event(consumed[k % 2])
-                    staging[k % 2].copy_(host_step[0], non_blocking=True)
-                    ready[k % 2].record(copy_stream)
+                    copy_stream.wait_event(consumed[sl])      # the step that last read this slot is done
+                    step.viewmat_slots[sl].copy_(host_step[1], non_blocking=True)
+                    step.target_slots[sl].copy_(host_step[0], non_blocking=True)
+                    ready[sl].record(copy_stream)
 
             upload(0)
 
             def e2e_step():
                 k = state["k"]
-                main.wait_event(ready[k % 2])
-                tgt_dev.copy_(staging[k % 2], non_blocking=True)
-                consumed[k % 2].record(main)
+                sl = k % 2
+                main.wait_event(ready[sl])
                 upload(k + 1)
                 for h, d in zip(hosts, devs):
                     d.copy_(h, non_blocking=True)
-                graph.replay()
+                step.replay(sl)
+                consumed[sl].record(main)
                 for o, d in outs:
                     o.copy_(d, non_blocking=True)
                 state["k"] = k + 1
@@ -330,13 +332,14 @@ def run_native(args, rank, world, local_rank):
             torch.cuda.synchronize()
             ems = max_over_ranks(a.elapsed_time(b) / k_e2e, dev)
             return {"value": round(whole_job_mpix_s(P, world, ems), 3), "unit": UNIT,
-                    "h2d_bytes_per_step": int(host_step[0].numel() * 4 + sum(h.numel() * 4 for h in hosts)),
+                    "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in host_step + hosts)),
                     "d2h_bytes_per_step": int(sum(o.numel() * 4 for o, _ in outs)),
                     "ms_per_step": round(ems, 4), "steps": k_e2e}
 
         e2e = run_e2e(False)
         e2e["inputs"] = ("target image and camera pose in, loss and pose gradient out; Gaussians resident; "
-                         "the next step's target uploads on a copy stream during the current step")
+                         "the next step's target and pose upload on a copy stream into the step's other "
+                         "input slot during the current step")
         e2e_params = run_e2e(True)
         e2e_params["inputs"] = "also all Gaussian parameters in and the rendered image out, every step"
 

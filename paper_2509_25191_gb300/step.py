@@ -12,6 +12,12 @@ targets) are copied into the captured tensors before a replay; an instance
 count above the capacity is reported in the device status word and
 ``GraphStep.check()`` re-plans.
 
+With ``slots=2`` the step keeps two copies of its per-step inputs (target
+images and view matrices) and captures one graph per copy, sharing every
+other buffer: a training loop writes step k+1's inputs into the other slot
+(e.g. by an asynchronous host-to-device copy on another stream) while step k
+runs, and replays ``replay(k % 2)``.
+
 ``PlainStep`` is the uncaptured reference path: the same calls made view by
 view, each with the host readback of the instance count that an uncaptured
 call needs.
@@ -30,8 +36,15 @@ class GraphStep:
     KERNELS_PER_STEP = 11   # project 1, bin/sort 5, render 1, loss 1, raster bwd 1, projection bwd 1, pose 1
 
     def __init__(self, g: Gaussians, views: Views, target, tile=(16, 16), headroom=1.25, capture=True,
-                 want_gaussian_grads=True, loss="l1", lam=0.2):
+                 want_gaussian_grads=True, loss="l1", lam=0.2, slots=1):
         self.g, self.views, self.target = g, views, target
+        if slots < 1:
+            raise ValueError("slots must be >= 1")
+        # per-slot inputs: slot 0 is the caller's target and view matrices
+        self.target_slots = [target] + [torch.empty_like(target) for _ in range(slots - 1)]
+        self.viewmat_slots = [views.viewmats] + [torch.empty_like(views.viewmats) for _ in range(slots - 1)]
+        self.slot_views = [views] + [Views(vm, views.intrinsics, views.width, views.height, views.gauss_begin,
+                                           views.gauss_count) for vm in self.viewmat_slots[1:]]
         self.want = want_gaussian_grads
         if loss not in ("l1", "l1_dssim"):
             raise ValueError(f"unknown loss {loss!r}")
@@ -52,15 +65,17 @@ class GraphStep:
         self.dviewmat = torch.empty(views.n, 12, device=dev)
         self.dtwist = torch.empty(views.n, 6, device=dev)
         self.graph = None
+        self.graphs = []
         if capture:
             self.capture()
 
-    def run(self, events=None):
+    def run(self, events=None, slot=0):
         """Enqueue the step on the current stream (optionally recording an
-        event before and after every call)."""
+        event before and after every call), reading the inputs of ``slot``."""
         rec = (lambda: events.append(torch.cuda.Event(enable_timing=True)) or events[-1].record()) \
             if events is not None else (lambda: None)
-        g, v, cfg, b, st = self.g, self.views, self.cfg, self.bins, self.status
+        g, v, cfg, b, st = self.g, self.slot_views[slot], self.cfg, self.bins, self.status
+        target = self.target_slots[slot]
         rec()
         _lib.gs_project(g, v, cfg, self.proj, st)
         rec()
@@ -69,9 +84,9 @@ class GraphStep:
         _lib.gs_render_fwd(v, cfg, self.proj, b, self.image, st)
         rec()
         if self.loss_kind == "l1":
-            _lib.gs_l1_loss(self.image, self.target, self.loss, self.dimg)
+            _lib.gs_l1_loss(self.image, target, self.loss, self.dimg)
         else:
-            _lib.gs_l1_dssim_loss(v, self.image, self.target, self.loss, self.dimg, self.lam)
+            _lib.gs_l1_dssim_loss(v, self.image, target, self.loss, self.dimg, self.lam)
         rec()
         _lib.gs_rasterize_bwd(v, cfg, self.proj, b, self.image, self.dimg, self.grads.grad2d, st)
         rec()
@@ -84,16 +99,20 @@ class GraphStep:
         dev = self.g.means.device
         s = torch.cuda.Stream(device=dev)
         s.wait_stream(torch.cuda.current_stream(dev))
-        self.graph = torch.cuda.CUDAGraph()
+        self.graphs = []
         with torch.cuda.stream(s):
             self.run()
             torch.cuda.synchronize(dev)
-            with torch.cuda.graph(self.graph, stream=s):
-                self.run()
+            for slot in range(len(self.target_slots)):
+                gr = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(gr, stream=s):
+                    self.run(slot=slot)
+                self.graphs.append(gr)
         torch.cuda.synchronize(dev)
+        self.graph = self.graphs[0]
 
-    def replay(self):
-        self.graph.replay()
+    def replay(self, slot=0):
+        self.graphs[slot].replay()
 
     def check(self):
         """Read the status word (synchronises). On a capacity overflow, grow

@@ -485,6 +485,41 @@ def test_l1_loss_kernel():
 # CUDA graph capture of a whole step
 # ---------------------------------------------------------------------------
 
+def test_graph_step_input_slots():
+    """A two-slot GraphStep captures one graph per input slot (target and
+    view matrices) over shared buffers; replaying a slot gives the results of
+    a single-slot step built on that slot's inputs."""
+    from paper_2509_25191_gb300.step import GraphStep
+    sc, vw = CASES["clustered_sh3"]()
+    g = _lib.Gaussians.from_scene(sc)
+    views = _lib.Views.from_synth(vw)
+    gen = torch.Generator("cuda").manual_seed(3)
+    t0 = torch.rand(views.num_image_floats(), device="cuda", generator=gen)
+    t1 = torch.rand(views.num_image_floats(), device="cuda", generator=gen)
+    vm1 = views.viewmats.clone()
+    vm1[:, 9:] += 0.02
+    step = GraphStep(g, views, t0, slots=2)
+    step.target_slots[1].copy_(t1)
+    step.viewmat_slots[1].copy_(vm1)
+    got = []
+    for sl in (0, 1, 0):
+        step.replay(sl)
+        got.append((step.loss.clone(), step.dviewmat.clone(), step.image.clone()))
+    views1 = _lib.Views(vm1, views.intrinsics, views.width, views.height, views.gauss_begin, views.gauss_count)
+    refs = []
+    for vv, tt in ((views, t0), (views1, t1)):
+        ref = GraphStep(g, vv, tt)
+        ref.replay()
+        refs.append((ref.loss.clone(), ref.dviewmat.clone(), ref.image.clone()))
+    torch.cuda.synchronize()
+    assert not step.check()
+    for (l, d, im), (rl, rd, rim) in zip(got, [refs[0], refs[1], refs[0]]):
+        assert torch.equal(im, rim)
+        assert abs(float(l) - float(rl)) <= 1e-6 * abs(float(rl))
+        check_grad(d.cpu().numpy(), rd.cpu().numpy(), "slot pose gradient", 1e-4, 1e-4, 1e-6)
+    assert not torch.equal(got[0][2], got[1][2])
+
+
 def test_graph_capture_replays_step():
     sc, vw = CASES["orbit_4views"]()
     g = _lib.Gaussians.from_scene(sc)
