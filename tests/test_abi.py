@@ -56,3 +56,21 @@ def test_cuda_calls_fail_cleanly_with_bad_arguments():
     assert lib.gs_project(None, None, None, None, None, None) == _lib.GS_ERR_ARG
     assert lib.gs_pose_grad(None, None, 0, None, None, None) == _lib.GS_ERR_ARG
     assert lib.gs_l1_loss(None, None, ctypes.c_int64(-1), None, None, None) == _lib.GS_ERR_ARG
+
+
+def test_tile_shapes_on_the_host():
+    """Every supported tile shape has a tile grid; an unsupported one is
+    rejected by the host-side checks before anything is enqueued."""
+    from paper_2509_25191_gb300 import _lib, synth
+    sc, vw = synth.single_view_small(n=8)
+    lib = _lib.load()
+    views = _lib.Views(None, None, vw.width, vw.height, vw.gauss_begin, vw.gauss_count)
+    c = views.c()
+    W, H = int(vw.width[0]), int(vw.height[0])
+    for tw, th in [(16, 16), (8, 8), (16, 8), (32, 8), (32, 16), (32, 32)]:
+        cfg = _lib.config(tile=(tw, th))
+        assert lib.gs_num_tiles(ctypes.byref(c), ctypes.byref(cfg)) == ((W + tw - 1) // tw) * ((H + th - 1) // th)
+    bad = _lib.config(tile=(24, 24))
+    g = _lib.gs_gaussians()
+    assert lib.gs_project(ctypes.byref(g), ctypes.byref(c), ctypes.byref(bad), None, None, None) == \
+        _lib.GS_ERR_UNSUPPORTED
