@@ -11,13 +11,16 @@
 // IEEE bits sort like the values.
 //
 // Kernels:
-//   k_bin_count    per-tile counts, block-aggregated in shared memory
+//   k_bin_count    per-tile counts, block-aggregated in shared memory; one
+//                  global atomic per (block, tile) reserves the block's
+//                  range in the tile (kept in a table when it fits)
 //   k_bin_scan     one block: tile ranges, cursors, instance total, capacity
 //                  check, and a work order of tiles by decreasing count
-//   k_bin_scatter  writes keys: one global reservation per (block, tile),
-//                  placement inside it by shared-memory atomics
+//   k_bin_scatter  writes keys inside the reserved ranges, placement by
+//                  shared-memory atomics
 //   k_sort_tiles   persistent, largest tiles first; radix sort on chip
-//                  (chunks + merge path for tiles above 4096 instances)
+//                  (a tile above 4096 instances is first partitioned by
+//                  depth, and runs of partitions are sorted on chip)
 #include "gs_common.cuh"
 
 namespace gsk {

@@ -3,7 +3,9 @@
 //
 // One thread per Gaussian (fixed grid, grid-stride), looping over the views of
 // its scene: the Gaussian's parameters are read once, its gradients are summed
-// over views in registers and written once (overwrite). Each view's pose
+// over views in registers and written once (overwrite). For degree-3 SH the
+// block's SH rows and first-view 2D-gradient rows arrive by tensor copies and
+// its SH-coefficient gradients leave by tensor stores (see PbStage). Each view's pose
 // gradient (dL/dR, dL/dt; Section 3.4 needs it for the pose residuals) is
 // summed over a warp with shuffles, kept per warp in shared memory, and
 // written as one partial per block; k_pose_reduce then sums the partials in a
