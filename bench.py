@@ -214,7 +214,7 @@ def run_native(args, rank, world, local_rank):
 
     # two input slots (target, view matrices): the end-to-end loop below
     # uploads step k+1's inputs into one while step k runs on the other
-    step = GraphStep(g, views, target, tile=tile, slots=2)
+    step = GraphStep(g, views, target, tile=tile, slots=2, slot_gaussians=not args.no_e2e)
     rast, cfg, bins = step.rast, step.cfg, step.bins
     image, dvm, loss = step.image, step.dviewmat, step.loss
     kernels_per_step = GraphStep.KERNELS_PER_STEP
@@ -276,7 +276,6 @@ def run_native(args, rank, world, local_rank):
         tgt_dev = step.target
         host_step = [tgt_dev.cpu().pin_memory(), views.viewmats.cpu().pin_memory()]
         host_par = [t.cpu().pin_memory() for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.sh)]
-        dev_par = [g.means, g.log_scales, g.quats, g.opacity_logits, g.sh]
         out_img = torch.empty(image.shape, dtype=torch.float32).pin_memory()
         out_pose = torch.empty(dvm.shape, dtype=torch.float32).pin_memory()
         out_loss = torch.empty(loss.shape, dtype=torch.float32).pin_memory()
@@ -291,16 +290,18 @@ def run_native(args, rank, world, local_rank):
 
         def run_e2e(with_params):
             hosts = host_par if with_params else []
-            devs = dev_par if with_params else []
             outs = [(out_loss, loss), (out_pose, dvm)] + ([(out_img, image)] if with_params else [])
             state = {"k": 0}
 
             def upload(k):
                 sl = k % 2
+                gs = step.gauss_slots[sl]
                 with torch.cuda.stream(copy_stream):
                     copy_stream.wait_event(consumed[sl])      # the step that last read this slot is done
                     step.viewmat_slots[sl].copy_(host_step[1], non_blocking=True)
                     step.target_slots[sl].copy_(host_step[0], non_blocking=True)
+                    for h, d in zip(hosts, (gs.means, gs.log_scales, gs.quats, gs.opacity_logits, gs.sh)):
+                        d.copy_(h, non_blocking=True)
                     ready[sl].record(copy_stream)
 
             upload(0)
@@ -310,8 +311,6 @@ def run_native(args, rank, world, local_rank):
                 sl = k % 2
                 main.wait_event(ready[sl])
                 upload(k + 1)
-                for h, d in zip(hosts, devs):
-                    d.copy_(h, non_blocking=True)
                 step.replay(sl)
                 consumed[sl].record(main)
                 for o, d in outs:
@@ -341,7 +340,8 @@ def run_native(args, rank, world, local_rank):
                          "the next step's target and pose upload on a copy stream into the step's other "
                          "input slot during the current step")
         e2e_params = run_e2e(True)
-        e2e_params["inputs"] = "also all Gaussian parameters in and the rendered image out, every step"
+        e2e_params["inputs"] = ("also all Gaussian parameters in (uploaded with the step's other inputs into "
+                                "its other slot) and the rendered image out, every step")
 
     # roofline of the dominant kernel
     rt = RASTER_BWD_TRAFFIC

@@ -13,10 +13,11 @@ count above the capacity is reported in the device status word and
 ``GraphStep.check()`` re-plans.
 
 With ``slots=2`` the step keeps two copies of its per-step inputs (target
-images and view matrices) and captures one graph per copy, sharing every
-other buffer: a training loop writes step k+1's inputs into the other slot
-(e.g. by an asynchronous host-to-device copy on another stream) while step k
-runs, and replays ``replay(k % 2)``.
+images and view matrices, and with ``slot_gaussians=True`` the Gaussian
+parameters too) and captures one graph per copy, sharing every other buffer:
+a training loop writes step k+1's inputs into the other slot (e.g. by an
+asynchronous host-to-device copy on another stream) while step k runs, and
+replays ``replay(k % 2)``.
 
 ``PlainStep`` is the uncaptured reference path: the same calls made view by
 view, each with the host readback of the instance count that an uncaptured
@@ -36,7 +37,7 @@ class GraphStep:
     KERNELS_PER_STEP = 11   # project 1, bin/sort 5, render 1, loss 1, raster bwd 1, projection bwd 1, pose 1
 
     def __init__(self, g: Gaussians, views: Views, target, tile=(16, 16), headroom=1.25, capture=True,
-                 want_gaussian_grads=True, loss="l1", lam=0.2, slots=1):
+                 want_gaussian_grads=True, loss="l1", lam=0.2, slots=1, slot_gaussians=False):
         self.g, self.views, self.target = g, views, target
         if slots < 1:
             raise ValueError("slots must be >= 1")
@@ -45,6 +46,10 @@ class GraphStep:
         self.viewmat_slots = [views.viewmats] + [torch.empty_like(views.viewmats) for _ in range(slots - 1)]
         self.slot_views = [views] + [Views(vm, views.intrinsics, views.width, views.height, views.gauss_begin,
                                            views.gauss_count) for vm in self.viewmat_slots[1:]]
+        # (a Gaussian slot starts as a copy of the caller's parameters)
+        self.gauss_slots = [g] + [Gaussians(*(t.clone() for t in (g.means, g.log_scales, g.quats,
+                                                                  g.opacity_logits, g.sh)))
+                                  if slot_gaussians else g for _ in range(slots - 1)]
         self.want = want_gaussian_grads
         if loss not in ("l1", "l1_dssim"):
             raise ValueError(f"unknown loss {loss!r}")
@@ -74,7 +79,7 @@ class GraphStep:
         event before and after every call), reading the inputs of ``slot``."""
         rec = (lambda: events.append(torch.cuda.Event(enable_timing=True)) or events[-1].record()) \
             if events is not None else (lambda: None)
-        g, v, cfg, b, st = self.g, self.slot_views[slot], self.cfg, self.bins, self.status
+        g, v, cfg, b, st = self.gauss_slots[slot], self.slot_views[slot], self.cfg, self.bins, self.status
         target = self.target_slots[slot]
         rec()
         _lib.gs_project(g, v, cfg, self.proj, st)

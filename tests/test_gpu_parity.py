@@ -498,7 +498,7 @@ def test_graph_step_input_slots():
     t1 = torch.rand(views.num_image_floats(), device="cuda", generator=gen)
     vm1 = views.viewmats.clone()
     vm1[:, 9:] += 0.02
-    step = GraphStep(g, views, t0, slots=2)
+    step = GraphStep(g, views, t0, slots=2, slot_gaussians=True)
     step.target_slots[1].copy_(t1)
     step.viewmat_slots[1].copy_(vm1)
     got = []
