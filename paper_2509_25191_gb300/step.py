@@ -17,7 +17,10 @@ images and view matrices, and with ``slot_gaussians=True`` the Gaussian
 parameters too) and captures one graph per copy, sharing every other buffer:
 a training loop writes step k+1's inputs into the other slot (e.g. by an
 asynchronous host-to-device copy on another stream) while step k runs, and
-replays ``replay(k % 2)``.
+replays ``replay(k % 2)``. Gaussian slots are separate tensors (slot 0 is
+the caller's, slot 1 starts as a copy): an in-place update of one slot's
+parameters does not reach the other, so a loop that updates the parameters
+on the device writes each step's parameters into the slot it replays.
 
 ``PlainStep`` is the uncaptured reference path: the same calls made view by
 view, each with the host readback of the instance count that an uncaptured
