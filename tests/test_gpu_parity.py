@@ -486,9 +486,9 @@ def test_l1_loss_kernel():
 # ---------------------------------------------------------------------------
 
 def test_graph_step_input_slots():
-    """A two-slot GraphStep captures one graph per input slot (target and
-    view matrices) over shared buffers; replaying a slot gives the results of
-    a single-slot step built on that slot's inputs."""
+    """A two-slot GraphStep captures one graph per input slot (target, view
+    matrices and Gaussian parameters) over shared buffers; replaying a slot
+    gives the results of a single-slot step built on that slot's inputs."""
     from paper_2509_25191_gb300.step import GraphStep
     sc, vw = CASES["clustered_sh3"]()
     g = _lib.Gaussians.from_scene(sc)
@@ -498,26 +498,39 @@ def test_graph_step_input_slots():
     t1 = torch.rand(views.num_image_floats(), device="cuda", generator=gen)
     vm1 = views.viewmats.clone()
     vm1[:, 9:] += 0.02
+    # slot 1's Gaussians: slightly more opaque and moved
+    g1 = _lib.Gaussians(g.means + 0.01 * torch.randn(g.means.shape, device="cuda", generator=gen),
+                        g.log_scales.clone(), g.quats.clone(), g.opacity_logits + 0.25, g.sh.clone())
     step = GraphStep(g, views, t0, slots=2, slot_gaussians=True)
     step.target_slots[1].copy_(t1)
     step.viewmat_slots[1].copy_(vm1)
+    for dst, src in zip(_gauss_tensors(step.gauss_slots[1]), _gauss_tensors(g1)):
+        dst.copy_(src)
     got = []
     for sl in (0, 1, 0):
         step.replay(sl)
-        got.append((step.loss.clone(), step.dviewmat.clone(), step.image.clone()))
+        got.append((step.loss.clone(), step.dviewmat.clone(), step.image.clone(), step.grads.means.clone(),
+                    step.grads.opacity_logits.clone()))
     views1 = _lib.Views(vm1, views.intrinsics, views.width, views.height, views.gauss_begin, views.gauss_count)
     refs = []
-    for vv, tt in ((views, t0), (views1, t1)):
-        ref = GraphStep(g, vv, tt)
+    for gg, vv, tt in ((g, views, t0), (g1, views1, t1)):
+        ref = GraphStep(gg, vv, tt)
         ref.replay()
-        refs.append((ref.loss.clone(), ref.dviewmat.clone(), ref.image.clone()))
+        refs.append((ref.loss.clone(), ref.dviewmat.clone(), ref.image.clone(), ref.grads.means.clone(),
+                     ref.grads.opacity_logits.clone()))
     torch.cuda.synchronize()
     assert not step.check()
-    for (l, d, im), (rl, rd, rim) in zip(got, [refs[0], refs[1], refs[0]]):
+    for (l, d, im, gm, go), (rl, rd, rim, rgm, rgo) in zip(got, [refs[0], refs[1], refs[0]]):
         assert torch.equal(im, rim)
         assert abs(float(l) - float(rl)) <= 1e-6 * abs(float(rl))
         check_grad(d.cpu().numpy(), rd.cpu().numpy(), "slot pose gradient", 1e-4, 1e-4, 1e-6)
+        check_grad(gm.cpu().numpy(), rgm.cpu().numpy(), "slot mean gradient", 1e-3, 1e-3, 1e-6)
+        check_grad(go.cpu().numpy(), rgo.cpu().numpy(), "slot opacity gradient", 1e-3, 1e-3, 1e-6)
     assert not torch.equal(got[0][2], got[1][2])
+
+
+def _gauss_tensors(g):
+    return (g.means, g.log_scales, g.quats, g.opacity_logits, g.sh)
 
 
 def test_graph_capture_replays_step():
