@@ -626,14 +626,34 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_tiles(const Launch L, con
         for (int i = threadIdx.x; i < n; i += SORT_THREADS)
             atomicAdd(&mcnt[(((unsigned int)(keys[r.x + i] >> 32)) - kmin) >> mshift], 1u);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned int acc = 0;
-            for (int b = 0; b < 256; ++b) {
-                S.moff[b] = acc;
-                acc += mcnt[b];
-                mcnt[b] = S.moff[b];   // becomes the scatter cursor
+        {
+            // exclusive scan of the 256 bin counts, thread b owning bin b; the
+            // offsets become the scatter cursors
+            const int b = threadIdx.x, lane = b & 31, wid = b >> 5;
+            const unsigned int c = mcnt[b];
+            unsigned int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
             }
-            S.moff[256] = acc;
+            if (lane == 31) S.part[wid] = incl;
+            __syncthreads();
+            if (wid == 0) {
+                const unsigned int w = lane < SORT_WARPS ? S.part[lane] : 0u;
+                unsigned int wi = w;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned int t = __shfl_up_sync(0xffffffffu, wi, o);
+                    if (lane >= o) wi += t;
+                }
+                if (lane < SORT_WARPS) S.part[lane] = wi - w;
+            }
+            __syncthreads();
+            const unsigned int excl = S.part[wid] + incl - c;
+            S.moff[b] = excl;
+            mcnt[b] = excl;
+            if (b == 255) S.moff[256] = excl + c;
         }
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
