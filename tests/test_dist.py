@@ -48,3 +48,20 @@ def test_single_process_reduction_is_identity():
     import bench
     assert bench.max_over_ranks(4.25) == 4.25
     assert bench.whole_job_mpix_s(1_016_814, 1, 2.0) == pytest.approx(508.407)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """The reference arm (the FP64 oracle on the host cores) on a reduced
+    scene: one JSON line with the contract's keys, the oracle named as the
+    CPU baseline, and no host<->device bytes."""
+    import bench
+    args = type("A", (), dict(steps=2, warmup=1, n=20_000, ref_fraction=1.0 / 64.0))()
+    out = bench.run_reference(args, 0, 1)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in out, k
+    assert out["impl"] == "reference" and out["dtype"] == "f64" and out["steps"] == 2
+    assert out["value"] > 0 and out["cpu_baseline"]["kind"] == "oracle"
+    assert out["cpu_baseline"]["value"] == out["value"] and out["e2e"]["value"] == out["value"]
+    assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["d2h_bytes_per_step"] == 0
+    assert out["metric"] == bench.METRIC and out["unit"] == bench.UNIT
