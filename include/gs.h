@@ -421,6 +421,15 @@ int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *views, const g
                            const float *grad2d, const gs_grads *grads, int want_gaussian_grads,
                            float *dL_dviewmat, float *dL_dtwist, int32_t *status, void *stream);
 
+/* Check of the device-side failure path: enqueues one thread that arms a
+ * copy barrier (PTX mbarrier with 16 transaction bytes) for a copy that is
+ * never issued and waits on it with the same bounded wait the projection
+ * kernels use. The wait gives up after about one second and the thread sets
+ * status = {GS_ERR_TIMEOUT, 0} (DEVICE int32[4]; the caller zeroes it before
+ * the call and reads it after synchronising); nothing faults or traps, and
+ * the context stays usable. Returns GS_ERR_ARG for a NULL status. */
+int gs_check_bounded_wait(int32_t *status, void *stream);
+
 const char *gs_error_string(int code);
 int gs_version(void);
 

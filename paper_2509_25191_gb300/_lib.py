@@ -25,7 +25,8 @@ EXPORTED = ["gs_config_default", "gs_num_slots", "gs_slot_base", "gs_num_tiles",
             "gs_num_image_floats", "gs_pixel_base", "gs_pose_blocks", "gs_project", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version",
             "gs_project_bwd_noalloc", "gs_sgld_adam_step", "gs_ga_select_pairs", "gs_ga_incidence",
-            "gs_ga_epipolar", "gs_ga_weights_scratch_bytes", "gs_ga_weights", "gs_ga_step", "gs_l1_dssim_loss"]
+            "gs_ga_epipolar", "gs_ga_weights_scratch_bytes", "gs_ga_weights", "gs_ga_step", "gs_l1_dssim_loss",
+            "gs_check_bounded_wait"]
 GS_GA_MAX_CAMS = 8192
 GS_GA_PAIR_FLOATS = 12
 GS_GA_MAX_BINS = 16384
@@ -409,6 +410,12 @@ def gs_l1_dssim_loss(views: Views, image, target, loss, dL_dimage, lam=0.2, stre
     gradient, views concatenated [3,H,W] each."""
     _check(load().gs_l1_dssim_loss(ctypes.byref(views.c()), _ptr(image), _ptr(target), ctypes.c_float(lam),
                                    _ptr(loss), _ptr(dL_dimage), _stream(stream)), "gs_l1_dssim_loss")
+
+
+def gs_check_bounded_wait(status, stream=None):
+    """Enqueue the bounded-wait check: status (int32[4], zeroed by the
+    caller) becomes {GS_ERR_TIMEOUT, 0, ...} after about a second."""
+    _check(load().gs_check_bounded_wait(_ptr(status), _stream(stream)), "gs_check_bounded_wait")
 
 
 def gs_l1_loss(image, target, loss, dL_dimage, stream=None):

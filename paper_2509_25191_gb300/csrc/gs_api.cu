@@ -436,6 +436,7 @@ const char *gs_error_string(int code) {
     case GS_ERR_UNSUPPORTED: return "unsupported configuration";
     case GS_ERR_OVERFLOW: return "more than 2^31-1 tile instances";
     case GS_ERR_TOO_LARGE: return "pose partials exceed the fixed scratch of the allocation-free entry point";
+    case GS_ERR_TIMEOUT: return "a bounded wait for an asynchronous copy ran out";
     default: return "unknown status";
     }
 }
@@ -510,4 +511,28 @@ extern "C" int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *vw,
                             want_gaussian_grads, nblk, status, st);
     if (rc) return rc;
     return launch_pose_reduce(L.n_views, scratch, nblk, vw->viewmats, dL_dviewmat, dL_dtwist, st);
+}
+
+// ---------------------------------------------------------------------------
+// Check of the bounded wait (gs_check_bounded_wait): one thread arms an
+// mbarrier for 16 bytes of a copy that is never issued and waits on it with
+// the projection kernels' bounded wait, which must give up and report.
+// ---------------------------------------------------------------------------
+namespace gsk {
+__global__ void k_wait_check(int32_t *status) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, 16);   // the one arrival, with 16 bytes outstanding that nothing delivers
+    if (!mbar_wait(&bar, 0)) {
+        atomicCAS(status, 0, GS_ERR_TIMEOUT);
+        atomicExch(status + 1, 0);
+    }
+}
+}  // namespace gsk
+
+extern "C" int gs_check_bounded_wait(int32_t *status, void *stream) {
+    if (!status) return GS_ERR_ARG;
+    gsk::k_wait_check<<<1, 32, 0, (cudaStream_t)stream>>>(status);
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

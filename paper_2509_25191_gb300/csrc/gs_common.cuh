@@ -259,10 +259,19 @@ __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, flo
 
 // ---------------------------------------------------------------------------
 // asynchronous bulk copies (TMA) with an mbarrier, PTX ISA "cp.async.bulk"
-// and "mbarrier". Every wait is bounded: it gives up after ~2^20 polls of
-// mbarrier.try_wait (each poll may suspend the thread for a while), so a
+// and "mbarrier". Every wait is bounded: it gives up after 2^20 polls of
+// mbarrier.try_wait or once GS_WAIT_LIMIT_NS of the global nanosecond timer
+// have passed, whichever comes first (a poll may suspend the thread for a
+// system-dependent time, so the timer bounds the wait's duration), and a
 // copy that never lands ends in an error status instead of a hang.
 // ---------------------------------------------------------------------------
+constexpr unsigned long long GS_WAIT_LIMIT_NS = 1000000000ull;   // 1 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
@@ -279,6 +288,7 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t
 // number of polls ran out first
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
     const uint32_t a = smem_u32(bar);
+    unsigned long long t0 = 0;
     for (int it = 0; it < (1 << 20); ++it) {
         uint32_t done;
         asm volatile(
@@ -287,6 +297,11 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((it & 63) == 0) {   // the timer is read only while the copy is late
+            const unsigned long long t = global_ns();
+            if (it == 0) t0 = t;
+            else if (t - t0 > GS_WAIT_LIMIT_NS) return false;
+        }
     }
     return false;
 }

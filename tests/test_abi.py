@@ -29,6 +29,7 @@ def test_library_exports_every_declared_symbol():
     assert lib.gs_version() >= 1
     lib.gs_error_string.restype = ctypes.c_char_p
     assert lib.gs_error_string(3) == b"instance capacity exceeded"
+    assert lib.gs_error_string(7) == b"a bounded wait for an asynchronous copy ran out"
 
 
 def test_host_layout_queries_without_gpu():

@@ -481,6 +481,29 @@ def test_l1_loss_kernel():
     assert np.array_equal(grad.cpu().numpy(), (np.sign(d) / d.size).astype(np.float32))
 
 
+def test_bounded_wait_runs_out_and_reports():
+    """The projection kernels' bounded wait, on a copy barrier that nothing
+    completes, gives up after about a second and reports GS_ERR_TIMEOUT in
+    the status word; nothing faults and the context keeps running kernels."""
+    import time
+    status = torch.zeros(4, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _lib.gs_check_bounded_wait(status)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    assert status.tolist() == [_lib.GS_ERR_TIMEOUT, 0, 0, 0]
+    assert 0.5 < dt < 30.0, dt
+    assert "bounded wait" in _lib.error_string(_lib.GS_ERR_TIMEOUT)
+    # the context still runs the library's kernels
+    a = torch.zeros(3 * 64, device="cuda")
+    b = torch.full_like(a, 0.5)
+    loss = torch.empty(1, device="cuda")
+    _lib.gs_l1_loss(a, b, loss, torch.empty_like(a))
+    torch.cuda.synchronize()
+    assert loss.item() == 0.5
+
+
 # ---------------------------------------------------------------------------
 # CUDA graph capture of a whole step
 # ---------------------------------------------------------------------------
