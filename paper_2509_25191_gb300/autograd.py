@@ -7,7 +7,9 @@ grow the buffers when needed; captured (CUDA graph) calls run with a fixed
 capacity and report overflow through the device status word.
 
 ``RasterizeViews`` is the autograd.Function: forward = gs_project +
-gs_bin_sort + gs_render_fwd, backward = gs_render_bwd + gs_pose_grad. The
+gs_bin_sort + gs_render_fwd, backward = gs_render_bwd + gs_pose_grad (after
+rebuilding the forward's tile lists if the same ``Rasterizer`` has run
+another forward in between). The
 backward recomputes transmittance from the forward image instead of storing
 it (Section 3.4's joint pose optimisation over many views needs the memory).
 Gradients flow to means, log-scales, quaternions, opacity logits, SH
@@ -35,6 +37,7 @@ class Rasterizer:
         self.fixed_capacity = False   # set for graph capture: never read back
         self._grads = None
         self.last_instances = None
+        self.generation = 0           # counts bin_sort calls: which forward the tile lists belong to
 
     # ------------------------------------------------------------------
     def _ensure_bins(self, views: Views, capacity: int, device):
@@ -65,6 +68,7 @@ class Rasterizer:
         elif self.bins.n_tiles != views.num_tiles(self.cfg):
             self._ensure_bins(views, self.bins.capacity, dev)
         _lib.gs_bin_sort(views, self.cfg, proj, self.bins, self.status)
+        self.generation += 1
         if not self.fixed_capacity:
             n = int(self.bins.counters[0].item())   # the one readback of the uncaptured path
             self.last_instances = n
@@ -122,7 +126,7 @@ class RasterizeViews(torch.autograd.Function):
                       opacity_logits.detach().contiguous(), sh.detach().contiguous())
         views = Views(viewmats.detach().contiguous(), intrinsics.detach().contiguous(), *layout)
         image, proj = rast.forward(g, views)
-        ctx.rast, ctx.g, ctx.views, ctx.proj = rast, g, views, proj
+        ctx.rast, ctx.g, ctx.views, ctx.proj, ctx.generation = rast, g, views, proj, rast.generation
         ctx.want_gauss = any(ctx.needs_input_grad[:5])
         ctx.save_for_backward(image)
         return image
@@ -130,6 +134,10 @@ class RasterizeViews(torch.autograd.Function):
     @staticmethod
     def backward(ctx, dL_dimage):
         (image,) = ctx.saved_tensors
+        if ctx.rast.generation != ctx.generation:
+            # the rasterizer has binned another forward since: rebuild this
+            # forward's tile lists from its projected records (same lists)
+            ctx.rast.bin_sort(ctx.views, ctx.proj)
         grads, dvm, _ = ctx.rast.backward(ctx.g, ctx.views, ctx.proj, image, dL_dimage.contiguous(),
                                           want_gaussian_grads=ctx.want_gauss)
         if ctx.want_gauss:

@@ -468,6 +468,35 @@ def test_autograd_and_pose_residual_chain():
     check_grad(params[0].grad.cpu().numpy(), rg["means"], "means via autograd")
 
 
+def test_autograd_shared_rasterizer_two_forwards():
+    """Two forwards through one Rasterizer (different views), then one
+    backward of both: each backward uses its own forward's tile lists, so the
+    gradients equal those of two separate rasterizers."""
+    from paper_2509_25191_gb300.autograd import RasterizeViews
+    sc, vw = CASES["orbit_4views"]()
+    g = _lib.Gaussians.from_scene(sc)
+    parts = [vw.select([0, 1]), vw.select([2, 3])]
+    gen = torch.Generator("cuda").manual_seed(9)
+    ws = [torch.randn(3 * int((p.width * p.height).sum()), device="cuda", generator=gen) for p in parts]
+
+    def run(shared):
+        params = [t.clone().requires_grad_(True) for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.sh)]
+        rast = Rasterizer()
+        loss = 0.0
+        for p, w in zip(parts, ws):
+            layout = (p.width, p.height, p.gauss_begin, p.gauss_count)
+            img = RasterizeViews.apply(*params, torch.as_tensor(p.viewmats).cuda(),
+                                       torch.as_tensor(p.intrinsics).cuda(), layout,
+                                       rast if shared else Rasterizer())
+            loss = loss + (img * w).sum()
+        loss.backward()
+        return [t.grad.cpu().numpy() for t in params]
+
+    shared, separate = run(True), run(False)
+    for name, a, b in zip(("means", "log_scales", "quats", "opacity", "sh"), shared, separate):
+        check_grad(a, b, f"shared rasterizer {name}", 1e-4, 1e-3, 1e-6)
+
+
 def test_l1_loss_kernel():
     a = torch.rand(3 * 37 * 41 + 3, device="cuda")
     b = torch.rand_like(a)
