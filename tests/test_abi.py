@@ -75,3 +75,39 @@ def test_tile_shapes_on_the_host():
     g = _lib.gs_gaussians()
     assert lib.gs_project(ctypes.byref(g), ctypes.byref(c), ctypes.byref(bad), None, None, None) == \
         _lib.GS_ERR_UNSUPPORTED
+
+
+def test_host_checks_reject_bad_layouts():
+    """Every layout error is caught by the host-side checks and returned
+    before anything is enqueued (no device is touched: the pointers below
+    are placeholders that are never dereferenced)."""
+    import numpy as np
+    from paper_2509_25191_gb300 import _lib
+    lib = _lib.load()
+    fake = ctypes.c_void_p(1 << 20)   # 16-byte aligned, never dereferenced
+
+    def views(widths, heights, begins, counts):
+        arrs = (np.asarray(widths, np.int32), np.asarray(heights, np.int32), np.asarray(begins, np.int64),
+                np.asarray(counts, np.int64))
+        v = _lib.gs_views(len(widths), fake, fake, *(a.ctypes.data for a in arrs))
+        return v, arrs
+
+    def project(v, cfg=None, n=100, deg=0):
+        g = _lib.gs_gaussians(n, deg, fake, fake, fake, fake, fake)
+        cfg = cfg or _lib.config()
+        return lib.gs_project(ctypes.byref(g), ctypes.byref(v), ctypes.byref(cfg), fake, None, None)
+
+    ok_v, keep = views([64], [48], [0], [100])
+    too_many, k1 = views([8] * 65, [8] * 65, [0] * 65, [10] * 65)
+    assert project(too_many) == _lib.GS_ERR_ARG                      # more than GS_MAX_VIEWS views
+    zero_w, k2 = views([0], [48], [0], [10])
+    assert project(zero_w) == _lib.GS_ERR_ARG                        # empty image
+    beyond, k3 = views([64], [48], [90], [20])
+    assert project(beyond) == _lib.GS_ERR_ARG                        # view range past the last Gaussian
+    overlap, k4 = views([64, 64], [48, 48], [0, 50], [60, 50])
+    assert project(overlap) == _lib.GS_ERR_ARG                       # scene ranges overlap
+    assert project(ok_v, deg=4) == _lib.GS_ERR_UNSUPPORTED           # SH degree above 3
+    bad_alpha = _lib.config()
+    bad_alpha.alpha_max = 1.0
+    assert project(ok_v, cfg=bad_alpha) == _lib.GS_ERR_ARG           # alpha clamp must be below 1
+    assert lib.gs_check_bounded_wait(None, None) == _lib.GS_ERR_ARG
