@@ -5,8 +5,9 @@ and the raster kernels' block shape, and the best choice depends on the
 scene (Gaussian footprints), the resolution and the number of views. The
 tuner times the whole captured training step (GraphStep) for each candidate
 tile shape on the caller's own inputs and keeps the fastest. The shared
-memory batch is tied to the tile (one staged Gaussian per pixel of the tile),
-so choosing the tile chooses the batch. Results are cached in a JSON file
+memory batch is tied to the tile (per batch the forward stages one Gaussian
+per pixel of the tile, the backward one per thread, i.e. per two pixels), so
+choosing the tile chooses the batch. Results are cached in a JSON file
 keyed by GPU name and a coarse workload signature (Gaussian count, views,
 pixels, SH degree), so a training run pays for tuning once.
 """
