@@ -30,7 +30,8 @@
  *     status word int32[4] = {code, detail_lo, detail_hi, 0}; the caller reads
  *     it at a point of its choosing. Kernels never trap; the only waits
  *     are the projection kernels' bounded waits for their own tensor copies
- *     (GS_ERR_TIMEOUT if one runs out).
+ *     (GS_ERR_TIMEOUT if one runs out; gs_check_bounded_wait makes one run
+ *     out on purpose, for tests of this path).
  *   - The enqueued work also depends on the environment variable
  *     GS_DISABLE_TMA, read at each call: "1" makes the projection kernels
  *     read and write per thread instead of staging through tensor copies
