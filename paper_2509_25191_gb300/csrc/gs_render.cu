@@ -11,8 +11,9 @@
 // Both kernels are persistent: blocks pull tiles from an atomic queue over
 // tile_order (largest tiles first). Each thread owns two pixels and each warp
 // an 8x8-pixel patch of the tile; a tile's instances are staged through
-// shared memory in batches (two per thread), and a warp skips every staged
-// Gaussian that cannot reach its patch.
+// shared memory in batches (two per thread in the forward, one in the
+// backward), and a warp skips every staged Gaussian that cannot reach its
+// patch.
 //
 // The backward does not store or replay transmittance: it walks the same list
 // front to back with bit-identical arithmetic (explicit-rounding intrinsics,
