@@ -394,6 +394,27 @@ def test_backward_parity(case):
     check_grad(dtw.cpu().numpy(), tw, "twist")
 
 
+def test_maximum_view_count_parity():
+    """GS_MAX_VIEWS (64) views of one scene in one call: images, mean and
+    pose gradients against the oracle."""
+    sc, vw = synth.orbit_views(0, 3000, 64, 48, 32, 1000.0 * 48 / 979.0)
+    assert vw.n == _lib.GS_MAX_VIEWS
+    bg = (0.2, 0.1, 0.3)
+    rast, g, views, image, proj = gpu_forward(sc, vw, bg=bg)
+    ref = oracle_forward(sc, vw, bg=bg)
+    err, flagged = image_errors(split(image, vw), ref)
+    assert err <= 1e-4, (err, flagged)
+    assert flagged <= 0.01 * vw.pixels
+    ups = upstream(vw, ref)
+    up = torch.as_tensor(np.concatenate([u.reshape(-1) for u in ups])).cuda()
+    grads, dvm, dtw = rast.backward(g, views, proj, image, up)
+    torch.cuda.synchronize()
+    rg, dRt, tw, _ = O.backward(sc, vw, ref, [u.astype(np.float64) for u in ups], params=O.Params(bg=bg))
+    check_grad(grads.means.cpu().numpy(), rg["means"], "means, 64 views")
+    check_grad(dvm.cpu().numpy(), dRt, "dL/d(R,t), 64 views")
+    check_grad(dtw.cpu().numpy(), tw, "twist, 64 views")
+
+
 @pytest.mark.parametrize("case", ["clustered_sh3", "orbit_4views", "uneven_3scenes", "subset_view"])
 def test_projection_backward_staged_path_equals_per_thread_path(case, monkeypatch):
     """The degree-3 projection backward stages SH rows in and SH gradients
