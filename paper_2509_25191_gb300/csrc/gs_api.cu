@@ -274,6 +274,7 @@ int gs_rasterize_bwd(const gs_views *vw, const gs_config *cfg, const float *proj
         !b->ids)
         return GS_ERR_ARG;
     if (!aligned16(grad2d)) return GS_ERR_ARG;
+    (void)status;   // the raster backward reports nothing on the device
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_FLOATS * (size_t)L.n_slots, st) != cudaSuccess)
         return GS_ERR_CUDA;

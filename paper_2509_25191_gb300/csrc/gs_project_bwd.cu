@@ -610,6 +610,9 @@ int launch_l1(const float *image, const float *target, long long n, float *loss,
     const long long n4 = al ? n / 4 : 0;
     long long blocks = (n + 1023) / 1024;
     if (blocks > 8LL * num_sms()) blocks = 8LL * num_sms();
+    // grad4 and grad1 view the same buffer but address disjoint ranges (the
+    // float4 body [0, 4 n4) and the scalar tail [4 n4, n)), as do img/img1
+    // and tgt/tgt1, so the restrict qualifiers hold
     k_l1<<<(int)blocks, 256, 0, st>>>(reinterpret_cast<const float4 *>(image), reinterpret_cast<const float4 *>(target),
                                       n4, image, target, n, 1.f / (float)n, reinterpret_cast<float4 *>(grad), grad,
                                       loss);
