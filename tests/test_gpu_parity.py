@@ -141,7 +141,7 @@ def test_projection_parity(case):
 
 
 @pytest.mark.parametrize("case", ["clustered_sh3", "orbit_4views", "uneven_3scenes", "subset_view"])
-def test_projection_staged_path_equals_per_thread_path(case, monkeypatch):
+def test_projection_staged_path_equals_per_thread_path(case):
     """Degree 3 stages each full block's SH rows and records with tensor
     copies (swizzled boxes); blocks that straddle scenes, the tail block and
     the fallback read and write per thread. Both give the same records, bit
@@ -155,8 +155,7 @@ def test_projection_staged_path_equals_per_thread_path(case, monkeypatch):
     b = torch.full((n_slots, 16), float("nan"), device="cuda")
     status = _lib.new_status()
     _lib.gs_project(g, views, cfg, a, status)
-    monkeypatch.setenv("GS_DISABLE_TMA", "1")
-    _lib.gs_project(g, views, cfg, b, status)
+    _lib.gs_project(g, views, _lib.config(use_tma=False), b, status)
     torch.cuda.synchronize()
     assert int(status[0].item()) == 0
     A, B = a.cpu().numpy(), b.cpu().numpy()
@@ -416,7 +415,7 @@ def test_maximum_view_count_parity():
 
 
 @pytest.mark.parametrize("case", ["clustered_sh3", "orbit_4views", "uneven_3scenes", "subset_view"])
-def test_projection_backward_staged_path_equals_per_thread_path(case, monkeypatch):
+def test_projection_backward_staged_path_equals_per_thread_path(case):
     """The degree-3 projection backward stages SH rows in and SH gradients
     out with tensor copies for full blocks; partial blocks and the fallback
     go per thread. Same arithmetic in the same order: the raw-parameter
@@ -432,8 +431,8 @@ def test_projection_backward_staged_path_equals_per_thread_path(case, monkeypatc
     status = _lib.new_status()
     _lib.gs_rasterize_bwd(views, cfg, proj, rast.bins, image, up, grad2d, status)
     outs = []
-    for no_tma in ("0", "1"):
-        monkeypatch.setenv("GS_DISABLE_TMA", no_tma)
+    for use_tma in (True, False):
+        cfg = _lib.config(tile=rast.tile, use_tma=use_tma)
         gr = _lib.Grads(g.n, g.sh_degree, n_slots, vw.n)
         gr.grad2d = grad2d
         for t in (gr.means, gr.log_scales, gr.quats, gr.opacity_logits, gr.sh, gr.pose_partials):
@@ -461,31 +460,36 @@ def test_pose_only_backward_matches_full():
 
 def test_autograd_and_pose_residual_chain():
     """images -> L = <w, images>; gradients of the 6D/translation pose
-    residuals through torch match the oracle's dL/d(R,t) chained in FP64."""
+    residuals (away from the identity) through torch match the oracle's
+    dL/d(R', t') chained through the FP64 pose-residual oracle."""
+    import dataclasses
+
+    from oracle import pose as OP
     from paper_2509_25191_gb300 import pose
     from paper_2509_25191_gb300.autograd import RasterizeViews
     sc, vw = CASES["orbit_4views"]()
-    ref = oracle_forward(sc, vw)
-    ups = upstream(vw, ref, seed=5)
-    w = torch.as_tensor(np.concatenate([u.reshape(-1) for u in ups])).cuda()
+    rng = np.random.default_rng(21)
+    dr0 = (OP.identity_6d(vw.n) + 0.02 * rng.standard_normal((vw.n, 6))).astype(np.float32)
+    dt0 = (0.01 * rng.standard_normal((vw.n, 3))).astype(np.float32)
     base = torch.as_tensor(vw.viewmats).cuda()
-    dr = pose.identity_6d(vw.n, device="cuda").requires_grad_(True)
-    dt = torch.zeros(vw.n, 3, device="cuda", requires_grad=True)
+    dr = torch.as_tensor(dr0).cuda().requires_grad_(True)
+    dt = torch.as_tensor(dt0).cuda().requires_grad_(True)
     g = _lib.Gaussians.from_scene(sc)
     params = [t.clone().requires_grad_(True) for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.sh)]
     vm = pose.apply_residual(base, dr, dt)
+    # the oracle renders at the refined poses the GPU used (float32)
+    vw_ref = dataclasses.replace(vw, viewmats=vm.detach().cpu().numpy().astype(np.float32))
+    assert np.allclose(vw_ref.viewmats, OP.apply_residual(vw.viewmats, dr0, dt0), atol=1e-5)
+    ref = oracle_forward(sc, vw_ref)
+    ups = upstream(vw_ref, ref, seed=5)
+    w = torch.as_tensor(np.concatenate([u.reshape(-1) for u in ups])).cuda()
     layout = (vw.width, vw.height, vw.gauss_begin, vw.gauss_count)
     img = RasterizeViews.apply(*params, vm, torch.as_tensor(vw.intrinsics).cuda(), layout, Rasterizer())
     (img * w).sum().backward()
-    # oracle chain: dL/dR' from the oracle, then the same residual map in FP64 on CPU
-    _, dRt, _, _ = O.backward(sc, vw, ref, [u.astype(np.float64) for u in ups])
-    dr64 = pose.identity_6d(vw.n, dtype=torch.float64).requires_grad_(True)
-    dt64 = torch.zeros(vw.n, 3, dtype=torch.float64, requires_grad=True)
-    vm64 = pose.apply_residual(torch.as_tensor(vw.viewmats, dtype=torch.float64), dr64, dt64)
-    (vm64 * torch.as_tensor(dRt)).sum().backward()
-    check_grad(dr.grad.cpu().numpy(), dr64.grad.numpy(), "d(6D residual)")
-    check_grad(dt.grad.cpu().numpy(), dt64.grad.numpy(), "d(translation residual)")
-    rg, _, _, _ = O.backward(sc, vw, ref, [u.astype(np.float64) for u in ups])
+    rg, dRt, _, _ = O.backward(sc, vw_ref, ref, [u.astype(np.float64) for u in ups])
+    d_dr, d_dt = OP.residual_vjp(vw.viewmats, dr0, dt0, dRt)
+    check_grad(dr.grad.cpu().numpy(), d_dr, "d(6D residual)")
+    check_grad(dt.grad.cpu().numpy(), d_dt, "d(translation residual)")
     check_grad(params[0].grad.cpu().numpy(), rg["means"], "means via autograd")
 
 
