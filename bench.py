@@ -50,10 +50,10 @@ FP32_LANES_PER_SM = 128
 
 
 # DRAM traffic per launch of the raster backward (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of three launches of one ncu capture; command
-# and figures in profiles/k_render_bwd_single_view_1m.md). It holds only for
-# the kernel source it was measured on (hash of its two source files) and for
-# the default workload and tile; otherwise the bench reports null.
+# dram__bytes_write.sum, mean of three launches of one ncu capture of this
+# workload). It holds only for the kernel source it was measured on (hash of
+# its two source files) and for the default workload and tile; otherwise the
+# bench reports null.
 RASTER_BWD_TRAFFIC = {"bytes": 51968000, "sources_sha256_16": "99e3c618f09b48d9", "n": 1_000_000,
                       "tile": (32, 16)}
 
@@ -554,7 +554,7 @@ def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
         last["pose_grad_norm"] = float(torch.cat([dr.grad.reshape(-1), dt.grad.reshape(-1)]).norm())
         groups = [(p, gr, m, v, lr) for p, gr, (m, v), lr in zip(gp, gg, mom, lrs)]
         _lib.gs_sgld_adam_step(groups, k + 1, noise=noise[k % 4], noise_scale=1e-4, noise_group=0)
-        lr_pose = 1e-4 * 0.1 ** (k / 30000.0)           # pose lr 1e-4 decayed exponentially to x0.1
+        lr_pose = pose.pose_lr(k)                       # Section 4.1: 1e-4 decayed exponentially to x0.1
         _lib.gs_sgld_adam_step([(dr.data, dr.grad, pose_m[0][0], pose_m[0][1], lr_pose),
                                 (dt.data, dt.grad, pose_m[1][0], pose_m[1][1], lr_pose)], k + 1)
         dr.grad.zero_()

@@ -18,8 +18,8 @@
  *   - All functions return int: GS_OK (0) or a gs_status code. No exception
  *     or abort crosses the ABI. gs_error_string() names a code.
  *   - Buffers marked DEVICE are device pointers owned by the caller; the
- *     library never allocates, frees or synchronises. Buffers marked HOST are
- *     read during the call only.
+ *     library never allocates or frees, and only gs_status_read waits for
+ *     the device. Buffers marked HOST are read during the call only.
  *   - Work is enqueued on the caller's stream (a cudaStream_t passed as
  *     void*; NULL = legacy default stream). Given the same host arguments,
  *     the enqueued work is the same on every call, so a call sequence can be
@@ -28,14 +28,14 @@
  *     enqueued; a failed launch returns GS_ERR_CUDA. Conditions found on the
  *     device (instance capacity exceeded) are written to the caller's DEVICE
  *     status word int32[4] = {code, detail_lo, detail_hi, 0}; the caller reads
- *     it at a point of its choosing. Kernels never trap; the only waits
- *     are the projection kernels' bounded waits for their own tensor copies
- *     (GS_ERR_TIMEOUT if one runs out; gs_check_bounded_wait makes one run
- *     out on purpose, for tests of this path).
- *   - The enqueued work also depends on the environment variable
- *     GS_DISABLE_TMA, read at each call: "1" makes the projection kernels
- *     read and write per thread instead of staging through tensor copies
- *     (the same results, bit for bit; the tests compare the two).
+ *     it at a point of its choosing (gs_status_read). Kernels never trap; the
+ *     only waits are the projection kernels' bounded waits for their own
+ *     tensor copies (GS_ERR_TIMEOUT if one runs out; gs_check_bounded_wait
+ *     makes one run out on purpose, for tests of this path). When the status
+ *     word is non-zero after a call, that call's outputs are undefined.
+ *   - The enqueued work depends only on the arguments: no environment
+ *     variable or global setting steers it (gs_config.use_tma selects the
+ *     projection kernels' staging).
  *   - float32 everywhere. Quaternions are (w,x,y,z). Cameras are
  *     world->camera rigid transforms with OpenCV axes (x right, y down,
  *     z forward); a pixel (u,v) has its centre at (u+0.5, v+0.5).
@@ -80,6 +80,12 @@ typedef struct gs_config {
     float bg[3];          /* [0,0,0] background colour */
     int count_pairs;      /* [0] if nonzero, the raster backward also counts the pixel-Gaussian pairs it
                              evaluates and composites into bins->counters (diagnostics; costs time) */
+    int accumulate_grads; /* [0] 0: the backward overwrites the raw-parameter gradients (gs_grads.means ..
+                             .sh); nonzero: it adds to them (+=), so gradients of several calls (views,
+                             losses) sum in the caller's buffers, which the caller zeroes first */
+    int use_tma;          /* [1] nonzero: the projection kernels stage degree-3 SH rows, records and
+                             gradient rows by tensor copies where the layout allows; 0: per-thread loads
+                             and stores. The results are the same bit for bit. */
 } gs_config;
 
 /* Gaussians (all DEVICE, float32, contiguous). Several scenes may be
@@ -120,12 +126,19 @@ typedef struct gs_bins {
     int32_t *counters;    /* [GS_NUM_COUNTERS] scratch; counters[0] = instances after the call;
                              int64 at counters+8: pixel-Gaussian pairs evaluated by gs_render_fwd,
                              +10: composited by it, +12/+14: the same for gs_rasterize_bwd */
+    int32_t *last_contrib;/* optional [sum_v H_v W_v] (NULL = not kept): per pixel (view v's pixel
+                             (u, y) at gs_pixel_base(v)/3 + y W_v + u), one past the instance index
+                             (into keys/ids) of the last Gaussian gs_render_fwd composited there (the
+                             tile's start if none). gs_render_fwd writes it; gs_rasterize_bwd, given the
+                             same bins, then stops each pixel there instead of replaying its list to
+                             the end. 4 bytes per pixel: an index, not a stored transmittance. */
 } gs_bins;
 #define GS_NUM_COUNTERS 16
 
 /* Gradient outputs of gs_render_bwd (all DEVICE). The parameter gradients are
- * OVERWRITTEN (not accumulated). grad2d and pose_partials are caller-owned
- * scratch that also remain readable after the call. */
+ * overwritten, or accumulated (+=) when gs_config.accumulate_grads is set.
+ * grad2d and pose_partials are caller-owned scratch that also remain
+ * readable after the call. */
 typedef struct gs_grads {
     float *means;          /* [n,3] */
     float *log_scales;     /* [n,3] */
@@ -155,6 +168,31 @@ int64_t gs_pixel_base(const gs_views *views, int v);
 /* Blocks of the projection-backward grid for n Gaussians (pose partials). */
 int gs_pose_blocks(int64_t n);
 
+/* One caller buffer for every scratch array of a forward + backward step over
+ * these views: the tile lists of gs_bins (tile_ranges, keys, ids, keys_tmp,
+ * tile_order, tile_scratch, counters, last_contrib for `capacity` tile
+ * instances) and the backward's grad2d [P,12] and pose_partials [V,
+ * gs_pose_blocks(n_gaussians), 12]. gs_workspace_size returns its size in
+ * bytes (0 for invalid arguments); gs_workspace_carve fills bins (all of its
+ * fields) and grads->grad2d, grads->pose_partials with 256-byte aligned
+ * pieces of ws (DEVICE, ws_bytes >= gs_workspace_size(...), 256-byte
+ * aligned); the parameter-gradient pointers of grads are left as they are.
+ * Both are host arithmetic only (nothing is enqueued or touched on the
+ * device). The instance count of a step is known after gs_bin_sort
+ * (counters[0]; GS_ERR_CAPACITY in the status word if capacity was too
+ * small). */
+size_t gs_workspace_size(const gs_views *views, const gs_config *cfg, int64_t n_gaussians, int64_t capacity);
+int gs_workspace_carve(const gs_views *views, const gs_config *cfg, int64_t n_gaussians, int64_t capacity,
+                       void *ws, size_t ws_bytes, gs_bins *bins, gs_grads *grads);
+
+/* Copy the DEVICE status word int32[4] to host_status (HOST int32[4]) once
+ * the work enqueued on `stream` so far has finished: the one entry point
+ * that synchronises (the caller's chosen sync point; not capturable). Returns
+ * GS_ERR_CUDA if the copy or the wait fails; host_status[0] is then the
+ * status code the kernels left (GS_OK, GS_ERR_CAPACITY with the needed
+ * instance count in host_status[1..2], GS_ERR_OVERFLOW or GS_ERR_TIMEOUT). */
+int gs_status_read(const int32_t *status, int32_t *host_status, void *stream);
+
 /* ---------------- the rasterizer ---------------- */
 
 /* Project every Gaussian into every view that sees it (Section 3.1
@@ -178,10 +216,10 @@ int gs_pose_blocks(int64_t n);
  *                       channel c was clamped.
  * Culled records are all zero.
  * proj: DEVICE [P,16], 16-byte aligned. status: DEVICE int32[4] or NULL;
- * the degree-3 path stages each block's SH rows and records with tensor
- * copies, and if a bounded wait for one runs out (a copy that never lands)
- * it sets status = {GS_ERR_TIMEOUT, block} and leaves that block's records
- * unwritten. */
+ * with cfg->use_tma the degree-3 path stages each block's SH rows and
+ * records with tensor copies, and if a bounded wait for one runs out (a copy
+ * that never lands) it sets status = {GS_ERR_TIMEOUT, block} and leaves that
+ * block's records unwritten. */
 int gs_project(const gs_gaussians *g, const gs_views *views, const gs_config *cfg,
                float *proj, int32_t *status, void *stream);
 
@@ -196,8 +234,9 @@ int gs_bin_sort(const gs_views *views, const gs_config *cfg, const float *proj,
                 const gs_bins *bins, int32_t *status, void *stream);
 
 /* Composite every pixel front to back (Section 3.1 alpha blending) and
- * write image: DEVICE [sum_v 3 H_v W_v] (view layout as gs_pixel_base). If a
- * capacity error is pending in counters, images are filled with zeros. */
+ * write image: DEVICE [sum_v 3 H_v W_v] (view layout as gs_pixel_base), and
+ * bins->last_contrib if it is set. If a capacity error is pending in
+ * counters, images are filled with zeros. */
 int gs_render_fwd(const gs_views *views, const gs_config *cfg, const float *proj,
                   const gs_bins *bins, float *image, int32_t *status, void *stream);
 
@@ -214,12 +253,17 @@ int gs_render_bwd(const gs_gaussians *g, const gs_views *views, const gs_config 
 
 /* The two stages of gs_render_bwd, callable separately (same arguments and
  * semantics as there). gs_rasterize_bwd zeroes grad2d [P,12] and adds the
- * per-slot 2D gradients (layout as gs_grads.grad2d); gs_project_bwd chains
- * grad2d to the raw parameters and the pose partials. With degree-3 SH and
- * want_gaussian_grads, gs_project_bwd stages each block's SH rows, first-view
+ * per-slot 2D gradients (layout as gs_grads.grad2d); if bins->last_contrib is
+ * set it must hold what gs_render_fwd wrote for this image with these bins,
+ * and each pixel's replay ends at its last composited Gaussian (the result is
+ * the same as without it). gs_project_bwd chains grad2d to the raw
+ * parameters (overwritten, or added with cfg->accumulate_grads) and the pose
+ * partials (always overwritten). With degree-3 SH, want_gaussian_grads and
+ * cfg->use_tma, gs_project_bwd stages each block's SH rows, first-view
  * 2D-gradient rows and SH-gradient rows by tensor copies (grads->sh must then
  * be 16-byte aligned, else the per-thread path runs); a bounded wait for one
- * that runs out sets status = {GS_ERR_TIMEOUT, block}. */
+ * that runs out sets status = {GS_ERR_TIMEOUT, block}, and that block writes
+ * zero pose partials. */
 int gs_rasterize_bwd(const gs_views *views, const gs_config *cfg, const float *proj, const gs_bins *bins,
                      const float *image, const float *dL_dimage, float *grad2d, int32_t *status,
                      void *stream);
@@ -411,11 +455,15 @@ int gs_ga_weights(const float *dist, int64_t n, int n_bins, double alpha, uint32
  * process exits. The pose partials of one call need V * gs_pose_blocks(n) *
  * 12 floats; a call beyond that returns GS_ERR_TOO_LARGE before enqueuing
  * anything. Every call shares the one array and leaves its contents behind
- * (each call overwrites all the partials it reads, so nothing needs
- * clearing): calls that overlap on the GPU (other streams, other host
- * threads on the same device) race and must be serialised by the caller.
- * The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture. */
+ * (each call overwrites all the partials it reads, a block whose bounded
+ * copy wait runs out with zeros, so nothing needs clearing; the outputs of
+ * a call that sets the status word are undefined): calls that overlap on
+ * the GPU (other streams, other host threads on the same device) race and
+ * must be serialised by the caller. An uncaptured call looks up the array's
+ * device address with the current device's context (so a context that was
+ * destroyed and created again is followed); a call made while its stream is
+ * being captured uses the address the last uncaptured call on that device
+ * found, so make one uncaptured call on each device before any capture. */
 #define GS_NOALLOC_MAX_BLOCKS 1024
 #define GS_NOALLOC_POSE_FLOATS (GS_MAX_VIEWS * GS_NOALLOC_MAX_BLOCKS * 12)
 int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *views, const gs_config *cfg, const float *proj,

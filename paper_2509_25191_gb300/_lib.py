@@ -26,7 +26,7 @@ EXPORTED = ["gs_config_default", "gs_num_slots", "gs_slot_base", "gs_num_tiles",
             "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version",
             "gs_project_bwd_noalloc", "gs_sgld_adam_step", "gs_ga_select_pairs", "gs_ga_incidence",
             "gs_ga_epipolar", "gs_ga_weights_scratch_bytes", "gs_ga_weights", "gs_ga_step", "gs_l1_dssim_loss",
-            "gs_check_bounded_wait"]
+            "gs_check_bounded_wait", "gs_workspace_size", "gs_workspace_carve", "gs_status_read"]
 GS_GA_MAX_CAMS = 8192
 GS_GA_PAIR_FLOATS = 12
 GS_GA_MAX_BINS = 16384
@@ -43,7 +43,8 @@ class gs_config(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("pixel_gate", ctypes.c_int),
                 ("near_z", ctypes.c_float), ("dilation", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float), ("fov_clamp", ctypes.c_float),
-                ("bg", ctypes.c_float * 3), ("count_pairs", ctypes.c_int)]
+                ("bg", ctypes.c_float * 3), ("count_pairs", ctypes.c_int), ("accumulate_grads", ctypes.c_int),
+                ("use_tma", ctypes.c_int)]
 
 
 class gs_gaussians(ctypes.Structure):
@@ -61,7 +62,7 @@ class gs_views(ctypes.Structure):
 class gs_bins(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int64), ("tile_ranges", ctypes.c_void_p), ("keys", ctypes.c_void_p),
                 ("ids", ctypes.c_void_p), ("keys_tmp", ctypes.c_void_p), ("tile_order", ctypes.c_void_p),
-                ("tile_scratch", ctypes.c_void_p), ("counters", ctypes.c_void_p)]
+                ("tile_scratch", ctypes.c_void_p), ("counters", ctypes.c_void_p), ("last_contrib", ctypes.c_void_p)]
 
 
 class gs_adam_group(ctypes.Structure):
@@ -106,6 +107,10 @@ def load():
         getattr(lib, name).restype = ctypes.c_int64
     lib.gs_error_string.restype = ctypes.c_char_p
     lib.gs_ga_weights_scratch_bytes.restype = ctypes.c_size_t
+    lib.gs_workspace_size.restype = ctypes.c_size_t
+    lib.gs_workspace_size.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]
+    lib.gs_workspace_carve.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]
     _lib = lib
     return lib
 
@@ -140,7 +145,8 @@ def _stream(stream):
 # ---------------------------------------------------------------------------
 
 def config(tile=(16, 16), pixel_gate=True, bg=(0.0, 0.0, 0.0), near=0.2, dilation=0.3,
-           alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, fov_clamp=1.3, count_pairs=False) -> gs_config:
+           alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, fov_clamp=1.3, count_pairs=False,
+           accumulate_grads=False, use_tma=True) -> gs_config:
     c = gs_config()
     load().gs_config_default(ctypes.byref(c))
     c.tile_w, c.tile_h = int(tile[0]), int(tile[1])
@@ -149,6 +155,8 @@ def config(tile=(16, 16), pixel_gate=True, bg=(0.0, 0.0, 0.0), near=0.2, dilatio
         near, dilation, alpha_min, alpha_max, t_min, fov_clamp
     c.bg = (ctypes.c_float * 3)(*bg)
     c.count_pairs = int(bool(count_pairs))
+    c.accumulate_grads = int(bool(accumulate_grads))
+    c.use_tma = int(bool(use_tma))
     return c
 
 
@@ -224,10 +232,12 @@ class Views:
 
 
 class Bins:
-    """Caller-owned tile-list buffers (device)."""
+    """Caller-owned tile-list buffers (device). With pixels > 0 the per-pixel
+    last-contributor record is kept too (the forward writes it, the backward
+    ends each pixel's replay there)."""
 
-    def __init__(self, n_tiles, capacity, device="cuda"):
-        self.n_tiles, self.capacity = int(n_tiles), int(capacity)
+    def __init__(self, n_tiles, capacity, device="cuda", pixels=0):
+        self.n_tiles, self.capacity, self.pixels = int(n_tiles), int(capacity), int(pixels)
         i32 = dict(dtype=torch.int32, device=device)
         self.tile_ranges = torch.empty(max(1, self.n_tiles) * 2, **i32)
         self.tile_order = torch.empty(max(1, self.n_tiles), **i32)
@@ -237,10 +247,14 @@ class Bins:
         self.keys = torch.empty(cap, dtype=torch.int64, device=device)
         self.keys_tmp = torch.empty(cap, dtype=torch.int64, device=device)
         self.ids = torch.empty(cap, dtype=torch.int32, device=device)
+        self.last_contrib = torch.empty(self.pixels, **i32) if self.pixels > 0 else None
 
-    def c(self) -> gs_bins:
+    def c(self, last=True) -> gs_bins:
+        """The C struct; last=False leaves the last-contributor record out
+        (NULL), e.g. for a backward whose forward wrote another image."""
         return gs_bins(self.capacity, _ptr(self.tile_ranges), _ptr(self.keys), _ptr(self.ids), _ptr(self.keys_tmp),
-                       _ptr(self.tile_order), _ptr(self.tile_scratch), _ptr(self.counters))
+                       _ptr(self.tile_order), _ptr(self.tile_scratch), _ptr(self.counters),
+                       _ptr(self.last_contrib) if last else None)
 
 
 class Grads:
@@ -288,17 +302,18 @@ def gs_render_fwd(views: Views, cfg: gs_config, proj, bins: Bins, image, status=
 
 
 def gs_render_bwd(g: Gaussians, views: Views, cfg: gs_config, proj, bins: Bins, image, dL_dimage, grads: Grads,
-                  want_gaussian_grads=True, status=None, stream=None):
+                  want_gaussian_grads=True, status=None, stream=None, use_last=True):
     _check(load().gs_render_bwd(ctypes.byref(g.c()), ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj),
-                                ctypes.byref(bins.c()), _ptr(image), _ptr(dL_dimage), ctypes.byref(grads.c()),
-                                int(bool(want_gaussian_grads)), _ptr(status), _stream(stream)), "gs_render_bwd")
+                                ctypes.byref(bins.c(use_last)), _ptr(image), _ptr(dL_dimage),
+                                ctypes.byref(grads.c()), int(bool(want_gaussian_grads)), _ptr(status),
+                                _stream(stream)), "gs_render_bwd")
 
 
 def gs_rasterize_bwd(views: Views, cfg: gs_config, proj, bins: Bins, image, dL_dimage, grad2d, status=None,
-                     stream=None):
-    _check(load().gs_rasterize_bwd(ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj), ctypes.byref(bins.c()),
-                                   _ptr(image), _ptr(dL_dimage), _ptr(grad2d), _ptr(status), _stream(stream)),
-           "gs_rasterize_bwd")
+                     stream=None, use_last=True):
+    _check(load().gs_rasterize_bwd(ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj),
+                                   ctypes.byref(bins.c(use_last)), _ptr(image), _ptr(dL_dimage), _ptr(grad2d),
+                                   _ptr(status), _stream(stream)), "gs_rasterize_bwd")
 
 
 def gs_project_bwd(g: Gaussians, views: Views, cfg: gs_config, proj, grads: Grads, want_gaussian_grads=True,
@@ -410,6 +425,32 @@ def gs_l1_dssim_loss(views: Views, image, target, loss, dL_dimage, lam=0.2, stre
     gradient, views concatenated [3,H,W] each."""
     _check(load().gs_l1_dssim_loss(ctypes.byref(views.c()), _ptr(image), _ptr(target), ctypes.c_float(lam),
                                    _ptr(loss), _ptr(dL_dimage), _stream(stream)), "gs_l1_dssim_loss")
+
+
+def gs_workspace_size(views: Views, cfg: gs_config, n_gaussians, capacity):
+    """Bytes of the one-buffer step workspace (tile lists, 2D gradients, pose
+    partials); host arithmetic only."""
+    return int(load().gs_workspace_size(ctypes.byref(views.c()), ctypes.byref(cfg), int(n_gaussians),
+                                        int(capacity)))
+
+
+def gs_workspace_carve(views: Views, cfg: gs_config, n_gaussians, capacity, ws_ptr, ws_bytes):
+    """(gs_bins, grad2d address, pose_partials address) carved from the
+    workspace at device address ws_ptr (host arithmetic only)."""
+    b = gs_bins()
+    gr = gs_grads()
+    _check(load().gs_workspace_carve(ctypes.byref(views.c()), ctypes.byref(cfg), int(n_gaussians), int(capacity),
+                                     ctypes.c_void_p(ws_ptr), ctypes.c_size_t(ws_bytes), ctypes.byref(b),
+                                     ctypes.byref(gr)), "gs_workspace_carve")
+    return b, gr.grad2d, gr.pose_partials
+
+
+def gs_status_read(status, stream=None):
+    """The device status word as 4 host ints, after the stream's work so far
+    (the library's one synchronising call)."""
+    out = (ctypes.c_int32 * 4)()
+    _check(load().gs_status_read(_ptr(status), out, _stream(stream)), "gs_status_read")
+    return list(out)
 
 
 def gs_check_bounded_wait(status, stream=None):

@@ -26,6 +26,8 @@ import torch
 from . import _lib
 from ._lib import Bins, Gaussians, Grads, Views
 
+INSTANCE_LIMIT = 0x7fffffff   # the instance count saturates here (32-bit tile ranges)
+
 
 class Rasterizer:
     def __init__(self, tile=(16, 16), pixel_gate=True, bg=(0.0, 0.0, 0.0), capacity_headroom=1.3, **kw):
@@ -42,8 +44,9 @@ class Rasterizer:
     # ------------------------------------------------------------------
     def _ensure_bins(self, views: Views, capacity: int, device):
         T = views.num_tiles(self.cfg)
-        if self.bins is None or self.bins.n_tiles != T or self.bins.capacity < capacity:
-            self.bins = Bins(T, capacity, device)
+        if (self.bins is None or self.bins.n_tiles != T or self.bins.capacity < capacity or
+                self.bins.pixels != views.pixels):
+            self.bins = Bins(T, capacity, device, pixels=views.pixels)
         if self.status is None or self.status.device != torch.device(device):
             self.status = _lib.new_status(device)
         return self.bins
@@ -65,17 +68,22 @@ class Rasterizer:
         dev = proj.device
         if self.bins is None:
             self._ensure_bins(views, max(1024, 4 * views.num_slots()), dev)
-        elif self.bins.n_tiles != views.num_tiles(self.cfg):
+        elif self.bins.n_tiles != views.num_tiles(self.cfg) or self.bins.pixels != views.pixels:
             self._ensure_bins(views, self.bins.capacity, dev)
         _lib.gs_bin_sort(views, self.cfg, proj, self.bins, self.status)
         self.generation += 1
         if not self.fixed_capacity:
             n = int(self.bins.counters[0].item())   # the one readback of the uncaptured path
             self.last_instances = n
+            if n >= INSTANCE_LIMIT:
+                # the count saturates at 2^31 - 1: more instances than the
+                # 32-bit tile ranges can address; growing cannot help
+                raise _lib.GsError(_lib.GS_ERR_OVERFLOW, f"gs_bin_sort ({n} or more tile instances)")
             if n > self.bins.capacity:
                 self.status.zero_()
                 self._ensure_bins(views, int(math.ceil(n * self.headroom)) + 1024, dev)
                 _lib.gs_bin_sort(views, self.cfg, proj, self.bins, self.status)
+                self.check_status()   # the re-bin must fit (it reads the status word once)
         return self.bins
 
     def render(self, views: Views, proj, bins: Bins, image=None):
@@ -98,10 +106,13 @@ class Rasterizer:
         return self._grads[1]
 
     def backward(self, g: Gaussians, views: Views, proj, image, dL_dimage, want_gaussian_grads=True,
-                 grads: Grads = None):
+                 grads: Grads = None, use_last=True):
+        """use_last=False when the tile lists were rebuilt after another
+        forward wrote the last-contributor record (the replay then runs to
+        saturation instead; the same gradients)."""
         grads = grads or self.grads_buffers(g, views, want_gaussian_grads)
         _lib.gs_render_bwd(g, views, self.cfg, proj, self.bins, image, dL_dimage, grads, want_gaussian_grads,
-                           self.status)
+                           self.status, use_last=use_last)
         dvm = torch.empty(views.n, 12, dtype=torch.float32, device=proj.device)
         dtw = torch.empty(views.n, 6, dtype=torch.float32, device=proj.device)
         _lib.gs_pose_grad(views, grads.pose_partials, grads.n_blocks, dvm, dtw)
@@ -134,12 +145,15 @@ class RasterizeViews(torch.autograd.Function):
     @staticmethod
     def backward(ctx, dL_dimage):
         (image,) = ctx.saved_tensors
-        if ctx.rast.generation != ctx.generation:
+        own = ctx.rast.generation == ctx.generation
+        if not own:
             # the rasterizer has binned another forward since: rebuild this
-            # forward's tile lists from its projected records (same lists)
+            # forward's tile lists from its projected records (same lists);
+            # the last-contributor record is the other forward's, so the
+            # replay runs without it
             ctx.rast.bin_sort(ctx.views, ctx.proj)
         grads, dvm, _ = ctx.rast.backward(ctx.g, ctx.views, ctx.proj, image, dL_dimage.contiguous(),
-                                          want_gaussian_grads=ctx.want_gauss)
+                                          want_gaussian_grads=ctx.want_gauss, use_last=own)
         if ctx.want_gauss:
             out = [grads.means.clone(), grads.log_scales.clone(), grads.quats.clone(),
                    grads.opacity_logits.clone(), grads.sh.clone()]

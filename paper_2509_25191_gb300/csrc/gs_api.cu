@@ -1,6 +1,7 @@
 // extern "C" entry points of libgsplat_gb300.so (declared in include/gs.h):
 // host-side argument checks, the per-call launch description, and dispatch
-// to the kernels. No allocation, no synchronisation.
+// to the kernels. No allocation; the one synchronising call is
+// gs_status_read.
 #include <math.h>
 #include <string.h>
 
@@ -112,6 +113,8 @@ static int build_launch(const gs_views *vw, const gs_config *cfg, Launch &L) {
     L.fov_clamp = cfg->fov_clamp;
     L.bg[0] = cfg->bg[0]; L.bg[1] = cfg->bg[1]; L.bg[2] = cfg->bg[2];
     L.count_pairs = cfg->count_pairs != 0;
+    L.accumulate = cfg->accumulate_grads != 0;
+    L.use_tma = cfg->use_tma != 0;
     if (!(L.alpha_max > 0.f && L.alpha_max < 1.f) || !(L.t_min > 0.f)) return GS_ERR_ARG;
     long long slot = 0, pix = 0, tiles = 0;
     for (int v = 0; v < V; ++v) {
@@ -186,6 +189,8 @@ void gs_config_default(gs_config *cfg) {
     cfg->fov_clamp = 1.3f;
     cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.0f;
     cfg->count_pairs = 0;
+    cfg->accumulate_grads = 0;
+    cfg->use_tma = 1;
 }
 
 int64_t gs_num_slots(const gs_views *vw) {
@@ -230,6 +235,65 @@ int64_t gs_pixel_base(const gs_views *vw, int v) {
 }
 
 int gs_pose_blocks(int64_t n) { return pose_blocks(n); }
+
+// Pieces of the step workspace, in this order, each at a 256-byte boundary.
+static size_t ws_layout(const gs_views *vw, const gs_config *cfg, int64_t n, int64_t cap, size_t off[10]) {
+    if (!vw || !cfg || vw->n_views < 1 || vw->n_views > GS_MAX_VIEWS || !vw->width || !vw->height ||
+        !vw->gauss_count || n < 0 || cap < 0 || cfg->tile_w < 1 || cfg->tile_h < 1)
+        return 0;
+    const int64_t T = gs_num_tiles(vw, cfg), P = gs_num_slots(vw), px = gs_num_image_floats(vw) / 3;
+    const int64_t c = cap > 0 ? cap : 1;
+    const size_t sizes[10] = {
+        sizeof(int32_t) * 2 * (size_t)(T > 0 ? T : 1),           // tile_ranges
+        sizeof(uint64_t) * (size_t)c,                            // keys
+        sizeof(uint32_t) * (size_t)c,                            // ids
+        sizeof(uint64_t) * (size_t)c,                            // keys_tmp
+        sizeof(int32_t) * (size_t)(T > 0 ? T : 1),               // tile_order
+        sizeof(int32_t) * (size_t)(T > 0 ? T : 1),               // tile_scratch
+        sizeof(int32_t) * GS_NUM_COUNTERS,                       // counters
+        sizeof(int32_t) * (size_t)(px > 0 ? px : 1),             // last_contrib
+        sizeof(float) * GS_GRAD2D_FLOATS * (size_t)(P > 0 ? P : 1),                      // grad2d
+        sizeof(float) * 12 * (size_t)vw->n_views * (size_t)pose_blocks(n)};              // pose_partials
+    size_t at = 0;
+    for (int k = 0; k < 10; ++k) {
+        off[k] = at;
+        at += (sizes[k] + 255) & ~(size_t)255;
+    }
+    return at;
+}
+
+size_t gs_workspace_size(const gs_views *vw, const gs_config *cfg, int64_t n_gaussians, int64_t capacity) {
+    size_t off[10];
+    return ws_layout(vw, cfg, n_gaussians, capacity, off);
+}
+
+int gs_workspace_carve(const gs_views *vw, const gs_config *cfg, int64_t n_gaussians, int64_t capacity, void *ws,
+                       size_t ws_bytes, gs_bins *bins, gs_grads *grads) {
+    size_t off[10];
+    const size_t need = ws_layout(vw, cfg, n_gaussians, capacity, off);
+    if (!need || !ws || ws_bytes < need || ((uintptr_t)ws & 255u) || !bins || !grads) return GS_ERR_ARG;
+    char *b = static_cast<char *>(ws);
+    bins->capacity = capacity;
+    bins->tile_ranges = reinterpret_cast<int32_t *>(b + off[0]);
+    bins->keys = reinterpret_cast<uint64_t *>(b + off[1]);
+    bins->ids = reinterpret_cast<uint32_t *>(b + off[2]);
+    bins->keys_tmp = reinterpret_cast<uint64_t *>(b + off[3]);
+    bins->tile_order = reinterpret_cast<int32_t *>(b + off[4]);
+    bins->tile_scratch = reinterpret_cast<int32_t *>(b + off[5]);
+    bins->counters = reinterpret_cast<int32_t *>(b + off[6]);
+    bins->last_contrib = reinterpret_cast<int32_t *>(b + off[7]);
+    grads->grad2d = reinterpret_cast<float *>(b + off[8]);
+    grads->pose_partials = reinterpret_cast<float *>(b + off[9]);
+    return GS_OK;
+}
+
+int gs_status_read(const int32_t *status, int32_t *host_status, void *stream) {
+    if (!status || !host_status) return GS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(host_status, status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return GS_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
 
 int gs_project(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, float *proj, int32_t *status,
                void *stream) {
@@ -294,7 +358,7 @@ int gs_project_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *c
         return GS_ERR_ARG;
     if (!aligned16(grad2d) || (want_gaussian_grads && g->n > 0 && !aligned16(out->quats))) return GS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (want_gaussian_grads) {
+    if (want_gaussian_grads && !L.accumulate) {
         // Gaussians outside every view's range still get (zero) gradients
         long long covered = 0;
         for (int a = 0; a < L.n_scenes; ++a) covered += L.s[a].g_count;
@@ -456,18 +520,25 @@ static __device__ __align__(256) float g_noalloc_pose[GS_NOALLOC_POSE_FLOATS];
 
 namespace {
 std::mutex g_noalloc_mu;
-float *g_noalloc_ptr[64];   // device address of g_noalloc_pose, per device
+float *g_noalloc_ptr[64];   // device address of g_noalloc_pose found by the last uncaptured call, per device
 
-// Host code cannot use the array's name as a device address; look the
-// address up once per device, with that device current.
-int noalloc_scratch(float **out) {
+// Host code cannot use the array's name as a device address; its address is
+// looked up with the device current. An uncaptured call looks it up every
+// time (the module, and with it the array, may have moved if the context was
+// destroyed and created again); a call whose stream is being captured cannot
+// load modules, so it uses the address the last uncaptured call found.
+int noalloc_scratch(cudaStream_t st, float **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GS_ERR_CUDA;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return GS_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_pose) != cudaSuccess || !p) return GS_ERR_CUDA;
         g_noalloc_ptr[dev] = static_cast<float *>(p);
+    } else if (!g_noalloc_ptr[dev]) {
+        return GS_ERR_CUDA;   // no uncaptured call on this device yet
     }
     *out = g_noalloc_ptr[dev];
     return GS_OK;
@@ -489,10 +560,10 @@ extern "C" int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *vw,
     if (!aligned16(grad2d) || (want_gaussian_grads && g->n > 0 && !aligned16(grads->quats))) return GS_ERR_ARG;
     const int nblk = pose_blocks(g->n);
     if ((long long)L.n_views * nblk * 12 > (long long)GS_NOALLOC_POSE_FLOATS) return GS_ERR_TOO_LARGE;
-    float *scratch = nullptr;
-    if ((rc = noalloc_scratch(&scratch))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    if (want_gaussian_grads) {
+    float *scratch = nullptr;
+    if ((rc = noalloc_scratch(st, &scratch))) return rc;
+    if (want_gaussian_grads && !L.accumulate) {
         long long covered = 0;
         for (int a = 0; a < L.n_scenes; ++a) covered += L.s[a].g_count;
         if (covered != g->n && g->n > 0) {

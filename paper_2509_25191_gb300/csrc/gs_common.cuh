@@ -37,6 +37,8 @@ struct Launch {
     int n_tiles;            // T
     int pixel_gate;
     int count_pairs;        // the raster backward also counts pixel-Gaussian pairs
+    int accumulate;         // the projection backward adds to the parameter gradients
+    int use_tma;            // the projection kernels may stage through tensor copies
     float near_z, dilation, alpha_min, alpha_max, t_min, fov_clamp;
     float bg[3];
     ViewDesc v[GS_MAX_VIEWS];

@@ -15,7 +15,6 @@
 // bounding box has half-extents sqrt(k Sigma'_xx), sqrt(k Sigma'_yy); they are
 // clipped to the radius and enlarged by 2^-14 relative so that float32
 // rounding never shrinks the region. A Gaussian with k <= 0 is culled.
-#include <stdlib.h>
 #include <string.h>
 
 #include "gs_common.cuh"
@@ -270,9 +269,8 @@ int launch_project(const Launch &L, int deg, const gs_gaussians *g, const float 
     memset(&ma, 0, sizeof ma); memset(&mb, 0, sizeof mb); memset(&mp, 0, sizeof mp);
     // degree 3 with 16-byte aligned SH rows and int32 row coordinates: the
     // staged path; anything else reads and writes per thread (also when the
-    // environment sets GS_DISABLE_TMA=1, which the tests use to compare the two)
-    const char *no_tma = getenv("GS_DISABLE_TMA");
-    const bool tma = deg == 3 && !(no_tma && no_tma[0] == '1') && ((uintptr_t)g->sh & 15u) == 0 &&
+    // configuration turns tensor copies off, which the tests use to compare the two)
+    const bool tma = deg == 3 && L.use_tma && ((uintptr_t)g->sh & 15u) == 0 &&
                      ((uintptr_t)proj & 15u) == 0 &&
                      L.n_slots < 0x7fffffffLL && g->n < 0x7fffffffLL &&
                      encode_tmap_2d(&ma, g->sh, 48, (uint64_t)g->n, 192, 32, PF_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&

@@ -3,7 +3,8 @@
 //
 // One thread per Gaussian (fixed grid, grid-stride), looping over the views of
 // its scene: the Gaussian's parameters are read once, its gradients are summed
-// over views in registers and written once (overwrite). For degree-3 SH the
+// over views in registers and written once (overwritten, or added to the
+// caller's values when the configuration accumulates). For degree-3 SH the
 // block's SH rows and first-view 2D-gradient rows arrive by tensor copies and
 // its SH-coefficient gradients leave by tensor stores (see PbStage). Each view's pose
 // gradient (dL/dR, dL/dt; Section 3.4 needs it for the pose residuals) is
@@ -18,7 +19,6 @@
 //   tangent), mean2D = f x / z + c, m = R_v mu + t_v, Sigma = M M^T with
 //   M = R(q) diag(exp l), q normalised, o = sigmoid, colour = max(0,
 //   sum f_k Y_k(d) + 0.5), d = normalise(mu - C_v), C_v = -R_v^T t_v.
-#include <stdlib.h>
 #include <string.h>
 
 #include "gs_common.cuh"
@@ -26,6 +26,9 @@
 namespace gsk {
 
 constexpr int PB_THREADS = 128;   // 128 registers: 4 blocks per SM, no spills
+
+// a parameter gradient: written (overwrite) or added to the caller's value
+__device__ __forceinline__ void put(float *p, float v, bool acc) { *p = acc ? *p + v : v; }
 constexpr int PB_WARPS = PB_THREADS / 32;
 
 // Staging of a block's 128 Gaussians on the degree-3 path: the SH rows arrive
@@ -93,16 +96,23 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                 row0 = (int)(L.s[s0].g_begin + base - L.s[s0].thread_base);
                 v_first = L.s[s0].v_begin;
             }
+            // with accumulation the SH-gradient rows start from the caller's
+            // values (loaded like the SH rows), otherwise from zero
+            const bool acc_rows = GAUSS && L.accumulate;
             if (threadIdx.x == 0) {
                 // the previous iteration's gradient stores have read the staging
                 if (GAUSS) bulk_wait_read_all();
                 if (full) {
                     fence_async_smem();
-                    mbar_expect_tx(&S[0].bar, PB_THREADS * (48 + 12) * 4);
+                    mbar_expect_tx(&S[0].bar, PB_THREADS * ((acc_rows ? 96 : 48) + 12) * 4);
                     tma_load_2d(S[0].shA, &tm_shA, 0, row0, &S[0].bar);
                     tma_load_2d(S[0].shB, &tm_shB, 32, row0, &S[0].bar);
                     const int srow = (int)(L.v[v_first].slot_base + base - L.s[scene_of_thread(L, base)].thread_base);
                     tma_load_2d(S[0].g2d, &tm_g2d, 0, srow, &S[0].bar);
+                    if (acc_rows) {
+                        tma_load_2d(S[0].gA, &tm_gA, 0, row0, &S[0].bar);
+                        tma_load_2d(S[0].gB, &tm_gB, 32, row0, &S[0].bar);
+                    }
                 }
             }
             __syncthreads();
@@ -114,12 +124,14 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
 #pragma unroll
                 for (int c = 0; c < 4; ++c) S[0].shB[swz64(r, c)] = src[8 + c];
             }
-            if (GAUSS) {
+            if (GAUSS && !(full && acc_rows)) {
                 const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 *cur = reinterpret_cast<const float4 *>(g_sh + 48LL * i);
+                const bool load = acc_rows && valid;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) S[0].gA[swz128(r, c)] = z;
+                for (int c = 0; c < 8; ++c) S[0].gA[swz128(r, c)] = load ? cur[c] : z;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) S[0].gB[swz64(r, c)] = z;
+                for (int c = 0; c < 4; ++c) S[0].gB[swz64(r, c)] = load ? cur[8 + c] : z;
             }
         }
 
@@ -171,6 +183,9 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                         }
                         mbar_wait(&S[0].bar, phase ^ 1);   // give the copy in flight (bounded) time to land
                     }
+                    // this block's pose partials are zero, not left from an earlier call
+                    for (int e = threadIdx.x; e < nv * 12; e += PB_THREADS)
+                        pose_partials[((long long)(e / 12) * gridDim.x + blockIdx.x) * 12 + e % 12] = 0.f;
                     return;
                 }
             } else {
@@ -389,9 +404,10 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                     gs[cc] += GM * Rq[3 * r + cc];
                     GRq[3 * r + cc] = GM * sc[cc];
                 }
-            g_log_scales[3 * i] = gs[0] * sc[0];
-            g_log_scales[3 * i + 1] = gs[1] * sc[1];
-            g_log_scales[3 * i + 2] = gs[2] * sc[2];
+            const bool acc = L.accumulate;
+            put(g_log_scales + 3 * i, gs[0] * sc[0], acc);
+            put(g_log_scales + 3 * i + 1, gs[1] * sc[1], acc);
+            put(g_log_scales + 3 * i + 2, gs[2] * sc[2], acc);
             // rotation of (w,x,y,z) -> quaternion gradient
             const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
             const float gw = 2.f * (-z * GRq[1] + y * GRq[2] + z * GRq[3] - x * GRq[5] - y * GRq[6] + x * GRq[7]);
@@ -403,12 +419,16 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                                      y * GRq[5] + x * GRq[6] + y * GRq[7]);
             const float dq = gw * w + gxq * x + gyq * y + gzq * z;
             const float iq = 1.f / qlen;
-            reinterpret_cast<float4 *>(g_quats)[i] =
-                make_float4((gw - w * dq) * iq, (gxq - x * dq) * iq, (gyq - y * dq) * iq, (gzq - z * dq) * iq);
-            g_means[3 * i] = gm[0];
-            g_means[3 * i + 1] = gm[1];
-            g_means[3 * i + 2] = gm[2];
-            g_logits[i] = go * opac * (1.f - opac);
+            float4 gq = make_float4((gw - w * dq) * iq, (gxq - x * dq) * iq, (gyq - y * dq) * iq, (gzq - z * dq) * iq);
+            if (acc) {
+                const float4 o = reinterpret_cast<const float4 *>(g_quats)[i];
+                gq = make_float4(o.x + gq.x, o.y + gq.y, o.z + gq.z, o.w + gq.w);
+            }
+            reinterpret_cast<float4 *>(g_quats)[i] = gq;
+            put(g_means + 3 * i, gm[0], acc);
+            put(g_means + 3 * i + 1, gm[1], acc);
+            put(g_means + 3 * i + 2, gm[2], acc);
+            put(g_logits + i, go * opac * (1.f - opac), acc);
         }
         if constexpr (GAUSS && TMA) {
             if (full) {
@@ -436,7 +456,7 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
             for (int e = threadIdx.x; e < PB_THREADS * 3 * K; e += PB_THREADS) {
                 const int rr = e / (3 * K), c = e % (3 * K);
                 const long long row = s_row[rr];
-                if (row >= 0) g_sh[row * 3 * K + c] = s_gf[rr * GP + c];
+                if (row >= 0) put(g_sh + row * 3 * K + c, s_gf[rr * GP + c], L.accumulate);
             }
             __syncthreads();
         } else if constexpr (TMA) {
@@ -472,12 +492,11 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
     memset(&ma, 0, sizeof ma); memset(&mb, 0, sizeof mb); memset(&ga, 0, sizeof ga); memset(&gb, 0, sizeof gb);
     memset(&m2, 0, sizeof m2);
     // degree 3 with 16-byte aligned SH rows and gradient rows: the staged
-    // path, unless the environment sets GS_DISABLE_TMA=1. The pose-only
+    // path, unless the configuration turns tensor copies off. The pose-only
     // backward reads SH rows only for Gaussians with a nonzero 2D gradient,
     // which the per-thread path does (measured faster there: 46 vs 63 us at
     // 1M Gaussians)
-    const char *no_tma = getenv("GS_DISABLE_TMA");
-    bool tma = want_gauss && deg == 3 && !(no_tma && no_tma[0] == '1') && ((uintptr_t)g->sh & 15u) == 0 &&
+    bool tma = want_gauss && deg == 3 && L.use_tma && ((uintptr_t)g->sh & 15u) == 0 &&
                g->n < 0x7fffffffLL &&
                encode_tmap_2d(&ma, g->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
                encode_tmap_2d(&mb, g->sh, 48, (uint64_t)g->n, 192, 16, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_64B);

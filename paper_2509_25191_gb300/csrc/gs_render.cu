@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
                                                             const int2 *__restrict__ ranges,
                                                             const unsigned int *__restrict__ ids,
                                                             const int *__restrict__ order, int *__restrict__ counters,
-                                                            float *__restrict__ image) {
+                                                            float *__restrict__ image, int *__restrict__ last_contrib) {
     constexpr int BS = TW * TH / 2, NB = TW * TH;
     __shared__ float4 s_xy[NB], s_con[NB], s_rgb[NB];
     __shared__ unsigned int s_mask[NB];
@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
         // lane .x = pixel (px, py0), lane .y = pixel (px, py0 + 4)
         float2 T = f2(1.f), CR = f2(0.f), CG = f2(0.f), CB = f2(0.f);
         bool done0 = !ti.in0, done1 = !ti.in1;
+        int end0 = r.x, end1 = r.x;   // one past the last composited instance
         const float2 PCY = make_float2(ti.pcy0, ti.pcy0 + 4.f);
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
             if (__syncthreads_count(done0 && done1) == BS) break;
@@ -242,6 +243,8 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
                     const bool cp0 = ok0 && !st0, cp1 = ok1 && !st1;
                     done0 = done0 || st0;
                     done1 = done1 || st1;
+                    end0 = cp0 ? b0 + k + 1 : end0;
+                    end1 = cp1 ? b0 + k + 1 : end1;
                     // weight and transmittance through a 0/1 mask (T (1 - alpha M) is
                     // T (1 - alpha) bit for bit when M = 1, T when M = 0)
                     const float2 Mcp = make_float2(cp0 ? 1.f : 0.f, cp1 ? 1.f : 0.f);
@@ -262,23 +265,32 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
             image[o] = abort ? 0.f : __fmaf_rn(T0, L.bg[0], C00);
             image[o + hw] = abort ? 0.f : __fmaf_rn(T0, L.bg[1], C01);
             image[o + 2 * hw] = abort ? 0.f : __fmaf_rn(T0, L.bg[2], C02);
+            if (last_contrib) last_contrib[vd.pix_base / 3 + (long long)ti.py0 * vd.W + ti.px] = end0;
         }
         if (ti.in1) {
             const long long o = vd.pix_base + (long long)(ti.py0 + 4) * vd.W + ti.px;
             image[o] = abort ? 0.f : __fmaf_rn(T1, L.bg[0], C10);
             image[o + hw] = abort ? 0.f : __fmaf_rn(T1, L.bg[1], C11);
             image[o + 2 * hw] = abort ? 0.f : __fmaf_rn(T1, L.bg[2], C12);
+            if (last_contrib) last_contrib[vd.pix_base / 3 + (long long)(ti.py0 + 4) * vd.W + ti.px] = end1;
         }
     }
 }
 
-template <int TW, int TH, bool COUNT>
+// With LAST, each pixel's replay ends at the position after its last
+// composited Gaussian, which the forward recorded in last_contrib: no
+// Gaussian before that position stops the pixel (the stop comes after the
+// last composited one), so every Gaussian that passes the alpha test there
+// is composited, and the warp and the block stop at their pixels' largest
+// end instead of walking on to saturation or the end of the list.
+template <int TW, int TH, bool COUNT, bool LAST>
 __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bwd(const Launch L, const float4 *__restrict__ proj,
                                                             const int2 *__restrict__ ranges,
                                                             const unsigned int *__restrict__ ids,
                                                             const int *__restrict__ order, int *__restrict__ counters,
                                                             const float *__restrict__ image,
                                                             const float *__restrict__ dL_dimage,
+                                                            const int *__restrict__ last_contrib,
                                                             float4 *__restrict__ grad2d) {
     // one staged Gaussian per thread and batch: the smaller shared-memory
     // footprint (17 KB) lets 9 blocks share an SM
@@ -327,13 +339,21 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
         }
         done0 = done0 || (gg[0][0] == 0.f && gg[0][1] == 0.f && gg[0][2] == 0.f);
         done1 = done1 || (gg[1][0] == 0.f && gg[1][1] == 0.f && gg[1][2] == 0.f);
+        // LAST: the end of each pixel's replay (the tile start for a pixel that
+        // needs none), and the later of the two
+        int end0 = r.x, end1 = r.x;
+        if (LAST) {
+            if (!done0) end0 = last_contrib[vd.pix_base / 3 + (long long)ti.py0 * vd.W + ti.px];
+            if (!done1) end1 = last_contrib[vd.pix_base / 3 + (long long)(ti.py0 + 4) * vd.W + ti.px];
+        }
+        const int endm = max(end0, end1);
         const float2 GR = make_float2(gg[0][0], gg[1][0]), GG = make_float2(gg[0][1], gg[1][1]),
                      GB = make_float2(gg[0][2], gg[1][2]), NIG = make_float2(-ig[0], -ig[1]);
         const float2 PCY = make_float2(ti.pcy0, ti.pcy0 + 4.f);
         float2 T = f2(1.f), CG = f2(0.f);
         unsigned int n_eval = 0, n_comp = 0;
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
-            if (__syncthreads_count(done0 && done1) == BS) break;
+            if (__syncthreads_count(LAST ? b0 >= endm : done0 && done1) == BS) break;
             stage_batch<TW, TH, 1>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
 #pragma unroll
             for (int h = 0; h < 1; ++h) {
@@ -344,7 +364,8 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
             __syncthreads();
             const int nb = min(NB, r.y - b0);
             for (int k0 = 0; k0 < nb; k0 += 32) {
-                if (__all_sync(0xffffffffu, done0 && done1)) break;   // the warp's pixels have all stopped
+                // the warp's pixels have all stopped
+                if (__all_sync(0xffffffffu, LAST ? b0 + k0 >= endm : done0 && done1)) break;
                 // only the staged Gaussians that may reach this warp's patch, in order
                 unsigned int hits = __ballot_sync(0xffffffffu, k0 + lane < nb && (s_mask[k0 + lane] & wbit));
                 while (hits) {
@@ -361,18 +382,22 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
                     const float2 oG = __fmul2_rn(f2(con.w), G);
                     const bool cl0 = oG.x > L.alpha_max, cl1 = oG.y > L.alpha_max;
                     const float a0 = cl0 ? L.alpha_max : oG.x, a1 = cl1 ? L.alpha_max : oG.y;
-                    const bool ev0 = col && !done0 && fabsf(dy.x) <= xy.w, ev1 = col && !done1 && fabsf(dy.y) <= xy.w;
+                    const bool live0 = LAST ? b0 + k < end0 : !done0, live1 = LAST ? b0 + k < end1 : !done1;
+                    const bool ev0 = col && live0 && fabsf(dy.x) <= xy.w, ev1 = col && live1 && fabsf(dy.y) <= xy.w;
                     const bool ok0 = ev0 && a0 >= L.alpha_min, ok1 = ev1 && a1 >= L.alpha_min;
                     if (COUNT) n_eval += (unsigned int)ev0 + (unsigned int)ev1;
                     if (!__any_sync(0xffffffffu, ok0 || ok1)) continue;
                     // transmittance: the pixel stops before a Gaussian that would
                     // bring T below t_min; otherwise the Gaussian is composited
+                    // (with LAST no such Gaussian comes before the pixel's end)
                     const float2 oma = __fadd2_rn(f2(1.f), make_float2(-a0, -a1));
                     const float2 Tn = __fmul2_rn(T, oma);
-                    const bool st0 = ok0 && Tn.x < L.t_min, st1 = ok1 && Tn.y < L.t_min;
+                    const bool st0 = !LAST && ok0 && Tn.x < L.t_min, st1 = !LAST && ok1 && Tn.y < L.t_min;
                     const bool cp0 = ok0 && !st0, cp1 = ok1 && !st1;
-                    done0 = done0 || st0;
-                    done1 = done1 || st1;
+                    if (!LAST) {
+                        done0 = done0 || st0;
+                        done1 = done1 || st1;
+                    }
                     if (COUNT) n_comp += (unsigned int)cp0 + (unsigned int)cp1;
                     // gradients; a pixel that does not composite contributes zeros
                     // (its weight and its alpha factors are zero)
@@ -463,34 +488,36 @@ static int launch_fwd_t(const Launch &L, const float *proj, const gs_bins *b, fl
     if (cudaMemsetAsync(b->counters + CNT_Q_FWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
     k_render_fwd<TW, TH><<<grid, TW * TH / 2, 0, st>>>(L, reinterpret_cast<const float4 *>(proj),
                                                        reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
-                                                       b->tile_order, b->counters, image);
+                                                       b->tile_order, b->counters, image, b->last_contrib);
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
-template <int TW, int TH, bool COUNT>
+template <int TW, int TH, bool COUNT, bool LAST>
 static int launch_bwd_c(const Launch &L, const float *proj, const gs_bins *b, const float *image,
                         const float *dL_dimage, float *grad2d, cudaStream_t st) {
     static int blocks_per_sm = 0;
     if (!blocks_per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_bwd<TW, TH, COUNT>, TW * TH / 2,
-                                                          0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_bwd<TW, TH, COUNT, LAST>,
+                                                          TW * TH / 2, 0) != cudaSuccess ||
             blocks_per_sm < 1)
             blocks_per_sm = 1;
     }
     const int grid = min(num_sms() * blocks_per_sm, max(1, L.n_tiles));
     if (cudaMemsetAsync(b->counters + CNT_Q_BWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
-    k_render_bwd<TW, TH, COUNT><<<grid, TW * TH / 2, 0, st>>>(L, reinterpret_cast<const float4 *>(proj),
-                                                              reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
-                                                              b->tile_order, b->counters, image, dL_dimage,
-                                                              reinterpret_cast<float4 *>(grad2d));
+    k_render_bwd<TW, TH, COUNT, LAST><<<grid, TW * TH / 2, 0, st>>>(
+        L, reinterpret_cast<const float4 *>(proj), reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
+        b->tile_order, b->counters, image, dL_dimage, b->last_contrib, reinterpret_cast<float4 *>(grad2d));
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
 template <int TW, int TH>
 static int launch_bwd_t(const Launch &L, const float *proj, const gs_bins *b, const float *image,
                         const float *dL_dimage, float *grad2d, cudaStream_t st) {
-    return L.count_pairs ? launch_bwd_c<TW, TH, true>(L, proj, b, image, dL_dimage, grad2d, st)
-                         : launch_bwd_c<TW, TH, false>(L, proj, b, image, dL_dimage, grad2d, st);
+    if (b->last_contrib)
+        return L.count_pairs ? launch_bwd_c<TW, TH, true, true>(L, proj, b, image, dL_dimage, grad2d, st)
+                             : launch_bwd_c<TW, TH, false, true>(L, proj, b, image, dL_dimage, grad2d, st);
+    return L.count_pairs ? launch_bwd_c<TW, TH, true, false>(L, proj, b, image, dL_dimage, grad2d, st)
+                         : launch_bwd_c<TW, TH, false, false>(L, proj, b, image, dL_dimage, grad2d, st);
 }
 
 int launch_render_fwd(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st) {

@@ -28,3 +28,14 @@ def apply_residual(viewmats, dr, dt):
     t = viewmats[:, 9:]
     Rn = rotation_6d(dr) @ R
     return torch.cat([Rn.reshape(-1, 9), t + dt], dim=1)
+
+
+def pose_lr(step, total_steps=30000, lr0=1e-4, factor=0.1):
+    """Learning rate of the pose residuals at training step ``step``
+    (Section 4.1, implementation details: initialised at 1e-4 and decayed
+    exponentially by a factor of 0.1 over the training run, whose length
+    follows the MCMC-3DGS schedule, 30,000 iterations):
+    lr0 * factor ** (step / total_steps), held at lr0 * factor afterwards."""
+    if total_steps <= 0:
+        raise ValueError("total_steps must be positive")
+    return lr0 * factor ** (min(max(step, 0), total_steps) / total_steps)

@@ -40,7 +40,7 @@ class GraphStep:
     KERNELS_PER_STEP = 11   # project 1, bin/sort 5, render 1, loss 1, raster bwd 1, projection bwd 1, pose 1
 
     def __init__(self, g: Gaussians, views: Views, target, tile=(16, 16), headroom=1.25, capture=True,
-                 want_gaussian_grads=True, loss="l1", lam=0.2, slots=1, slot_gaussians=False):
+                 want_gaussian_grads=True, loss="l1", lam=0.2, slots=1, slot_gaussians=False, capacity=None):
         self.g, self.views, self.target = g, views, target
         if slots < 1:
             raise ValueError("slots must be >= 1")
@@ -59,9 +59,12 @@ class GraphStep:
         self.loss_kind, self.lam = loss, float(lam)
         dev = g.means.device
         self.rast = Rasterizer(tile=tile)
-        _, _ = self.rast.forward(g, views)
-        torch.cuda.synchronize(dev)
-        self.capacity = int(self.rast.last_instances * headroom) + 4096
+        if capacity is None:
+            # size the instance capacity from one uncaptured forward
+            _, _ = self.rast.forward(g, views)
+            torch.cuda.synchronize(dev)
+            capacity = int(self.rast.last_instances * headroom) + 4096
+        self.capacity = int(capacity)
         self.rast.reserve(views, self.capacity, dev)
         self.cfg, self.bins, self.status = self.rast.cfg, self.rast.bins, self.rast.status
         self.proj = torch.empty(max(1, views.num_slots()), _lib.GS_RECORD_FLOATS, device=dev)
@@ -124,7 +127,10 @@ class GraphStep:
 
     def check(self):
         """Read the status word (synchronises). On a capacity overflow, grow
-        the capacity, re-capture, and report True (the step must be rerun)."""
+        the capacity, clear the word, re-capture, and report True (the step
+        must be rerun); otherwise report False. A loop of the form
+        ``while step.check(): step.replay()`` ends after the first replay
+        that fits."""
         st = self.status.cpu().numpy()
         if st[0] == 0:
             return False
@@ -134,6 +140,9 @@ class GraphStep:
         self.capacity = int(needed * 1.25) + 4096
         self.rast.reserve(self.views, self.capacity, self.g.means.device)
         self.bins, self.status = self.rast.bins, self.rast.status
+        # the overflow has been handled: clear the word (no kernel resets it),
+        # so that the next check reports only what the next replay finds
+        self.status.zero_()
         self.capture()
         return True
 

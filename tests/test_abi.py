@@ -110,3 +110,49 @@ def test_host_checks_reject_bad_layouts():
     bad_alpha.alpha_max = 1.0
     assert project(ok_v, cfg=bad_alpha) == _lib.GS_ERR_ARG           # alpha clamp must be below 1
     assert lib.gs_check_bounded_wait(None, None) == _lib.GS_ERR_ARG
+
+
+def test_config_defaults_of_the_boundary_flags():
+    """Gradients are overwritten unless accumulation is asked for, and the
+    projection kernels may use tensor copies unless told not to."""
+    from paper_2509_25191_gb300 import _lib
+    cfg = _lib.gs_config()
+    _lib.load().gs_config_default(ctypes.byref(cfg))
+    assert (cfg.accumulate_grads, cfg.use_tma, cfg.count_pairs) == (0, 1, 0)
+    c = _lib.config(accumulate_grads=True, use_tma=False)
+    assert (c.accumulate_grads, c.use_tma) == (1, 0)
+
+
+def test_workspace_layout_on_the_host():
+    """gs_workspace_size and gs_workspace_carve are host arithmetic: every
+    piece is 256-byte aligned, inside the buffer, large enough for its array
+    and disjoint from the others (checked on a placeholder address that is
+    never dereferenced)."""
+    from paper_2509_25191_gb300 import _lib, synth
+    sc, vw = synth.uneven_scenes(seeds=(1, 2), sizes=(10, 20), views_per_scene=2,
+                                 resolutions=((33, 17), (64, 48)))
+    views = _lib.Views(None, None, vw.width, vw.height, vw.gauss_begin, vw.gauss_count)
+    cfg = _lib.config(tile=(16, 8))
+    n, cap = int(sc.n), 1000
+    size = _lib.gs_workspace_size(views, cfg, n, cap)
+    base = 1 << 30
+    bins, g2d, pp = _lib.gs_workspace_carve(views, cfg, n, cap, base, size)
+    T = views.num_tiles(cfg)
+    P = views.num_slots()
+    blocks = int(_lib.load().gs_pose_blocks(ctypes.c_int64(n)))
+    pieces = [(bins.tile_ranges, 8 * T), (bins.keys, 8 * cap), (bins.ids, 4 * cap), (bins.keys_tmp, 8 * cap),
+              (bins.tile_order, 4 * T), (bins.tile_scratch, 4 * T), (bins.counters, 4 * _lib.GS_NUM_COUNTERS),
+              (bins.last_contrib, 4 * views.pixels), (g2d, 4 * 12 * P), (pp, 4 * 12 * views.n * blocks)]
+    spans = sorted((p, p + nbytes) for p, nbytes in pieces)
+    assert all(p % 256 == 0 and base <= p and e <= base + size for p, e in spans)
+    assert all(spans[i][1] <= spans[i + 1][0] for i in range(len(spans) - 1))
+    assert bins.capacity == cap
+    # too small a buffer, a misaligned one, or bad arguments are rejected
+    lib = _lib.load()
+    b, gr = _lib.gs_bins(), _lib.gs_grads()
+    c = views.c()
+    for ws, nbytes in ((base, size - 1), (base + 16, size)):
+        assert lib.gs_workspace_carve(ctypes.byref(c), ctypes.byref(cfg), n, cap, ctypes.c_void_p(ws),
+                                      ctypes.c_size_t(nbytes), ctypes.byref(b), ctypes.byref(gr)) == _lib.GS_ERR_ARG
+    assert _lib.gs_workspace_size(views, cfg, n, -1) == 0
+    assert lib.gs_status_read(None, None, None) == _lib.GS_ERR_ARG

@@ -54,3 +54,15 @@ def test_composition_and_gradients():
     assert np.allclose(out[:, :9].reshape(3, 3, 3), dR @ R, atol=1e-14)
     assert np.allclose(out[:, 9:], t + dt.detach().numpy(), atol=1e-15)
     assert torch.autograd.gradcheck(lambda a, b: pose.apply_residual(vm, a, b), (dr, dt), eps=1e-6, atol=1e-8)
+
+
+def test_pose_learning_rate_schedule():
+    """Section 4.1: 1e-4 at the start, decayed exponentially to a tenth over
+    the run (geometric mean half way), flat after the end."""
+    assert pose.pose_lr(0) == 1e-4
+    assert np.isclose(pose.pose_lr(30000), 1e-5, rtol=1e-12)
+    assert np.isclose(pose.pose_lr(15000), 1e-4 * 0.1 ** 0.5, rtol=1e-12)
+    assert np.isclose(pose.pose_lr(45000), 1e-5, rtol=1e-12)
+    lrs = [pose.pose_lr(k, total_steps=100) for k in range(101)]
+    ratios = np.array(lrs[1:]) / np.array(lrs[:-1])
+    assert np.allclose(ratios, 0.1 ** 0.01, rtol=1e-12)   # constant ratio: exponential
