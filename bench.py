@@ -38,12 +38,14 @@ if ROOT not in sys.path:
 METRIC = "fwd+bwd Mpix/s incl. pose grads at 1M Gaussians"
 UNIT = "Mpix/s"
 
-# FP32 operations per pixel-Gaussian pair, counted from the kernels'
-# arithmetic (gs_render.cu): every pair that passes the pixel gate evaluates
-# the exponent (dx, dy, 3 mul + 2 fma, o*G, clamp/threshold: 10 ops + 1 ex2);
-# a composited pair adds 9 in the forward (1-alpha, T update, weight,
-# 3 fma) and 50 in the backward (colour/alpha/conic/mean gradients and the
-# recomputed accumulation).
+# FP32 operations per pixel-Gaussian pair. The method's count: about 12
+# flops + 1 ex2 per evaluated pair in the forward and 40 flops + 1 ex2 in the
+# backward. The kernels' own arithmetic (gs_render.cu): every pair that
+# passes the pixel gate evaluates the exponent (dx, dy, 3 mul + 2 fma, o*G,
+# clamp/threshold: 10 ops + 1 ex2); a composited pair adds 9 in the forward
+# (1-alpha, T update, weight, 3 fma) and 50 in the backward (colour/alpha/
+# conic/mean gradients and the recomputed accumulation).
+FWD_FLOPS_EVAL, BWD_FLOPS_EVAL = 12, 40
 FWD_OPS_EVAL, FWD_OPS_COMP = 10, 9
 BWD_OPS_EVAL, BWD_OPS_COMP = 10, 50
 FP32_LANES_PER_SM = 128
@@ -82,10 +84,11 @@ def parse():
     ap.add_argument("--no-ga", action="store_true", help="skip the global-alignment workload")
     ap.add_argument("--only", choices=["ga"], default=None,
                     help="run only the named secondary workload and print its figures (for profiling)")
-    ap.add_argument("--extra", action="store_true",
-                    help="also time the uneven multi-scene batch and the dense-view joint pose step")
-    ap.add_argument("--ref-fraction", type=float, default=1.0 / 16.0,
-                    help="pixel fraction of each reference-arm step")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the uneven multi-scene batch and the dense-view joint pose step")
+    ap.add_argument("--ref-fraction", type=float, default=1.0,
+                    help="pixel fraction of each reference-arm step (1 = the whole workload, the same "
+                         "configuration as the native arm)")
     return ap.parse_args()
 
 
@@ -93,6 +96,24 @@ def workload(n):
     from paper_2509_25191_gb300 import synth
     sc, vw = synth.single_view_1m(0, n)
     return sc, vw
+
+
+def stage_bytes(n, sh_degree, slots, instances, pixels, n_tiles):
+    """Bytes each stage of the method must move per step (the raw record
+    R_in = 236 B for SH3): projection reads the records once for all views
+    and writes a 48-B record and a 4-B tile count per slot; binning writes
+    the instance list (12 B) and reads it sorted once, plus the tile ranges;
+    the forward gathers each instance's 36-B payload and 4-B id and writes the
+    image (12 B per pixel); the backward gathers them again (40 B), reads the
+    image and its gradient (24 B per pixel) and writes and reads the 2D
+    gradients (80 B per slot); the projection backward re-reads the records
+    and writes their gradients."""
+    r_in = 4 * (3 + 3 + 4 + 1 + 3 * (sh_degree + 1) ** 2)
+    return {"gs_project": n * r_in + 52 * slots,
+            "gs_bin_sort": 24 * instances + 8 * n_tiles,
+            "gs_render_fwd": 40 * instances + 12 * pixels,
+            "gs_rasterize_bwd": 40 * instances + 24 * pixels + 40 * slots,
+            "gs_project_bwd": 2 * n * r_in + 40 * slots}
 
 
 def algorithmic_bytes(n, sh_degree, slots, instances, pixels, n_tiles):
@@ -104,6 +125,40 @@ def algorithmic_bytes(n, sh_degree, slots, instances, pixels, n_tiles):
     per pixel), tile ranges."""
     r_in = 4 * (3 + 3 + 4 + 1 + 3 * (sh_degree + 1) ** 2)
     return 3 * n * r_in + 132 * slots + 108 * instances + 36 * pixels + 8 * n_tiles
+
+
+def measure_alu_peaks(dev, iters=16384, launches=60):
+    """Measured arithmetic throughput of one GB300 (CUDA events, after warm-up):
+    scalar FP32 FMA, packed f32x2 FMA and ex2.approx, from the library's probe
+    kernels, with the SM clock sampled meanwhile; FMA rates in FLOP/s (2 per
+    FMA), ex2 in operations/s, and each per SM and clock cycle."""
+    import torch
+
+    from paper_2509_25191_gb300 import _lib
+    out = None
+    res = {}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    with ClockSampler(dev.index or 0) as clk:
+        for kind, name in ((0, "fp32_fma"), (1, "fp32_fma_f32x2"), (2, "ex2")):
+            for _ in range(3):
+                out, ops = _lib.gs_peak_probe(kind, iters, out)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(launches):
+                _lib.gs_peak_probe(kind, iters, out)
+            b.record()
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) * 1e-3 / launches
+            res[name] = ops / sec * (1 if kind == 2 else 2)
+    clocks = clk.summary()
+    mhz = clocks.get("sm_mhz") or 2070.0
+    out = {k: round(v / 1e12, 3) for k, v in res.items()}
+    out["unit"] = "TFLOP/s (ex2: T ops/s)"
+    out["per_sm_per_clock"] = {k: round(v / (sms * mhz * 1e6), 2) for k, v in res.items()}
+    out["fp32_peak_tflops"] = round(max(res["fp32_fma"], res["fp32_fma_f32x2"]) / 1e12, 3)
+    out["clocks"] = clocks
+    return out
 
 
 class ClockSampler:
@@ -347,20 +402,33 @@ def run_native(args, rank, world, local_rank):
     raster_traffic = rt["bytes"] if (args.n == rt["n"] and tuple(tile) == rt["tile"] and
                                      raster_bwd_sources_hash() == rt["sources_sha256_16"]) else None
     peaks, peak_src = measured_peaks()
+    alu = measure_alu_peaks(dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     top = int(np.argmax(stage_ms))
     t_top = stage_ms[top] * 1e-3
     if names[top] in ("gs_render_fwd", "gs_rasterize_bwd"):
-        ev_, co_ = (pairs[0], pairs[1]) if names[top] == "gs_render_fwd" else (pairs[2], pairs[3])
-        ops = (FWD_OPS_EVAL * ev_ + FWD_OPS_COMP * co_) if names[top] == "gs_render_fwd" else \
-            (BWD_OPS_EVAL * ev_ + BWD_OPS_COMP * co_)
-        peak = sms * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        achieved = ops / t_top / 1e12
-        roof = {"kernel": names[top], "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+        fwd = names[top] == "gs_render_fwd"
+        ev_, co_ = (pairs[0], pairs[1]) if fwd else (pairs[2], pairs[3])
+        flops = (FWD_FLOPS_EVAL if fwd else BWD_FLOPS_EVAL) * ev_
+        kops = (FWD_OPS_EVAL * ev_ + FWD_OPS_COMP * co_) if fwd else (BWD_OPS_EVAL * ev_ + BWD_OPS_COMP * co_)
+        peak = alu["fp32_peak_tflops"]
+        achieved = flops / t_top / 1e12
+        nominal = sms * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"kernel": names[top], "bound": "alu", "achieved": round(achieved, 3), "peak": peak,
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": raster_traffic,
-                "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz"
-                               f" ({peak_src} max clock)",
-                "units": {"pairs_evaluated": ev_, "pairs_composited": co_, "fp32_ops": int(ops)}}
+                "peak_source": "measured: FP32 FMA probe kernels of this library on this GPU (best of scalar and "
+                               "packed f32x2), CUDA events, clocks sampled (alu_peaks)",
+                "ops_basis": f"{FWD_FLOPS_EVAL if fwd else BWD_FLOPS_EVAL} FP32 flops per evaluated pixel-Gaussian "
+                             "pair (the method's count)",
+                "units": {"pairs_evaluated": ev_, "pairs_composited": co_, "fp32_flops": int(flops)},
+                "kernel_ops": {"ops": int(kops), "basis": "the kernel's own arithmetic: "
+                               f"{BWD_OPS_EVAL if not fwd else FWD_OPS_EVAL} per evaluated + "
+                               f"{BWD_OPS_COMP if not fwd else FWD_OPS_COMP} per composited pair",
+                               "achieved": round(kops / t_top / 1e12, 3),
+                               "frac": round(kops / t_top / 1e12 / peak, 4)},
+                "nominal_peak": {"value": round(nominal, 2),
+                                 "basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                          f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}}
     else:
         hbm = peaks["hbm_gbs"]
         roof = {"kernel": names[top], "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
@@ -384,12 +452,16 @@ def run_native(args, rank, world, local_rank):
     pose_only["mpix_s"] = round(P / pose_only["ms_per_step"] / 1e3, 2)
     del pstep
     batched = None if args.no_batched else batched_vs_plain(dev, tile if args.tile != "auto" else "auto")
-    extra = {"uneven_scenes": run_uneven(dev), "dense_pose_step": run_dense(dev)} if args.extra else {}
+    extra = {} if args.no_extra else {"uneven_scenes": run_uneven(dev), "dense_pose_step": run_dense(dev)}
     if not args.no_ga:
         extra["ga_epipolar"] = run_ga(dev)
     extra = extra or None
     step_bytes = algorithmic_bytes(g.n, g.sh_degree, views.num_slots(), n_inst, P, views.num_tiles(cfg))
     hbm_frac_step = step_bytes / (ms * 1e-3) / (peaks["hbm_gbs"] * 1e9)
+    sb = stage_bytes(g.n, g.sh_degree, views.num_slots(), n_inst, P, views.num_tiles(cfg))
+    stage_frac = {n: {"algorithmic_bytes": int(sb[n]), "ms": round(float(t), 4),
+                      "frac_of_hbm": round(sb[n] / (float(t) * 1e-3) / (peaks["hbm_gbs"] * 1e9), 4)}
+                  for n, t in zip(names, stage_ms) if n in sb}
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -403,6 +475,8 @@ def run_native(args, rank, world, local_rank):
         "step_hbm_roofline": {"algorithmic_bytes": int(step_bytes), "frac": round(hbm_frac_step, 4),
                               "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src},
         "stages_ms": {n: round(float(t), 4) for n, t in zip(names, stage_ms)},
+        "stage_hbm_roofline": stage_frac,
+        "alu_peaks": alu,
         "autotune": tuning,
         "clocks": clocks,
         "pose_only_step": pose_only,
@@ -453,10 +527,35 @@ def batched_vs_plain(dev, tile, steps=20, plain_steps=5):
     torch.cuda.synchronize()
     tp = a.elapsed_time(b) / plain_steps
     px = views.pixels
+    # where each arm's time goes: eager per-stage events (the batched step's
+    # calls once over all views; the plain arm's calls per view, summed)
+    reps = 3
+    bn = ["gs_project", "gs_bin_sort", "gs_render_fwd", "gs_l1_loss", "gs_rasterize_bwd", "gs_project_bwd",
+          "gs_pose_grad"]
+    bacc = np.zeros(len(bn))
+    pacc = np.zeros(len(PlainStep.STAGES))
+    for _ in range(reps):
+        ev = []
+        gs.run(ev)
+        torch.cuda.synchronize()
+        bacc += [ev[i].elapsed_time(ev[i + 1]) for i in range(len(bn))]
+        ev = []
+        ps.run(ev)
+        torch.cuda.synchronize()
+        k = len(PlainStep.STAGES)
+        for v in range(len(ev) // (k + 1)):
+            e = ev[v * (k + 1):(v + 1) * (k + 1)]
+            pacc += [e[i].elapsed_time(e[i + 1]) for i in range(k)]
+    bst = {n: round(float(t) / reps, 4) for n, t in zip(bn, bacc)}
+    pst = {n: round(float(t) / reps, 4) for n, t in zip(PlainStep.STAGES, pacc)}
     return {"workload": "16 views 979x546 on a radius-5 orbit, 500K clustered SH3 Gaussians (seed 0), "
                         "fwd+L1+bwd+pose", "batched_ms": round(tb, 4), "plain_ms": round(tp, 4),
             "tile": list(tile), "batched_mpix_s": round(px / tb / 1e3, 2), "plain_mpix_s": round(px / tp / 1e3, 2),
-            "ratio": round(tp / tb, 3), "steps": steps, "plain_steps": plain_steps}
+            "ratio": round(tp / tb, 3), "steps": steps, "plain_steps": plain_steps,
+            "batched_stages_ms": bst,
+            "plain_stages_ms": pst,
+            "plain_definition": "the same library called view by view, uncaptured, each call with the instance-count "
+                                "readback an uncaptured call needs (bin_sort includes it)"}
 
 
 def _time_replays(step, steps):
@@ -676,16 +775,18 @@ def run_ga(dev, iterations=300, reps=50):
 # ---------------------------------------------------------------------------
 
 def oracle_step(sc, vw, fraction, seed):
-    """One oracle fwd+bwd+pose pass over a random pixel sample (all pixels if
-    fraction >= 1). Returns the number of pixels computed."""
+    """One oracle fwd + L1 + bwd + pose pass over a random pixel sample (all
+    pixels if fraction >= 1), against the native arm's target image (uniform
+    values, seed 1234). Returns the number of pixels computed."""
     from oracle import oracle as O
     W, H = int(vw.width[0]), int(vw.height[0])
     rng = np.random.default_rng(seed)
     mask = None if fraction >= 1 else rng.random((H, W)) < fraction
-    up = rng.standard_normal((3, H, W))
+    f = O.forward(sc, vw, masks=None if mask is None else [mask])
+    target = np.random.default_rng(1234).uniform(0, 1, 3 * W * H).astype(np.float32).reshape(3, H, W)
+    up = np.sign(f[0]["image"] - target) / (3.0 * W * H)          # the mean-L1 gradient
     if mask is not None:
         up[:, ~mask] = 0.0
-    f = O.forward(sc, vw, masks=None if mask is None else [mask])
     O.backward(sc, vw, f, [up])
     return W * H if mask is None else int(mask.sum())
 
@@ -740,13 +841,19 @@ def run_reference(args, rank, world):
         px = sum(pool.map(_ref_worker_step, [(args.ref_fraction, k) for k in range(args.steps)], chunksize=1))
         dt = time.perf_counter() - t
     val = px / dt / 1e6
-    sample = (f"each step: full projection, binning and projection backward of all {args.n} Gaussians, render "
-              f"forward+backward on a random {args.ref_fraction:.4f} of the 1237x822 pixels; FP64 C oracle, "
-              f"single-threaded per step, {cores} steps at a time on {cores} host cores")
+    if args.ref_fraction >= 1.0:
+        sample = (f"each step: the whole workload (projection, binning, render forward and backward of all 1237x822 "
+                  f"pixels, projection backward and pose gradient of all {args.n} Gaussians); FP64 C oracle, "
+                  f"single-threaded per step, {cores} steps at a time on {cores} host cores")
+    else:
+        sample = (f"each step: full projection, binning and projection backward of all {args.n} Gaussians, render "
+                  f"forward+backward on a random {args.ref_fraction:.4f} of the 1237x822 pixels; FP64 C oracle, "
+                  f"single-threaded per step, {cores} steps at a time on {cores} host cores")
     return {"metric": METRIC, "value": round(val, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"single view 1237x822, {args.n} clustered SH3 Gaussians (seed 0), fwd+bwd+pose"},
+            "config": {"workload": f"single view 1237x822, {args.n} clustered SH3 Gaussians (seed 0), fwd+L1+bwd+pose",
+                       "gaussians": args.n, "views": 1, "pixels_per_step": 1237 * 822},
             "cpu_baseline": {"value": round(val, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": round(val, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

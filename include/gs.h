@@ -257,8 +257,10 @@ int gs_render_bwd(const gs_gaussians *g, const gs_views *views, const gs_config 
  * set it must hold what gs_render_fwd wrote for this image with these bins,
  * and each pixel's replay ends at its last composited Gaussian (the result is
  * the same as without it). gs_project_bwd chains grad2d to the raw
- * parameters (overwritten, or added with cfg->accumulate_grads) and the pose
- * partials (always overwritten). With degree-3 SH, want_gaussian_grads and
+ * parameters (overwritten, or added with cfg->accumulate_grads; the staged
+ * degree-3 path adds each view's SH-coefficient gradient to the running
+ * value, so with several views per Gaussian the sum is rounded in that
+ * order) and the pose partials (always overwritten). With degree-3 SH, want_gaussian_grads and
  * cfg->use_tma, gs_project_bwd stages each block's SH rows, first-view
  * 2D-gradient rows and SH-gradient rows by tensor copies (grads->sh must then
  * be 16-byte aligned, else the per-thread path runs); a bounded wait for one
@@ -478,6 +480,18 @@ int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *views, const g
  * the call and reads it after synchronising); nothing faults or traps, and
  * the context stays usable. Returns GS_ERR_ARG for a NULL status. */
 int gs_check_bounded_wait(int32_t *status, void *stream);
+
+/* Arithmetic-throughput probes (measurement only; the paper has no
+ * counterpart): the raster kernels are bound by FP32 and special-function
+ * issue rather than by memory, so their roofline needs these pipes' measured
+ * rates. kind 0 = scalar FP32 fused multiply-add, 1 = packed f32x2 fused
+ * multiply-add, 2 = ex2.approx. One launch of gs_probe_blocks() blocks of 256
+ * threads, each thread running 8 independent chains of `iters` operations;
+ * out: DEVICE float [gs_probe_blocks() * 256] (overwritten). The caller
+ * times the launch: operations = blocks x 256 x 8 x iters (x 2 for kind 1;
+ * an FMA is 2 FLOPs). */
+int gs_probe_blocks(void);
+int gs_peak_probe(int kind, int iters, float *out, void *stream);
 
 const char *gs_error_string(int code);
 int gs_version(void);

@@ -26,7 +26,8 @@ EXPORTED = ["gs_config_default", "gs_num_slots", "gs_slot_base", "gs_num_tiles",
             "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version",
             "gs_project_bwd_noalloc", "gs_sgld_adam_step", "gs_ga_select_pairs", "gs_ga_incidence",
             "gs_ga_epipolar", "gs_ga_weights_scratch_bytes", "gs_ga_weights", "gs_ga_step", "gs_l1_dssim_loss",
-            "gs_check_bounded_wait", "gs_workspace_size", "gs_workspace_carve", "gs_status_read"]
+            "gs_check_bounded_wait", "gs_workspace_size", "gs_workspace_carve", "gs_status_read",
+            "gs_probe_blocks", "gs_peak_probe"]
 GS_GA_MAX_CAMS = 8192
 GS_GA_PAIR_FLOATS = 12
 GS_GA_MAX_BINS = 16384
@@ -451,6 +452,17 @@ def gs_status_read(status, stream=None):
     out = (ctypes.c_int32 * 4)()
     _check(load().gs_status_read(_ptr(status), out, _stream(stream)), "gs_status_read")
     return list(out)
+
+
+def gs_peak_probe(kind, iters, out=None, stream=None):
+    """One launch of the arithmetic-throughput probe (kind 0 FP32 FMA, 1
+    packed f32x2 FMA, 2 ex2.approx); returns (out, operations per launch,
+    counting an FMA lane as one operation)."""
+    blocks = int(load().gs_probe_blocks())
+    if out is None:
+        out = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    _check(load().gs_peak_probe(int(kind), int(iters), _ptr(out), _stream(stream)), "gs_peak_probe")
+    return out, blocks * 256 * 8 * int(iters) * (2 if kind == 1 else 1)
 
 
 def gs_check_bounded_wait(status, stream=None):

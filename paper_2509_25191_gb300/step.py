@@ -163,9 +163,24 @@ class PlainStep:
         dev = g.means.device
         self.loss = torch.empty(1, device=dev)
 
-    def run(self):
+    STAGES = ("project", "bin_sort", "render_fwd", "loss", "backward")
+
+    def run(self, events=None):
+        """The views one after another; with ``events`` (a list), an event is
+        recorded before and after each stage of each view (the bin_sort stage
+        includes the instance-count readback)."""
+        rec = (lambda: events.append(torch.cuda.Event(enable_timing=True)) or events[-1].record()) \
+            if events is not None else (lambda: None)
         for vv, tgt, rast in self.one:
-            image, proj = rast.forward(self.g, vv)          # includes the instance-count readback
+            rec()
+            proj = rast.project(self.g, vv)
+            rec()
+            bins = rast.bin_sort(vv, proj)                 # includes the instance-count readback
+            rec()
+            image = rast.render(vv, proj, bins)
+            rec()
             dimg = torch.empty_like(image)
             _lib.gs_l1_loss(image, tgt, self.loss, dimg)
+            rec()
             rast.backward(self.g, vv, proj, image, dimg)
+            rec()

@@ -35,3 +35,13 @@ def test_algorithmic_bytes_of_the_single_view_step():
     got = bench.algorithmic_bytes(n, 3, slots, inst, pix, tiles)
     assert got == 3 * n * 236 + 132 * slots + 108 * inst + 36 * pix + 8 * tiles == 1_261_304_568
     assert bench.algorithmic_bytes(10, 0, 10, 0, 0, 0) == 3 * 10 * 56 + 132 * 10
+
+
+def test_stage_bytes_partition_the_step():
+    """The per-stage algorithmic bytes cover the step's total: the stages sum
+    to the total except 4 B per instance (the step total counts 108 B per
+    instance, the three instance-touching stages 24 + 40 + 40)."""
+    n, slots, inst, pix, tiles = 1_000_000, 1_000_000, 3_561_880, 1237 * 822, 39 * 52
+    sb = bench.stage_bytes(n, 3, slots, inst, pix, tiles)
+    assert set(sb) == {"gs_project", "gs_bin_sort", "gs_render_fwd", "gs_rasterize_bwd", "gs_project_bwd"}
+    assert sum(sb.values()) + 4 * inst == bench.algorithmic_bytes(n, 3, slots, inst, pix, tiles)
