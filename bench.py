@@ -57,7 +57,7 @@ FP32_LANES_PER_SM = 128
 # its two source files) and for the default workload and tile; otherwise the
 # bench reports null.
 RASTER_BWD_TRAFFIC = {"bytes": 51968000, "sources_sha256_16": "99e3c618f09b48d9", "n": 1_000_000,
-                      "tile": (32, 16)}
+                      "tile": (32, 16), "batch": (2, 1)}
 
 
 def raster_bwd_sources_hash():
@@ -76,7 +76,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--tile", default="auto", help="tile shape WxH, or auto (the project's autotuner)")
+    ap.add_argument("--tile", default="auto", help="tile shape WxH, or auto (the project's autotuner picks the "
+                                                   "tile and the shared-memory batch)")
+    ap.add_argument("--batch", default="2,1", help="with a fixed --tile: Gaussians per thread per shared-memory "
+                                                   "batch, forward,backward")
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -260,15 +263,19 @@ def run_native(args, rank, world, local_rank):
     target = torch.as_tensor(rng.uniform(0, 1, views.num_image_floats()).astype(np.float32), device=dev)
     tuning = None
     if args.tile == "auto":
-        from paper_2509_25191_gb300.tune import autotune
-        tile, ms = autotune(g, views, target)
-        tuning = {"chosen": list(tile), "ms_per_step": {f"{t[0]}x{t[1]}": round(v, 4) for t, v in ms.items()}}
+        from paper_2509_25191_gb300.tune import autotune, key_str
+        choice, ms = autotune(g, views, target)
+        tile, batch = choice.tile, choice.batch
+        tuning = {"chosen": {"tile": list(tile), "batch": list(batch)},
+                  "ms_per_step": {key_str(c): round(v, 4) for c, v in sorted(ms.items(), key=lambda kv: kv[1])},
+                  "key": "tile WxH / Gaussians per thread per shared-memory batch (forward.backward)"}
     else:
         tile = tuple(int(x) for x in args.tile.split("x"))
+        batch = tuple(int(x) for x in args.batch.split(","))
 
     # two input slots (target, view matrices): the end-to-end loop below
     # uploads step k+1's inputs into one while step k runs on the other
-    step = GraphStep(g, views, target, tile=tile, slots=2, slot_gaussians=not args.no_e2e)
+    step = GraphStep(g, views, target, tile=tile, batch=batch, slots=2, slot_gaussians=not args.no_e2e)
     rast, cfg, bins = step.rast, step.cfg, step.bins
     image, dvm, loss = step.image, step.dviewmat, step.loss
     kernels_per_step = GraphStep.KERNELS_PER_STEP
@@ -399,8 +406,8 @@ def run_native(args, rank, world, local_rank):
 
     # roofline of the dominant kernel
     rt = RASTER_BWD_TRAFFIC
-    raster_traffic = rt["bytes"] if (args.n == rt["n"] and tuple(tile) == rt["tile"] and
-                                     raster_bwd_sources_hash() == rt["sources_sha256_16"]) else None
+    raster_traffic = rt["bytes"] if (args.n == rt["n"] and tuple(tile) == rt["tile"] and tuple(batch) == rt["batch"]
+                                     and raster_bwd_sources_hash() == rt["sources_sha256_16"]) else None
     peaks, peak_src = measured_peaks()
     alu = measure_alu_peaks(dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -434,7 +441,7 @@ def run_native(args, rank, world, local_rank):
         roof = {"kernel": names[top], "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                 "traffic": None}
     # the same step with the L1 + D-SSIM loss of Section 3.1 (fused kernel), and that kernel alone
-    dstep = GraphStep(g, views, target, tile=tile, loss="l1_dssim")
+    dstep = GraphStep(g, views, target, tile=tile, batch=batch, loss="l1_dssim")
     dssim = {"ms_per_step": round(_time_replays(dstep, 50), 4)}
     dssim["mpix_s"] = round(P / dssim["ms_per_step"] / 1e3, 2)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -447,11 +454,11 @@ def run_native(args, rank, world, local_rank):
     dssim["loss"] = [round(float(v), 6) for v in dstep.loss.cpu()]
     del dstep
     # test-time pose tuning (Gaussians frozen): the same step with the backward to the pose only
-    pstep = GraphStep(g, views, target, tile=tile, want_gaussian_grads=False)
+    pstep = GraphStep(g, views, target, tile=tile, batch=batch, want_gaussian_grads=False)
     pose_only = {"ms_per_step": round(_time_replays(pstep, 50), 4)}
     pose_only["mpix_s"] = round(P / pose_only["ms_per_step"] / 1e3, 2)
     del pstep
-    batched = None if args.no_batched else batched_vs_plain(dev, tile if args.tile != "auto" else "auto")
+    batched = None if args.no_batched else batched_vs_plain(dev, (tile, batch) if args.tile != "auto" else "auto")
     extra = {} if args.no_extra else {"uneven_scenes": run_uneven(dev), "dense_pose_step": run_dense(dev)}
     if not args.no_ga:
         extra["ga_epipolar"] = run_ga(dev)
@@ -468,7 +475,7 @@ def run_native(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"single view 1237x822, {g.n} clustered SH3 Gaussians (seed 0), fwd+L1+bwd+pose",
-                   "gaussians": g.n, "views": views.n, "pixels_per_step": P, "tile": list(tile),
+                   "gaussians": g.n, "views": views.n, "pixels_per_step": P, "tile": list(tile), "batch": list(batch),
                    "instances": n_inst, "l2": "inputs larger than L2 (236 MB raw records + 64 MB projected)",
                    "graph": "one CUDA graph per step", "parallelism": f"replicas x{world}"},
         "roofline": roof,
@@ -505,9 +512,12 @@ def batched_vs_plain(dev, tile, steps=20, plain_steps=5):
     target = torch.as_tensor(rng.uniform(0, 1, views.num_image_floats()).astype(np.float32), device=dev)
     if tile == "auto":
         from paper_2509_25191_gb300.tune import autotune
-        tile, _ = autotune(g, views, target)
-    gs = GraphStep(g, views, target, tile=tile)
-    ps = PlainStep(g, views, target, tile=tile)
+        choice, _ = autotune(g, views, target)
+        tile, batch = choice.tile, choice.batch
+    else:
+        tile, batch = tile
+    gs = GraphStep(g, views, target, tile=tile, batch=batch)
+    ps = PlainStep(g, views, target, tile=tile, batch=batch)
     for _ in range(3):
         gs.replay()
         ps.run()
@@ -550,7 +560,8 @@ def batched_vs_plain(dev, tile, steps=20, plain_steps=5):
     pst = {n: round(float(t) / reps, 4) for n, t in zip(PlainStep.STAGES, pacc)}
     return {"workload": "16 views 979x546 on a radius-5 orbit, 500K clustered SH3 Gaussians (seed 0), "
                         "fwd+L1+bwd+pose", "batched_ms": round(tb, 4), "plain_ms": round(tp, 4),
-            "tile": list(tile), "batched_mpix_s": round(px / tb / 1e3, 2), "plain_mpix_s": round(px / tp / 1e3, 2),
+            "tile": list(tile), "batch": list(batch), "batched_mpix_s": round(px / tb / 1e3, 2),
+            "plain_mpix_s": round(px / tp / 1e3, 2),
             "ratio": round(tp / tb, 3), "steps": steps, "plain_steps": plain_steps,
             "batched_stages_ms": bst,
             "plain_stages_ms": pst,
@@ -580,17 +591,22 @@ def run_uneven(dev, steps=10):
     from paper_2509_25191_gb300 import _lib, synth
     from paper_2509_25191_gb300.step import GraphStep
     from paper_2509_25191_gb300.tune import autotune
+    from paper_2509_25191_gb300.layout import reorder, spatial_order
     sc, vw = synth.uneven_scenes()
+    # each scene's Gaussians in spatial (Morton) order, kept in the scene's range
     g = _lib.Gaussians.from_scene(sc, dev)
+    ranges = sorted({(int(b), int(c)) for b, c in zip(vw.gauss_begin, vw.gauss_count)})
+    g = reorder(g, spatial_order(g.means, ranges))
     views = _lib.Views.from_synth(vw, dev)
     target = torch.rand(views.num_image_floats(), device=dev, generator=torch.Generator(dev).manual_seed(5))
-    tile, _ = autotune(g, views, target, reps=3)
-    step = GraphStep(g, views, target, tile=tile)
+    choice, _ = autotune(g, views, target, reps=3)
+    step = GraphStep(g, views, target, tile=choice.tile, batch=choice.batch)
     ms = _time_replays(step, steps)
     step.rast.check_status()
+    tile = choice.tile
     return {"workload": "8 scenes 0.2M-3M SH3 Gaussians (11.7M), 32 views at mixed resolutions, fwd+L1+bwd+pose",
             "gaussians": g.n, "views": views.n, "pixels_per_step": views.pixels, "tile": list(tile),
-            "instances": int(step.bins.counters[0].item()), "ms_per_step": round(ms, 3),
+            "batch": list(choice.batch), "instances": int(step.bins.counters[0].item()), "ms_per_step": round(ms, 3),
             "mpix_s": round(views.pixels / ms / 1e3, 2)}
 
 
@@ -605,8 +621,11 @@ def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
     from paper_2509_25191_gb300 import _lib, pose, synth
     from paper_2509_25191_gb300.autograd import Rasterizer
     from paper_2509_25191_gb300.step import GraphStep
+    from paper_2509_25191_gb300.layout import reorder, spatial_order
     sc, true_v, noisy_v = synth.dense_hemisphere(0, n, n_views)
+    # the training loop keeps its Gaussians in spatial (Morton) order
     g = _lib.Gaussians.from_scene(sc, dev)
+    g = reorder(g, spatial_order(g.means))
     W, H = int(true_v.width[0]), int(true_v.height[0])
     true_vm = torch.as_tensor(true_v.viewmats, device=dev)
     noisy_vm = torch.as_tensor(noisy_v.viewmats, device=dev)
@@ -637,8 +656,9 @@ def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
 
     vm = load(0)
     from paper_2509_25191_gb300.tune import autotune
-    tile, _ = autotune(g, views, tgt_static, reps=3)
-    step = GraphStep(g, views, tgt_static, tile=tile)
+    choice, _ = autotune(g, views, tgt_static, reps=3)
+    tile = choice.tile
+    step = GraphStep(g, views, tgt_static, tile=tile, batch=choice.batch)
     # Eq. 1 update state: Adam moments per group, a pool of exploration noise
     gp = [g.means, g.log_scales, g.quats, g.opacity_logits, g.sh]
     gg = [step.grads.means, step.grads.log_scales, step.grads.quats, step.grads.opacity_logits, step.grads.sh]
@@ -677,6 +697,17 @@ def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
     if step.check():
         raise RuntimeError("capacity overflow during the dense step")
     ms = a.elapsed_time(b) / steps
+    # where the rasterizer step's time goes (eager calls, per-stage events)
+    sn = ["gs_project", "gs_bin_sort", "gs_render_fwd", "gs_l1_loss", "gs_rasterize_bwd", "gs_project_bwd",
+          "gs_pose_grad"]
+    sacc = np.zeros(len(sn))
+    for _ in range(3):
+        ev = []
+        step.run(ev)
+        torch.cuda.synchronize()
+        sacc += [ev[i].elapsed_time(ev[i + 1]) for i in range(len(sn))]
+    dense_stages = {k: round(float(v) / 3, 4) for k, v in zip(sn, sacc)}
+    graph_ms = _time_replays(step, 10)
     # the Eq. 1 update alone, against the HBM roofline (every element: read p, g, m, v; write p, m, v)
     a.record()
     for k in range(5):
@@ -694,9 +725,11 @@ def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
     return {"workload": "6M SH3 Gaussians, 300 jittered hemisphere views 1600x1066, minibatch 8, L1 vs targets, "
                         "backward to Gaussians and poses (6D + translation residuals), Eq. 1 SGLD/Adam update",
             "ms_per_step": round(ms, 3), "mpix_s": round(px / ms / 1e3, 2), "pixels_per_step": px,
+            "rasterizer_graph_ms": round(graph_ms, 3), "rasterizer_stages_ms": dense_stages,
+            "gaussian_order": "spatial (Morton) order, as the training loop keeps it",
             "sgld_adam_update": opt,
             "pose_grad_norm_last_step": round(last["pose_grad_norm"], 6),
-            "tile": list(tile), "instances": int(step.bins.counters[0].item())}
+            "tile": list(tile), "batch": list(choice.batch), "instances": int(step.bins.counters[0].item())}
 
 
 def _rel_rot_err_deg(vm_a, vm_b, pairs):

@@ -86,6 +86,10 @@ typedef struct gs_config {
     int use_tma;          /* [1] nonzero: the projection kernels stage degree-3 SH rows, records and
                              gradient rows by tensor copies where the layout allows; 0: per-thread loads
                              and stores. The results are the same bit for bit. */
+    int fwd_batch;        /* [2] Gaussians each thread stages per shared-memory batch in gs_render_fwd:
+                             1, 2 or 4 (a batch is fwd_batch x tile_w x tile_h / 2 Gaussians) */
+    int bwd_batch;        /* [1] the same for gs_rasterize_bwd: 1 or 2. Neither changes the image; the
+                             2D gradients change only in the order of their float additions. */
 } gs_config;
 
 /* Gaussians (all DEVICE, float32, contiguous). Several scenes may be
@@ -480,6 +484,18 @@ int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *views, const g
  * the call and reads it after synchronising); nothing faults or traps, and
  * the context stays usable. Returns GS_ERR_ARG for a NULL status. */
 int gs_check_bounded_wait(int32_t *status, void *stream);
+
+/* Spatial (Morton) codes of the means (data layout; no result of the
+ * rasterizer depends on the order of the Gaussians, for distinct depths).
+ * A training loop that keeps its Gaussians sorted by these codes, refreshed
+ * between densification steps, makes Gaussians that project near each other
+ * neighbours in memory: binning writes longer runs per tile and the
+ * projection backward's warps agree on which Gaussians carry a gradient.
+ * codes DEVICE uint64 [n]: each coordinate of means (DEVICE [n,3]) quantised
+ * to 21 bits in box (HOST float [6] = lo x, y, z, hi x, y, z) as
+ * min(2^21 - 1, floor((m - lo) / (hi - lo) 2^21)) (0 below lo), bits
+ * interleaved x0 y0 z0 x1 y1 z1 ...; a non-finite mean gets UINT64_MAX. */
+int gs_spatial_codes(const float *means, int64_t n, const float *box, uint64_t *codes, void *stream);
 
 /* Arithmetic-throughput probes (measurement only; the paper has no
  * counterpart): the raster kernels are bound by FP32 and special-function

@@ -27,7 +27,7 @@ EXPORTED = ["gs_config_default", "gs_num_slots", "gs_slot_base", "gs_num_tiles",
             "gs_project_bwd_noalloc", "gs_sgld_adam_step", "gs_ga_select_pairs", "gs_ga_incidence",
             "gs_ga_epipolar", "gs_ga_weights_scratch_bytes", "gs_ga_weights", "gs_ga_step", "gs_l1_dssim_loss",
             "gs_check_bounded_wait", "gs_workspace_size", "gs_workspace_carve", "gs_status_read",
-            "gs_probe_blocks", "gs_peak_probe"]
+            "gs_probe_blocks", "gs_peak_probe", "gs_spatial_codes"]
 GS_GA_MAX_CAMS = 8192
 GS_GA_PAIR_FLOATS = 12
 GS_GA_MAX_BINS = 16384
@@ -45,7 +45,7 @@ class gs_config(ctypes.Structure):
                 ("near_z", ctypes.c_float), ("dilation", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float), ("fov_clamp", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("count_pairs", ctypes.c_int), ("accumulate_grads", ctypes.c_int),
-                ("use_tma", ctypes.c_int)]
+                ("use_tma", ctypes.c_int), ("fwd_batch", ctypes.c_int), ("bwd_batch", ctypes.c_int)]
 
 
 class gs_gaussians(ctypes.Structure):
@@ -147,7 +147,7 @@ def _stream(stream):
 
 def config(tile=(16, 16), pixel_gate=True, bg=(0.0, 0.0, 0.0), near=0.2, dilation=0.3,
            alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, fov_clamp=1.3, count_pairs=False,
-           accumulate_grads=False, use_tma=True) -> gs_config:
+           accumulate_grads=False, use_tma=True, batch=(2, 1)) -> gs_config:
     c = gs_config()
     load().gs_config_default(ctypes.byref(c))
     c.tile_w, c.tile_h = int(tile[0]), int(tile[1])
@@ -158,6 +158,7 @@ def config(tile=(16, 16), pixel_gate=True, bg=(0.0, 0.0, 0.0), near=0.2, dilatio
     c.count_pairs = int(bool(count_pairs))
     c.accumulate_grads = int(bool(accumulate_grads))
     c.use_tma = int(bool(use_tma))
+    c.fwd_batch, c.bwd_batch = int(batch[0]), int(batch[1])
     return c
 
 
@@ -452,6 +453,14 @@ def gs_status_read(status, stream=None):
     out = (ctypes.c_int32 * 4)()
     _check(load().gs_status_read(_ptr(status), out, _stream(stream)), "gs_status_read")
     return list(out)
+
+
+def gs_spatial_codes(means, box, codes, stream=None):
+    """Morton codes (int64 tensor viewed as uint64) of means [n,3] in box
+    (six floats: lo xyz, hi xyz)."""
+    b = (ctypes.c_float * 6)(*[float(v) for v in box])
+    _check(load().gs_spatial_codes(_ptr(means) if means.numel() else None, ctypes.c_int64(means.shape[0]), b,
+                                   _ptr(codes) if codes.numel() else None, _stream(stream)), "gs_spatial_codes")
 
 
 def gs_peak_probe(kind, iters, out=None, stream=None):

@@ -115,6 +115,10 @@ static int build_launch(const gs_views *vw, const gs_config *cfg, Launch &L) {
     L.count_pairs = cfg->count_pairs != 0;
     L.accumulate = cfg->accumulate_grads != 0;
     L.use_tma = cfg->use_tma != 0;
+    L.fwd_batch = cfg->fwd_batch;
+    L.bwd_batch = cfg->bwd_batch;
+    if (!(L.fwd_batch == 1 || L.fwd_batch == 2 || L.fwd_batch == 4) || !(L.bwd_batch == 1 || L.bwd_batch == 2))
+        return GS_ERR_UNSUPPORTED;
     if (!(L.alpha_max > 0.f && L.alpha_max < 1.f) || !(L.t_min > 0.f)) return GS_ERR_ARG;
     long long slot = 0, pix = 0, tiles = 0;
     for (int v = 0; v < V; ++v) {
@@ -191,6 +195,8 @@ void gs_config_default(gs_config *cfg) {
     cfg->count_pairs = 0;
     cfg->accumulate_grads = 0;
     cfg->use_tma = 1;
+    cfg->fwd_batch = 2;
+    cfg->bwd_batch = 1;
 }
 
 int64_t gs_num_slots(const gs_views *vw) {

@@ -39,6 +39,7 @@ struct Launch {
     int count_pairs;        // the raster backward also counts pixel-Gaussian pairs
     int accumulate;         // the projection backward adds to the parameter gradients
     int use_tma;            // the projection kernels may stage through tensor copies
+    int fwd_batch, bwd_batch;   // Gaussians staged per thread per shared-memory batch
     float near_z, dilation, alpha_min, alpha_max, t_min, fov_clamp;
     float bg[3];
     ViewDesc v[GS_MAX_VIEWS];

@@ -11,9 +11,9 @@
 // Both kernels are persistent: blocks pull tiles from an atomic queue over
 // tile_order (largest tiles first). Each thread owns two pixels and each warp
 // an 8x8-pixel patch of the tile; a tile's instances are staged through
-// shared memory in batches (two per thread in the forward, one in the
-// backward), and a warp skips every staged Gaussian that cannot reach its
-// patch.
+// shared memory in batches (the number per thread chosen at launch: by
+// default two in the forward, one in the backward), and a warp skips every
+// staged Gaussian that cannot reach its patch.
 //
 // The backward does not store or replay transmittance: it walks the same list
 // front to back with bit-identical arithmetic (explicit-rounding intrinsics,
@@ -168,15 +168,15 @@ __device__ __forceinline__ void count_pairs(int *counters, int at, unsigned int 
     }
 }
 
-// Stage instances [b0, min(b0 + PER BS, end)) of a tile: PER per thread.
-template <int TW, int TH, int PER>
+// Stage instances [b0, min(b0 + per BS, end)) of a tile: per (1, 2 or 4)
+// per thread, the batch size chosen at launch.
+template <int TW, int TH>
 __device__ __forceinline__ void stage_batch(const Launch &L, const float4 *__restrict__ proj,
-                                            const unsigned int *__restrict__ ids, int b0, int end,
+                                            const unsigned int *__restrict__ ids, int b0, int end, int per,
                                             const TileInfo &ti, float4 *s_xy, float4 *s_con, float4 *s_rgb,
                                             unsigned int *s_mask) {
     constexpr int BS = TW * TH / 2;
-#pragma unroll
-    for (int h = 0; h < PER; ++h) {
+    for (int h = 0; h < per; ++h) {
         const int k = threadIdx.x + h * BS;
         if (b0 + k < end) {
             stage(proj, ids[b0 + k], ti.ox, ti.oy, s_xy[k], s_con[k], s_rgb[k]);
@@ -185,15 +185,24 @@ __device__ __forceinline__ void stage_batch(const Launch &L, const float4 *__res
     }
 }
 
+// Shared-memory bytes of one staged Gaussian: position, conic and colour
+// (3 x 16 B) and the warp mask; the backward adds the conic's natural-log
+// terms (8 B) and the per-Gaussian gradient sums (9 floats).
+constexpr int FWD_STAGE_BYTES = 52;
+constexpr int BWD_STAGE_BYTES = 96;
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, const float4 *__restrict__ proj,
                                                             const int2 *__restrict__ ranges,
                                                             const unsigned int *__restrict__ ids,
                                                             const int *__restrict__ order, int *__restrict__ counters,
                                                             float *__restrict__ image, int *__restrict__ last_contrib) {
-    constexpr int BS = TW * TH / 2, NB = TW * TH;
-    __shared__ float4 s_xy[NB], s_con[NB], s_rgb[NB];
-    __shared__ unsigned int s_mask[NB];
+    // the staged batch (L.fwd_batch Gaussians per thread) in dynamic shared memory
+    constexpr int BS = TW * TH / 2;
+    const int NB = L.fwd_batch * BS;
+    extern __shared__ float4 s_dyn[];
+    float4 *s_xy = s_dyn, *s_con = s_xy + NB, *s_rgb = s_con + NB;
+    unsigned int *s_mask = reinterpret_cast<unsigned int *>(s_rgb + NB);
     __shared__ int s_item;
     const bool abort = counters[CNT_ABORT] != 0;
     const unsigned int wbit = 1u << (threadIdx.x >> 5);
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
         const float2 PCY = make_float2(ti.pcy0, ti.pcy0 + 4.f);
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
             if (__syncthreads_count(done0 && done1) == BS) break;
-            stage_batch<TW, TH, 2>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
+            stage_batch<TW, TH>(L, proj, ids, b0, r.y, L.fwd_batch, ti, s_xy, s_con, s_rgb, s_mask);
             __syncthreads();
             const int nb = min(NB, r.y - b0);
             // the warp walks only the staged Gaussians that may reach its patch:
@@ -294,11 +303,17 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
                                                             float4 *__restrict__ grad2d) {
     // one staged Gaussian per thread and batch: the smaller shared-memory
     // footprint (17 KB) lets 9 blocks share an SM
-    constexpr int BS = TW * TH / 2, NB = BS;
-    __shared__ float4 s_xy[NB], s_con[NB], s_rgb[NB];
-    __shared__ float2 s_ad[NB];    // per staged Gaussian: the conic's A and D (natural-log units)
-    __shared__ unsigned int s_mask[NB];
-    __shared__ float s_g[NB][9];   // per staged Gaussian: summed gradient (odd stride: no bank conflicts)
+    // the staged batch (L.bwd_batch Gaussians per thread) in dynamic shared
+    // memory: positions, conics, colours, the conic's A and D (natural-log
+    // units), warp masks and the per-Gaussian gradient sums (pitch 9, odd:
+    // no bank conflicts)
+    constexpr int BS = TW * TH / 2;
+    const int NB = L.bwd_batch * BS;
+    extern __shared__ float4 s_dyn[];
+    float4 *s_xy = s_dyn, *s_con = s_xy + NB, *s_rgb = s_con + NB;
+    float2 *s_ad = reinterpret_cast<float2 *>(s_rgb + NB);
+    float *s_g = reinterpret_cast<float *>(s_ad + NB);
+    unsigned int *s_mask = reinterpret_cast<unsigned int *>(s_g + 9 * NB);
     __shared__ float s_red[BS / 32][32 * 9];   // per warp: the lanes' 9 values, pitch 9
     __shared__ int s_item;
     if (counters[CNT_ABORT]) return;
@@ -310,7 +325,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
     // put the 27 reading lanes on 27 different banks at every step)
     const int red_j = lane % 9, red_p = lane / 9;
     for (int k = threadIdx.x; k < NB; k += BS)
-        for (int c = 0; c < 9; ++c) s_g[k][c] = 0.f;
+        for (int c = 0; c < 9; ++c) s_g[9 * k + c] = 0.f;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counters + CNT_Q_BWD, 1);
         __syncthreads();
@@ -354,9 +369,8 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
         unsigned int n_eval = 0, n_comp = 0;
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
             if (__syncthreads_count(LAST ? b0 >= endm : done0 && done1) == BS) break;
-            stage_batch<TW, TH, 1>(L, proj, ids, b0, r.y, ti, s_xy, s_con, s_rgb, s_mask);
-#pragma unroll
-            for (int h = 0; h < 1; ++h) {
+            stage_batch<TW, TH>(L, proj, ids, b0, r.y, L.bwd_batch, ti, s_xy, s_con, s_rgb, s_mask);
+            for (int h = 0; h < L.bwd_batch; ++h) {
                 const int k = threadIdx.x + h * BS;
                 if (b0 + k < r.y)
                     s_ad[k] = make_float2(s_con[k].x * (-2.f * LN2), s_con[k].z * (-2.f * LN2));
@@ -444,20 +458,20 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
                         }
                         const float t1 = __shfl_sync(0xffffffffu, acc, (lane + 9) & 31);
                         const float t2 = __shfl_sync(0xffffffffu, acc, (lane + 18) & 31);
-                        if (lane < 9) atomicAdd(&s_g[k][lane], acc + t1 + t2);
+                        if (lane < 9) atomicAdd(&s_g[9 * k + lane], acc + t1 + t2);
                         __syncwarp();   // the buffer is free for the next Gaussian
                     }
                 }
             }
             __syncthreads();
             // flush this batch's per-Gaussian sums
-#pragma unroll
-            for (int h = 0; h < 1; ++h) {
+            for (int h = 0; h < L.bwd_batch; ++h) {
                 const int k = threadIdx.x + h * BS;
                 if (k < nb) {
-                    const float a0 = s_g[k][0], a1 = s_g[k][1], a2 = 0.5f * s_g[k][2], a3 = s_g[k][3];
-                    const float a4 = 0.5f * s_g[k][4];
-                    const float a5 = s_g[k][5], a6 = s_g[k][6], a7 = s_g[k][7], a8 = s_g[k][8];
+                    const float *sg = s_g + 9 * k;
+                    const float a0 = sg[0], a1 = sg[1], a2 = 0.5f * sg[2], a3 = sg[3];
+                    const float a4 = 0.5f * sg[4];
+                    const float a5 = sg[5], a6 = sg[6], a7 = sg[7], a8 = sg[8];
                     if (a0 != 0.f || a1 != 0.f || a2 != 0.f || a3 != 0.f || a4 != 0.f || a5 != 0.f || a6 != 0.f ||
                         a7 != 0.f || a8 != 0.f) {
                         const unsigned int slot = __float_as_uint(s_rgb[k].w);
@@ -467,7 +481,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
                         atomicAdd(dst + 2, make_float4(a8, 0.f, 0.f, 0.f));
                     }
 #pragma unroll
-                    for (int cc = 0; cc < 9; ++cc) s_g[k][cc] = 0.f;
+                    for (int cc = 0; cc < 9; ++cc) s_g[9 * k + cc] = 0.f;
                 }
             }
         }
@@ -475,18 +489,33 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
     }
 }
 
+// Resident blocks per SM of a raster kernel at the launch's block and
+// dynamic shared-memory size (cached per batch size; the attribute that
+// allows more than 48 KB of dynamic shared memory is set on first use).
+template <typename K>
+static int raster_blocks_per_sm(K kernel, int threads, size_t smem, int batch, int *cache) {
+    if (!cache[batch]) {
+        int n = 0;
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) {
+            cudaGetLastError();   // the launch itself reports a size that cannot run
+            n = 1;
+        }
+        cache[batch] = n;
+    }
+    return cache[batch];
+}
+
 template <int TW, int TH>
 static int launch_fwd_t(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st) {
-    static int blocks_per_sm = 0;
-    if (!blocks_per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_fwd<TW, TH>, TW * TH / 2, 0) !=
-                cudaSuccess || blocks_per_sm < 1)
-            blocks_per_sm = 1;
-    }
-    const int grid = min(num_sms() * blocks_per_sm, max(1, L.n_tiles));
+    static int blocks_per_sm[5];
+    const size_t smem = (size_t)FWD_STAGE_BYTES * L.fwd_batch * (TW * TH / 2);
+    const int grid = min(num_sms() * raster_blocks_per_sm(k_render_fwd<TW, TH>, TW * TH / 2, smem, L.fwd_batch,
+                                                          blocks_per_sm),
+                         max(1, L.n_tiles));
     // every call walks all tiles again: reset this kernel's work-queue head
     if (cudaMemsetAsync(b->counters + CNT_Q_FWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
-    k_render_fwd<TW, TH><<<grid, TW * TH / 2, 0, st>>>(L, reinterpret_cast<const float4 *>(proj),
+    k_render_fwd<TW, TH><<<grid, TW * TH / 2, smem, st>>>(L, reinterpret_cast<const float4 *>(proj),
                                                        reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
                                                        b->tile_order, b->counters, image, b->last_contrib);
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
@@ -495,16 +524,13 @@ static int launch_fwd_t(const Launch &L, const float *proj, const gs_bins *b, fl
 template <int TW, int TH, bool COUNT, bool LAST>
 static int launch_bwd_c(const Launch &L, const float *proj, const gs_bins *b, const float *image,
                         const float *dL_dimage, float *grad2d, cudaStream_t st) {
-    static int blocks_per_sm = 0;
-    if (!blocks_per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_render_bwd<TW, TH, COUNT, LAST>,
-                                                          TW * TH / 2, 0) != cudaSuccess ||
-            blocks_per_sm < 1)
-            blocks_per_sm = 1;
-    }
-    const int grid = min(num_sms() * blocks_per_sm, max(1, L.n_tiles));
+    static int blocks_per_sm[5];
+    const size_t smem = (size_t)BWD_STAGE_BYTES * L.bwd_batch * (TW * TH / 2);
+    const int grid = min(num_sms() * raster_blocks_per_sm(k_render_bwd<TW, TH, COUNT, LAST>, TW * TH / 2, smem,
+                                                          L.bwd_batch, blocks_per_sm),
+                         max(1, L.n_tiles));
     if (cudaMemsetAsync(b->counters + CNT_Q_BWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
-    k_render_bwd<TW, TH, COUNT, LAST><<<grid, TW * TH / 2, 0, st>>>(
+    k_render_bwd<TW, TH, COUNT, LAST><<<grid, TW * TH / 2, smem, st>>>(
         L, reinterpret_cast<const float4 *>(proj), reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
         b->tile_order, b->counters, image, dL_dimage, b->last_contrib, reinterpret_cast<float4 *>(grad2d));
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;

@@ -40,7 +40,8 @@ class GraphStep:
     KERNELS_PER_STEP = 11   # project 1, bin/sort 5, render 1, loss 1, raster bwd 1, projection bwd 1, pose 1
 
     def __init__(self, g: Gaussians, views: Views, target, tile=(16, 16), headroom=1.25, capture=True,
-                 want_gaussian_grads=True, loss="l1", lam=0.2, slots=1, slot_gaussians=False, capacity=None):
+                 want_gaussian_grads=True, loss="l1", lam=0.2, slots=1, slot_gaussians=False, capacity=None,
+                 batch=(2, 1)):
         self.g, self.views, self.target = g, views, target
         if slots < 1:
             raise ValueError("slots must be >= 1")
@@ -58,7 +59,7 @@ class GraphStep:
             raise ValueError(f"unknown loss {loss!r}")
         self.loss_kind, self.lam = loss, float(lam)
         dev = g.means.device
-        self.rast = Rasterizer(tile=tile)
+        self.rast = Rasterizer(tile=tile, batch=batch)
         if capacity is None:
             # size the instance capacity from one uncaptured forward
             _, _ = self.rast.forward(g, views)
@@ -150,7 +151,7 @@ class GraphStep:
 class PlainStep:
     """The same step, uncaptured and view by view."""
 
-    def __init__(self, g: Gaussians, views: Views, target, tile=(16, 16)):
+    def __init__(self, g: Gaussians, views: Views, target, tile=(16, 16), batch=(2, 1)):
         self.g = g
         self.one = []
         off = 0
@@ -158,7 +159,7 @@ class PlainStep:
             vv = Views(views.viewmats[v:v + 1], views.intrinsics[v:v + 1], views.width[v:v + 1],
                        views.height[v:v + 1], views.gauss_begin[v:v + 1], views.gauss_count[v:v + 1])
             n = vv.num_image_floats()
-            self.one.append((vv, target[off:off + n], Rasterizer(tile=tile)))
+            self.one.append((vv, target[off:off + n], Rasterizer(tile=tile, batch=batch)))
             off += n
         dev = g.means.device
         self.loss = torch.empty(1, device=dev)

@@ -1,5 +1,5 @@
 """Parity at the full sizes of the batched workloads, through the captured
-training step (GraphStep) at the autotuner's tile, where the oracle can
+training step (GraphStep) at the autotuner's tile and batch, where the oracle can
 afford it:
 
 * 16 views 979x546 on the radius-5 orbit of one 500K-Gaussian clustered SH3
@@ -46,8 +46,8 @@ def _run(sc, vw, per_view, seed):
     g = _lib.Gaussians.from_scene(sc)
     views = _lib.Views.from_synth(vw)
     target = torch.zeros(views.num_image_floats(), device="cuda")
-    tile, _ = autotune(g, views, target, reps=3)
-    step = GraphStep(g, views, target, tile=tile)
+    choice, _ = autotune(g, views, target, reps=3)
+    step = GraphStep(g, views, target, tile=choice.tile, batch=choice.batch)
     step.replay()
     assert step.check() is False
     torch.cuda.synchronize()
@@ -81,12 +81,12 @@ def _run(sc, vw, per_view, seed):
         check_grad(getattr(step.grads, name).cpu().numpy(), rg[name], name)
     check_grad(step.dviewmat.cpu().numpy(), dRt, "dL/d(R,t)")
     check_grad(step.dtwist.cpu().numpy(), tw, "twist")
-    return step, tile, n_up
+    return step, choice, n_up
 
 
 def test_orbit_16_views_500k_full_size():
     sc, vw = synth.orbit_views(0, 500_000, 16, 979, 546)
-    step, tile, n_up = _run(sc, vw, per_view=1500, seed=31)
+    step, choice, n_up = _run(sc, vw, per_view=1500, seed=31)
     assert n_up > 5000
     assert int(step.bins.counters[0].item()) > 1_000_000
 
@@ -94,7 +94,7 @@ def test_orbit_16_views_500k_full_size():
 def test_dense_minibatch_8_views_6m_full_size():
     sc, true_v, noisy_v = synth.dense_hemisphere(0)
     vw = noisy_v.select(synth.minibatch(0, noisy_v.n, 8))
-    step, tile, n_up = _run(sc, vw, per_view=1000, seed=41)
+    step, choice, n_up = _run(sc, vw, per_view=1000, seed=41)
     assert n_up > 2000
     assert int(step.bins.counters[0].item()) > 50_000_000
     assert int(step.bins.counters[6].item()) > 4 * SORT_ON_CHIP   # the largest tile takes the partition pass

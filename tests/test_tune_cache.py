@@ -1,5 +1,6 @@
-"""The autotuner's result cache (host logic, no GPU): a cached workload
-signature returns its tile and timings without timing anything."""
+"""The autotuner's result cache and candidate set (host logic, no GPU): a
+cached workload signature returns its (tile, batch) choice and timings
+without timing anything."""
 import json
 
 from paper_2509_25191_gb300 import tune
@@ -7,8 +8,8 @@ from paper_2509_25191_gb300 import tune
 
 def test_cached_signature_short_circuits_the_search(tmp_path, monkeypatch):
     path = tmp_path / "tune.json"
-    path.write_text(json.dumps({"GB300|n2^20|v1|px2^20|sh3": {"tile": [32, 16],
-                                                               "ms": {"32x16": 0.87, "16x16": 0.93}}}))
+    path.write_text(json.dumps({"GB300|n2^20|v1|px2^20|sh3": {"best": "32x16/2.1",
+                                                               "ms": {"32x16/2.1": 0.87, "16x16/1.1": 0.93}}}))
     monkeypatch.setattr(tune, "signature", lambda g, views: "GB300|n2^20|v1|px2^20|sh3")
 
     def no_step(*a, **k):
@@ -16,7 +17,16 @@ def test_cached_signature_short_circuits_the_search(tmp_path, monkeypatch):
 
     monkeypatch.setattr(tune, "GraphStep", no_step)
     best, times = tune.autotune(None, None, None, cache_path=str(path))
-    assert best == (32, 16) and times == {(32, 16): 0.87, (16, 16): 0.93}
+    assert best == tune.Choice((32, 16), (2, 1)) and best.tile == (32, 16) and best.batch == (2, 1)
+    assert times == {tune.Choice((32, 16), (2, 1)): 0.87, tune.Choice((16, 16), (1, 1)): 0.93}
+
+
+def test_candidates_cover_every_tile_and_batch():
+    cands = tune.candidates()
+    assert len(cands) == len(tune.TILES) * len(tune.BATCHES) == len(set(cands))
+    assert tune.Choice((32, 16), tune.DEFAULT_BATCH) in cands
+    for c in cands:
+        assert tune.parse_key(tune.key_str(c)) == c
 
 
 def test_unreadable_cache_is_ignored(tmp_path):
