@@ -49,6 +49,10 @@ FWD_FLOPS_EVAL, BWD_FLOPS_EVAL = 12, 40
 FWD_OPS_EVAL, FWD_OPS_COMP = 10, 9
 BWD_OPS_EVAL, BWD_OPS_COMP = 10, 50
 FP32_LANES_PER_SM = 128
+# tile shapes the autotuner tries on the large secondary workloads (uneven
+# scenes, dense step), where each candidate step is expensive to build: the
+# shapes that won on any workload measured so far (every batch is tried)
+SECONDARY_TILES = ((16, 16), (32, 16), (32, 32))
 
 
 # DRAM traffic per launch of the raster backward (dram__bytes_read.sum +
@@ -599,7 +603,7 @@ def run_uneven(dev, steps=10):
     g = reorder(g, spatial_order(g.means, ranges))
     views = _lib.Views.from_synth(vw, dev)
     target = torch.rand(views.num_image_floats(), device=dev, generator=torch.Generator(dev).manual_seed(5))
-    choice, _ = autotune(g, views, target, reps=3)
+    choice, _ = autotune(g, views, target, tiles=SECONDARY_TILES, reps=3)
     step = GraphStep(g, views, target, tile=choice.tile, batch=choice.batch)
     ms = _time_replays(step, steps)
     step.rast.check_status()
@@ -656,7 +660,7 @@ def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
 
     vm = load(0)
     from paper_2509_25191_gb300.tune import autotune
-    choice, _ = autotune(g, views, tgt_static, reps=3)
+    choice, _ = autotune(g, views, tgt_static, tiles=SECONDARY_TILES, reps=3)
     tile = choice.tile
     step = GraphStep(g, views, tgt_static, tile=tile, batch=choice.batch)
     # Eq. 1 update state: Adam moments per group, a pool of exploration noise

@@ -301,8 +301,6 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
                                                             const float *__restrict__ dL_dimage,
                                                             const int *__restrict__ last_contrib,
                                                             float4 *__restrict__ grad2d) {
-    // one staged Gaussian per thread and batch: the smaller shared-memory
-    // footprint (17 KB) lets 9 blocks share an SM
     // the staged batch (L.bwd_batch Gaussians per thread) in dynamic shared
     // memory: positions, conics, colours, the conic's A and D (natural-log
     // units), warp masks and the per-Gaussian gradient sums (pitch 9, odd:

@@ -38,7 +38,7 @@ def _range_order(m: torch.Tensor) -> torch.Tensor:
     mf = m[finite] if not bool(finite.all()) else m
     lo = mf.min(dim=0).values.tolist() if mf.numel() else [0.0, 0.0, 0.0]
     hi = mf.max(dim=0).values.tolist() if mf.numel() else [0.0, 0.0, 0.0]
-    codes = torch.empty(count, dtype=torch.int64, device=means.device)
+    codes = torch.empty(count, dtype=torch.int64, device=m.device)
     _lib.gs_spatial_codes(m, lo + hi, codes)
     # the codes are unsigned: flip the top bit so that signed order is their order
     key = codes ^ torch.iinfo(torch.int64).min
