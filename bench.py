@@ -60,7 +60,7 @@ SECONDARY_TILES = ((16, 16), (32, 16), (32, 32))
 # workload). It holds only for the kernel source it was measured on (hash of
 # its two source files) and for the default workload and tile; otherwise the
 # bench reports null.
-RASTER_BWD_TRAFFIC = {"bytes": 51968000, "sources_sha256_16": "99e3c618f09b48d9", "n": 1_000_000,
+RASTER_BWD_TRAFFIC = {"bytes": 55859456, "sources_sha256_16": "93d319c6d68d0120", "n": 1_000_000,
                       "tile": (32, 16), "batch": (2, 1)}
 
 
@@ -89,8 +89,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-ga", action="store_true", help="skip the global-alignment workload")
-    ap.add_argument("--only", choices=["ga"], default=None,
-                    help="run only the named secondary workload and print its figures (for profiling)")
+    ap.add_argument("--only", choices=["ga", "oracle_views"], default=None,
+                    help="run only the named secondary workload and print its figures (for profiling); "
+                         "oracle_views times the FP64 oracle on one view of each configuration")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the uneven multi-scene batch and the dense-view joint pose step")
     ap.add_argument("--ref-fraction", type=float, default=1.0,
@@ -457,6 +458,17 @@ def run_native(args, rank, world, local_rank):
     dssim["loss_kernel_ms"] = round(ev0.elapsed_time(ev1) / 20, 4)
     dssim["loss"] = [round(float(v), 6) for v in dstep.loss.cpu()]
     del dstep
+    # the small configuration (2,000 SH0 Gaussians, one 128x128 view), captured the same way
+    from paper_2509_25191_gb300 import synth as _synth
+    ssc, svw = _synth.single_view_small()
+    sg = _lib.Gaussians.from_scene(ssc, dev)
+    sv = _lib.Views.from_synth(svw, dev)
+    sstep = GraphStep(sg, sv, torch.rand(sv.num_image_floats(), device=dev, generator=torch.Generator(dev).manual_seed(3)),
+                      tile=(16, 16))
+    small = {"workload": "2,000 SH0 Gaussians uniform in a box, one 128x128 view, fwd+L1+bwd+pose, 16x16 tiles",
+             "ms_per_step": round(_time_replays(sstep, 200), 4)}
+    small["mpix_s"] = round(sv.pixels / small["ms_per_step"] / 1e3, 2)
+    del sstep
     # test-time pose tuning (Gaussians frozen): the same step with the backward to the pose only
     pstep = GraphStep(g, views, target, tile=tile, batch=batch, want_gaussian_grads=False)
     pose_only = {"ms_per_step": round(_time_replays(pstep, 50), 4)}
@@ -491,6 +503,7 @@ def run_native(args, rank, world, local_rank):
         "autotune": tuning,
         "clocks": clocks,
         "pose_only_step": pose_only,
+        "small_case": small,
         "l1_dssim_step": dssim,
         "batched_vs_plain": batched,
         "other_workloads": extra,
@@ -828,6 +841,39 @@ def oracle_step(sc, vw, fraction, seed):
     return W * H if mask is None else int(mask.sum())
 
 
+def oracle_views():
+    """The FP64 oracle (single thread) on one whole view of each
+    configuration: projection, binning and render forward of every pixel,
+    the mean-L1 gradient against a uniform target, render and projection
+    backward and the pose gradient; per view, labelled, not extrapolated."""
+    from paper_2509_25191_gb300 import synth
+    out = {}
+    cases = [("2,000 SH0 Gaussians, 128x128", lambda: synth.single_view_small()),
+             ("1M clustered SH3, 1237x822", lambda: synth.single_view_1m(0)),
+             ("500K clustered SH3, view 0 of the 16-view 979x546 orbit",
+              lambda: (lambda sc, vw: (sc, vw.select([0])))(*synth.orbit_views(0, 500_000, 16, 979, 546))),
+             ("uneven scenes: the 3M-Gaussian scene, its first view",
+              lambda: _uneven_first_view()),
+             ("6M SH3 dense scene, view 0 of minibatch 0 (1600x1066)",
+              lambda: (lambda sc, tv, nv: (sc, nv.select(synth.minibatch(0, nv.n, 8)[:1])))(*synth.dense_hemisphere(0)))]
+    for name, make in cases:
+        sc, vw = make()
+        t = time.perf_counter()
+        px = oracle_step(sc, vw, 1.0, 7)
+        out[name] = {"seconds_per_view": round(time.perf_counter() - t, 2), "pixels": px, "threads": 1}
+    return out
+
+
+def _uneven_first_view():
+    from paper_2509_25191_gb300 import synth
+    sc, vw = synth.uneven_scenes()
+    v = int(np.argmax(vw.gauss_count))
+    b, c = int(vw.gauss_begin[v]), int(vw.gauss_count[v])
+    one = vw.select([v])
+    one.gauss_begin[:] = 0
+    return sc.subset(np.arange(b, b + c)), one
+
+
 def cpu_baseline(sc, vw):
     t = time.perf_counter()
     npx = oracle_step(sc, vw, 1.0, 7)
@@ -908,6 +954,11 @@ def main():
     if args.only == "ga":
         import torch
         print(json.dumps(run_ga(torch.device("cuda", local_rank))), flush=True)
+        return
+    if args.only == "oracle_views":
+        from oracle import oracle as O
+        O.build()
+        print(json.dumps({"oracle_per_view": oracle_views()}), flush=True)
         return
     if world > 1:
         import torch
