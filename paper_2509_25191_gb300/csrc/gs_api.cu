@@ -5,9 +5,22 @@
 #include <math.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gs_common.cuh"
 
 namespace gsk {
+
+// A named NVTX range around each entry point that enqueues work, so that a
+// profiler's timeline shows which library call launched which kernels (the
+// header-only NVTX library does nothing unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define GS_TRACE() gsk::NvtxRange gs_trace_range_(__func__)
 
 int launch_project(const Launch &L, int deg, const gs_gaussians *g, const float *viewmats, const float *intr,
                    float *proj, int32_t *status, cudaStream_t st);
@@ -294,6 +307,7 @@ int gs_workspace_carve(const gs_views *vw, const gs_config *cfg, int64_t n_gauss
 }
 
 int gs_status_read(const int32_t *status, int32_t *host_status, void *stream) {
+    GS_TRACE();
     if (!status || !host_status) return GS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemcpyAsync(host_status, status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -303,6 +317,7 @@ int gs_status_read(const int32_t *status, int32_t *host_status, void *stream) {
 
 int gs_project(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, float *proj, int32_t *status,
                void *stream) {
+    GS_TRACE();
     Launch L;
     int rc = build_launch(vw, cfg, L);
     if (rc) return rc;
@@ -314,6 +329,7 @@ int gs_project(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, 
 
 int gs_bin_sort(const gs_views *vw, const gs_config *cfg, const float *proj, const gs_bins *b, int32_t *status,
                 void *stream) {
+    GS_TRACE();
     Launch L;
     int rc = build_launch(vw, cfg, L);
     if (rc) return rc;
@@ -326,6 +342,7 @@ int gs_bin_sort(const gs_views *vw, const gs_config *cfg, const float *proj, con
 
 int gs_render_fwd(const gs_views *vw, const gs_config *cfg, const float *proj, const gs_bins *b, float *image,
                   int32_t *status, void *stream) {
+    GS_TRACE();
     (void)status;
     Launch L;
     int rc = build_launch(vw, cfg, L);
@@ -337,6 +354,7 @@ int gs_render_fwd(const gs_views *vw, const gs_config *cfg, const float *proj, c
 int gs_rasterize_bwd(const gs_views *vw, const gs_config *cfg, const float *proj, const gs_bins *b,
                      const float *image, const float *dL_dimage, float *grad2d, int32_t *status,
                      void *stream) {
+    GS_TRACE();
     Launch L;
     int rc = build_launch(vw, cfg, L);
     if (rc) return rc;
@@ -354,6 +372,7 @@ int gs_rasterize_bwd(const gs_views *vw, const gs_config *cfg, const float *proj
 int gs_project_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, const float *proj,
                    const float *grad2d, const gs_grads *out, int want_gaussian_grads, int32_t *status,
                    void *stream) {
+    GS_TRACE();
     Launch L;
     int rc = build_launch(vw, cfg, L);
     if (rc) return rc;
@@ -386,6 +405,7 @@ int gs_project_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *c
 int gs_render_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, const float *proj,
                   const gs_bins *b, const float *image, const float *dL_dimage, const gs_grads *out,
                   int want_gaussian_grads, int32_t *status, void *stream) {
+    GS_TRACE();
     if (!out) return GS_ERR_ARG;
     int rc = check_gaussians(g, vw);
     if (rc) return rc;
@@ -396,6 +416,7 @@ int gs_render_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *cf
 
 int gs_pose_grad(const gs_views *vw, const float *pose_partials, int n_blocks, float *dL_dviewmat,
                  float *dL_dtwist, void *stream) {
+    GS_TRACE();
     if (!vw || vw->n_views < 1 || vw->n_views > GS_MAX_VIEWS || !pose_partials || !dL_dviewmat || n_blocks < 1 ||
         !vw->viewmats)
         return GS_ERR_ARG;
@@ -405,12 +426,14 @@ int gs_pose_grad(const gs_views *vw, const float *pose_partials, int n_blocks, f
 
 int gs_l1_loss(const float *image, const float *target, int64_t count, float *loss, float *dL_dimage,
                void *stream) {
+    GS_TRACE();
     if (count < 0 || !loss || (count > 0 && (!image || !target || !dL_dimage))) return GS_ERR_ARG;
     return launch_l1(image, target, count, loss, dL_dimage, (cudaStream_t)stream);
 }
 
 int gs_sgld_adam_step(const gs_adam_group *groups, int n_groups, int step, double beta1, double beta2, double eps,
                       const float *noise, float noise_scale, int noise_group, void *stream) {
+    GS_TRACE();
     if (!groups || n_groups < 1 || n_groups > GS_MAX_ADAM_GROUPS || step < 1) return GS_ERR_ARG;
     if (!(beta1 >= 0.0 && beta1 < 1.0 && beta2 >= 0.0 && beta2 < 1.0 && eps >= 0.0)) return GS_ERR_ARG;
     for (int k = 0; k < n_groups; ++k) {
@@ -424,6 +447,7 @@ int gs_sgld_adam_step(const gs_adam_group *groups, int n_groups, int step, doubl
 
 int gs_l1_dssim_loss(const gs_views *views, const float *image, const float *target, float lambda, float *loss,
                      float *dL_dimage, void *stream) {
+    GS_TRACE();
     if (!views || views->n_views < 1 || views->n_views > GS_MAX_VIEWS || !views->width || !views->height ||
         !image || !target || !loss || !dL_dimage || !(lambda >= 0.f && lambda <= 1.f))
         return GS_ERR_ARG;
@@ -436,6 +460,7 @@ int gs_l1_dssim_loss(const gs_views *views, const float *image, const float *tar
 
 int gs_ga_select_pairs(const float *viewmats, int n_cams, double max_angle_deg, int32_t *pairs, int64_t capacity,
                        int64_t *n_pairs_out, int32_t *status, void *stream) {
+    GS_TRACE();
     if (!viewmats || n_cams < 1 || n_cams > GS_GA_MAX_CAMS || capacity < 0 || (capacity > 0 && !pairs) ||
         !n_pairs_out || !(max_angle_deg > 0.0 && max_angle_deg <= 180.0))
         return GS_ERR_ARG;
@@ -446,6 +471,7 @@ int gs_ga_select_pairs(const float *viewmats, int n_cams, double max_angle_deg, 
 
 int gs_ga_incidence(const int32_t *pairs, int64_t n_pairs, int n_cams, int32_t *cam_offsets, int32_t *cam_pairs,
                     int32_t *status, void *stream) {
+    GS_TRACE();
     if (n_cams < 1 || n_cams > GS_GA_MAX_CAMS || n_pairs < 0 || 2 * n_pairs > 0x7fffffffLL || !cam_offsets ||
         (n_pairs > 0 && (!pairs || !cam_pairs)))
         return GS_ERR_ARG;
@@ -455,6 +481,7 @@ int gs_ga_incidence(const int32_t *pairs, int64_t n_pairs, int n_cams, int32_t *
 int gs_ga_epipolar(const gs_ga_problem *p, float *dist, float *pair_sums, const int32_t *cam_offsets,
                    const int32_t *cam_pairs, float *loss, float *d_intrinsics, float *d_viewmats, int32_t *status,
                    void *stream) {
+    GS_TRACE();
     if (!p || p->n_cams < 1 || p->n_cams > GS_GA_MAX_CAMS || !p->intrinsics || !p->viewmats || p->n_pairs < 0 ||
         p->n_matches < 0 || !loss || 2 * p->n_pairs > 0x7fffffffLL)
         return GS_ERR_ARG;
@@ -469,6 +496,7 @@ int gs_ga_epipolar(const gs_ga_problem *p, float *dist, float *pair_sums, const 
 
 int gs_ga_step(const gs_ga_state *s, const gs_ga_problem *p, float *pair_sums, const int32_t *cam_offsets,
                const int32_t *cam_pairs, float *loss, float *d_residuals, int32_t *status, void *stream) {
+    GS_TRACE();
     if (!s || !p || s->n_cams != p->n_cams || !s->intrinsics0 || !s->viewmats0 || !s->residuals || !s->exp_avg ||
         !s->exp_avg_sq || !s->step || !s->intrinsics || !s->viewmats || p->intrinsics != s->intrinsics ||
         p->viewmats != s->viewmats)
@@ -491,6 +519,7 @@ size_t gs_ga_weights_scratch_bytes(int n_bins) {
 
 int gs_ga_weights(const float *dist, int64_t n, int n_bins, double alpha, uint32_t *counts, float *weights,
                   float *stats, void *scratch, void *stream) {
+    GS_TRACE();
     if (n < 0 || n > 0xffffffffLL || n_bins < 1 || n_bins > GS_GA_MAX_BINS || !(alpha >= 0.0) || !counts ||
         !stats || !scratch || (n > 0 && (!dist || !weights)))
         return GS_ERR_ARG;
@@ -555,6 +584,7 @@ extern "C" int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *vw,
                                       const float *proj, const float *grad2d, const gs_grads *grads,
                                       int want_gaussian_grads, float *dL_dviewmat, float *dL_dtwist,
                                       int32_t *status, void *stream) {
+    GS_TRACE();
     Launch L;
     int rc = build_launch(vw, cfg, L);
     if (rc) return rc;
@@ -610,6 +640,7 @@ __global__ void k_wait_check(int32_t *status) {
 }  // namespace gsk
 
 extern "C" int gs_check_bounded_wait(int32_t *status, void *stream) {
+    GS_TRACE();
     if (!status) return GS_ERR_ARG;
     gsk::k_wait_check<<<1, 32, 0, (cudaStream_t)stream>>>(status);
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
