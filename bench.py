@@ -574,6 +574,9 @@ def batched_vs_plain(dev, tile, steps=20, plain_steps=5):
             e = ev[v * (k + 1):(v + 1) * (k + 1)]
             pacc += [e[i].elapsed_time(e[i + 1]) for i in range(k)]
     bst = {n: round(float(t) / reps, 4) for n, t in zip(bn, bacc)}
+    peaks, _ = measured_peaks()
+    bbytes = algorithmic_bytes(g.n, g.sh_degree, views.num_slots(), int(gs.bins.counters[0].item()), px,
+                               views.num_tiles(gs.cfg))
     pst = {n: round(float(t) / reps, 4) for n, t in zip(PlainStep.STAGES, pacc)}
     return {"workload": "16 views 979x546 on a radius-5 orbit, 500K clustered SH3 Gaussians (seed 0), "
                         "fwd+L1+bwd+pose", "batched_ms": round(tb, 4), "plain_ms": round(tp, 4),
@@ -581,6 +584,8 @@ def batched_vs_plain(dev, tile, steps=20, plain_steps=5):
             "plain_mpix_s": round(px / tp / 1e3, 2),
             "ratio": round(tp / tb, 3), "steps": steps, "plain_steps": plain_steps,
             "batched_stages_ms": bst,
+            "batched_hbm_roofline": {"algorithmic_bytes": int(bbytes),
+                                     "frac": round(bbytes / (tb * 1e-3) / (peaks["hbm_gbs"] * 1e9), 4)},
             "plain_stages_ms": pst,
             "plain_definition": "the same library called view by view, uncaptured, each call with the instance-count "
                                 "readback an uncaptured call needs (bin_sort includes it)"}
@@ -621,9 +626,14 @@ def run_uneven(dev, steps=10):
     ms = _time_replays(step, steps)
     step.rast.check_status()
     tile = choice.tile
+    peaks, _ = measured_peaks()
+    ubytes = algorithmic_bytes(g.n, g.sh_degree, views.num_slots(), int(step.bins.counters[0].item()), views.pixels,
+                               views.num_tiles(step.cfg))
     return {"workload": "8 scenes 0.2M-3M SH3 Gaussians (11.7M), 32 views at mixed resolutions, fwd+L1+bwd+pose",
             "gaussians": g.n, "views": views.n, "pixels_per_step": views.pixels, "tile": list(tile),
             "batch": list(choice.batch), "instances": int(step.bins.counters[0].item()), "ms_per_step": round(ms, 3),
+            "hbm_roofline": {"algorithmic_bytes": int(ubytes),
+                             "frac": round(ubytes / (ms * 1e-3) / (peaks["hbm_gbs"] * 1e9), 4)},
             "mpix_s": round(views.pixels / ms / 1e3, 2)}
 
 
@@ -725,6 +735,8 @@ def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
         sacc += [ev[i].elapsed_time(ev[i + 1]) for i in range(len(sn))]
     dense_stages = {k: round(float(v) / 3, 4) for k, v in zip(sn, sacc)}
     graph_ms = _time_replays(step, 10)
+    dbytes = algorithmic_bytes(g.n, g.sh_degree, views.num_slots(), int(step.bins.counters[0].item()), views.pixels,
+                               views.num_tiles(step.cfg))
     # the Eq. 1 update alone, against the HBM roofline (every element: read p, g, m, v; write p, m, v)
     a.record()
     for k in range(5):
@@ -743,6 +755,9 @@ def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
                         "backward to Gaussians and poses (6D + translation residuals), Eq. 1 SGLD/Adam update",
             "ms_per_step": round(ms, 3), "mpix_s": round(px / ms / 1e3, 2), "pixels_per_step": px,
             "rasterizer_graph_ms": round(graph_ms, 3), "rasterizer_stages_ms": dense_stages,
+            "rasterizer_hbm_roofline": {"algorithmic_bytes": int(dbytes),
+                                        "frac": round(dbytes / (graph_ms * 1e-3) / (measured_peaks()[0]["hbm_gbs"] * 1e9),
+                                                      4)},
             "gaussian_order": "spatial (Morton) order, as the training loop keeps it",
             "sgld_adam_update": opt,
             "pose_grad_norm_last_step": round(last["pose_grad_norm"], 6),
@@ -824,20 +839,21 @@ def run_ga(dev, iterations=300, reps=50):
 # the oracle on the host cores
 # ---------------------------------------------------------------------------
 
-def oracle_step(sc, vw, fraction, seed):
+def oracle_step(sc, vw, fraction, seed, threads=1):
     """One oracle fwd + L1 + bwd + pose pass over a random pixel sample (all
     pixels if fraction >= 1), against the native arm's target image (uniform
-    values, seed 1234). Returns the number of pixels computed."""
+    values, seed 1234); threads > 1 splits its projection and render passes
+    over that many threads. Returns the number of pixels computed."""
     from oracle import oracle as O
     W, H = int(vw.width[0]), int(vw.height[0])
     rng = np.random.default_rng(seed)
     mask = None if fraction >= 1 else rng.random((H, W)) < fraction
-    f = O.forward(sc, vw, masks=None if mask is None else [mask])
+    f = O.forward(sc, vw, masks=None if mask is None else [mask], threads=threads)
     target = np.random.default_rng(1234).uniform(0, 1, 3 * W * H).astype(np.float32).reshape(3, H, W)
     up = np.sign(f[0]["image"] - target) / (3.0 * W * H)          # the mean-L1 gradient
     if mask is not None:
         up[:, ~mask] = 0.0
-    O.backward(sc, vw, f, [up])
+    O.backward(sc, vw, f, [up], threads=threads)
     return W * H if mask is None else int(mask.sum())
 
 
@@ -875,23 +891,33 @@ def _uneven_first_view():
 
 
 def cpu_baseline(sc, vw):
+    """The FP64 oracle on the host: one full step threaded over all cores
+    (the reported value) and one single-threaded, and the small workload."""
+    cores = os.cpu_count() or 1
     t = time.perf_counter()
-    npx = oracle_step(sc, vw, 1.0, 7)
+    npx = oracle_step(sc, vw, 1.0, 7, threads=cores)
     dt = time.perf_counter() - t
-    out = {"value": round(npx / dt / 1e6, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"one full step: all {npx} pixels of the same workload, FP64 C oracle, single thread",
-           "seconds": round(dt, 2)}
+    t = time.perf_counter()
+    oracle_step(sc, vw, 1.0, 7)
+    dt1 = time.perf_counter() - t
+    out = {"value": round(npx / dt / 1e6, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"one full step: all {npx} pixels of the same workload, FP64 C oracle, projection and render "
+                     f"passes threaded over {cores} host cores (binning single-threaded)",
+           "seconds": round(dt, 2),
+           "single_thread": {"seconds": round(dt1, 2), "mpix_s": round(npx / dt1 / 1e6, 6)}}
     # the small 2,000-Gaussian 128x128 case as well (full step, single thread)
     from paper_2509_25191_gb300 import synth
     ssc, svw = synth.single_view_small()
-    t = time.perf_counter()
-    reps = 0
-    while time.perf_counter() - t < 1.0:
-        spx = oracle_step(ssc, svw, 1.0, 7 + reps)
-        reps += 1
-    sdt = (time.perf_counter() - t) / reps
-    out["small_case"] = {"workload": "2,000 SH0 Gaussians, one 128x128 view", "mpix_s": round(spx / sdt / 1e6, 6),
-                         "ms_per_step": round(sdt * 1e3, 3)}
+    for threads in (1, cores):
+        t = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t < 1.0:
+            spx = oracle_step(ssc, svw, 1.0, 7 + reps, threads=threads)
+            reps += 1
+        sdt = (time.perf_counter() - t) / reps
+        out["small_case" if threads == 1 else "small_case_threaded"] = {
+            "workload": "2,000 SH0 Gaussians, one 128x128 view", "threads": threads,
+            "mpix_s": round(spx / sdt / 1e6, 6), "ms_per_step": round(sdt * 1e3, 3)}
     return out
 
 

@@ -739,3 +739,223 @@ void or_pose_twist(const double *R, const double *t, const double *gR, const dou
     twist[4] = M[2] - M[6];
     twist[5] = M[3] - M[1];
 }
+
+/* ------------------------------------------------------------------------ */
+/* Threaded variants, for timing the oracle on all host cores (the tests    */
+/* check them against the single-threaded functions above): the same       */
+/* per-Gaussian or per-pixel work split over threads -- Gaussians in        */
+/* contiguous chunks, pixels by interleaved rows of tiles -- with partial   */
+/* sums combined in thread order.                                          */
+/* ------------------------------------------------------------------------ */
+#include <pthread.h>
+
+#define OR_MAX_THREADS 256
+
+typedef struct {
+    int tid, nth;
+    int64_t n;
+    int deg;
+    const double *means, *log_scales, *quats, *logits, *sh;
+    const or_cam *cam;
+    const or_params *P;
+    /* projection outputs */
+    double *xy, *depth, *conic, *cov, *opac, *rgb, *r_real, *ext;
+    int32_t *radius, *clamped;
+    /* projection backward */
+    const double *g2d;
+    double *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh, gR[9], gt[3];
+    /* rendering */
+    const double *cxy, *cconic, *copac, *crgb, *cr_real, *cdepth;
+    const int32_t *cradius, *ids;
+    const int64_t *ranges;
+    int W, H, TW, TH;
+    const uint8_t *mask;
+    double *img, *T_final;
+    int32_t *n_contrib, *flags;
+    const double *dL_dimg;
+    double *g2d_out;
+} or_job;
+
+static void chunk(int64_t n, int tid, int nth, int64_t *b, int64_t *e)
+{
+    *b = n * tid / nth;
+    *e = n * (tid + 1) / nth;
+}
+
+static void *project_worker(void *arg)
+{
+    or_job *j = (or_job *)arg;
+    int K = (j->deg + 1) * (j->deg + 1);
+    int64_t b, e;
+    chunk(j->n, j->tid, j->nth, &b, &e);
+    or_project(e - b, j->deg, j->means + 3 * b, j->log_scales + 3 * b, j->quats + 4 * b, j->logits + b,
+               j->sh + 3 * K * b, j->cam, j->P, j->xy + 2 * b, j->depth + b, j->conic + 3 * b, j->cov + 3 * b,
+               j->opac + b, j->rgb + 3 * b, j->radius + b, j->r_real + b, j->clamped + 3 * b, j->ext + 2 * b);
+    return NULL;
+}
+
+static void *project_bwd_worker(void *arg)
+{
+    or_job *j = (or_job *)arg;
+    int K = (j->deg + 1) * (j->deg + 1);
+    int64_t b, e;
+    chunk(j->n, j->tid, j->nth, &b, &e);
+    for (int a = 0; a < 9; ++a) j->gR[a] = 0.0;
+    for (int a = 0; a < 3; ++a) j->gt[a] = 0.0;
+    or_project_bwd(e - b, j->deg, j->means + 3 * b, j->log_scales + 3 * b, j->quats + 4 * b, j->logits + b,
+                   j->sh + 3 * K * b, j->cam, j->P, j->g2d + 9 * b, j->g_means + 3 * b, j->g_log_scales + 3 * b,
+                   j->g_quats + 4 * b, j->g_logits + b, j->g_sh + 3 * K * b, j->gR, j->gt);
+    return NULL;
+}
+
+static void *render_worker(void *arg)
+{
+    or_job *j = (or_job *)arg;
+    int Gx = (j->W + j->TW - 1) / j->TW, Gy = (j->H + j->TH - 1) / j->TH;
+    for (int ty = j->tid; ty < Gy; ty += j->nth)
+        for (int py = ty * j->TH; py < (ty + 1) * j->TH && py < j->H; ++py)
+            for (int px = 0; px < j->W; ++px) {
+                if (j->mask && !j->mask[(int64_t)py * j->W + px]) continue;
+                int64_t t = (int64_t)(py / j->TH) * Gx + px / j->TW;
+                double C[3], T;
+                int fl;
+                int nh = composite_pixel(px, py, j->ranges[2 * t], j->ranges[2 * t + 1], j->ids, j->cxy, j->cconic,
+                                         j->copac, j->crgb, j->cradius, j->cr_real, j->cdepth, j->P, NULL, C, &T,
+                                         &fl);
+                int64_t p = (int64_t)py * j->W + px;
+                for (int ch = 0; ch < 3; ++ch) j->img[(int64_t)ch * j->W * j->H + p] = C[ch] + T * j->P->bg[ch];
+                j->T_final[p] = T;
+                j->n_contrib[p] = nh;
+                j->flags[p] = fl;
+            }
+    return NULL;
+}
+
+/* one thread's pixels (interleaved rows of tiles) of or_render_bwd, into
+ * its own g2d_out */
+static void *render_bwd_worker(void *arg)
+{
+    or_job *j = (or_job *)arg;
+    int Gx = (j->W + j->TW - 1) / j->TW, Gy = (j->H + j->TH - 1) / j->TH;
+    /* a copy of the image gradient that is zero outside this thread's rows:
+     * or_render_bwd skips pixels whose upstream gradient is zero */
+    int64_t WH = (int64_t)j->W * j->H;
+    double *up = (double *)calloc((size_t)(3 * WH), sizeof(double));
+    if (!up) return (void *)1;
+    for (int ty = j->tid; ty < Gy; ty += j->nth)
+        for (int py = ty * j->TH; py < (ty + 1) * j->TH && py < j->H; ++py)
+            for (int ch = 0; ch < 3; ++ch)
+                memcpy(up + ch * WH + (int64_t)py * j->W, j->dL_dimg + ch * WH + (int64_t)py * j->W,
+                       sizeof(double) * (size_t)j->W);
+    (void)Gx;
+    or_render_bwd(j->n, j->cxy, j->cconic, j->copac, j->crgb, j->cradius, j->cdepth, j->W, j->H, j->TW, j->TH,
+                  j->ranges, j->ids, j->P, up, j->g2d_out);
+    free(up);
+    return NULL;
+}
+
+static int run_jobs(or_job *jobs, int nth, void *(*fn)(void *))
+{
+    pthread_t th[OR_MAX_THREADS];
+    int started = 0, rc = 0;
+    for (int t = 1; t < nth; ++t) {
+        if (pthread_create(&th[t], NULL, fn, &jobs[t]) != 0) break;
+        started = t;
+    }
+    for (int t = started + 1; t < nth; ++t) fn(&jobs[t]);   /* threads that could not start run here */
+    if (fn(&jobs[0])) rc = 1;
+    for (int t = 1; t <= started; ++t) {
+        void *r = NULL;
+        pthread_join(th[t], &r);
+        if (r) rc = 1;
+    }
+    return rc;
+}
+
+static int clamp_threads(int nth) { return nth < 1 ? 1 : (nth > OR_MAX_THREADS ? OR_MAX_THREADS : nth); }
+
+void or_project_mt(int64_t n, int deg, const double *means, const double *log_scales, const double *quats,
+                   const double *logits, const double *sh, const or_cam *cam, const or_params *P, double *xy,
+                   double *depth, double *conic, double *cov, double *opac, double *rgb, int32_t *radius,
+                   double *r_real, int32_t *clamped, double *ext, int nth)
+{
+    nth = clamp_threads(nth);
+    or_job jobs[OR_MAX_THREADS];
+    for (int t = 0; t < nth; ++t) {
+        or_job *j = &jobs[t];
+        memset(j, 0, sizeof *j);
+        j->tid = t; j->nth = nth; j->n = n; j->deg = deg;
+        j->means = means; j->log_scales = log_scales; j->quats = quats; j->logits = logits; j->sh = sh;
+        j->cam = cam; j->P = P;
+        j->xy = xy; j->depth = depth; j->conic = conic; j->cov = cov; j->opac = opac; j->rgb = rgb;
+        j->radius = radius; j->r_real = r_real; j->clamped = clamped; j->ext = ext;
+    }
+    run_jobs(jobs, nth, project_worker);
+}
+
+void or_project_bwd_mt(int64_t n, int deg, const double *means, const double *log_scales, const double *quats,
+                       const double *logits, const double *sh, const or_cam *cam, const or_params *P,
+                       const double *g2d, double *g_means, double *g_log_scales, double *g_quats, double *g_logits,
+                       double *g_sh, double *gR, double *gt, int nth)
+{
+    nth = clamp_threads(nth);
+    or_job jobs[OR_MAX_THREADS];
+    for (int t = 0; t < nth; ++t) {
+        or_job *j = &jobs[t];
+        memset(j, 0, sizeof *j);
+        j->tid = t; j->nth = nth; j->n = n; j->deg = deg;
+        j->means = means; j->log_scales = log_scales; j->quats = quats; j->logits = logits; j->sh = sh;
+        j->cam = cam; j->P = P; j->g2d = g2d;
+        j->g_means = g_means; j->g_log_scales = g_log_scales; j->g_quats = g_quats; j->g_logits = g_logits;
+        j->g_sh = g_sh;
+    }
+    run_jobs(jobs, nth, project_bwd_worker);
+    for (int t = 0; t < nth; ++t) {
+        for (int a = 0; a < 9; ++a) gR[a] += jobs[t].gR[a];
+        for (int a = 0; a < 3; ++a) gt[a] += jobs[t].gt[a];
+    }
+}
+
+void or_render_mt(const double *xy, const double *conic, const double *opac, const double *rgb,
+                  const int32_t *radius, const double *r_real, const double *depth, int W, int H, int TW, int TH,
+                  const int64_t *ranges, const int32_t *ids, const or_params *P, const uint8_t *mask, double *img,
+                  double *T_final, int32_t *n_contrib, int32_t *flags, int nth)
+{
+    nth = clamp_threads(nth);
+    or_job jobs[OR_MAX_THREADS];
+    for (int t = 0; t < nth; ++t) {
+        or_job *j = &jobs[t];
+        memset(j, 0, sizeof *j);
+        j->tid = t; j->nth = nth; j->P = P;
+        j->cxy = xy; j->cconic = conic; j->copac = opac; j->crgb = rgb; j->cradius = radius; j->cr_real = r_real;
+        j->cdepth = depth; j->W = W; j->H = H; j->TW = TW; j->TH = TH; j->ranges = ranges; j->ids = ids;
+        j->mask = mask; j->img = img; j->T_final = T_final; j->n_contrib = n_contrib; j->flags = flags;
+    }
+    run_jobs(jobs, nth, render_worker);
+}
+
+/* returns 0, or 1 if a thread could not allocate its scratch (g2d is then
+ * incomplete) */
+int or_render_bwd_mt(int64_t n, const double *xy, const double *conic, const double *opac, const double *rgb,
+                     const int32_t *radius, const double *depth, int W, int H, int TW, int TH,
+                     const int64_t *ranges, const int32_t *ids, const or_params *P, const double *dL_dimg,
+                     double *g2d, int nth)
+{
+    nth = clamp_threads(nth);
+    or_job jobs[OR_MAX_THREADS];
+    double *part = (double *)calloc((size_t)nth * (size_t)(9 * (n > 0 ? n : 1)), sizeof(double));
+    if (!part) return 1;
+    for (int t = 0; t < nth; ++t) {
+        or_job *j = &jobs[t];
+        memset(j, 0, sizeof *j);
+        j->tid = t; j->nth = nth; j->n = n; j->P = P;
+        j->cxy = xy; j->cconic = conic; j->copac = opac; j->crgb = rgb; j->cradius = radius; j->cdepth = depth;
+        j->W = W; j->H = H; j->TW = TW; j->TH = TH; j->ranges = ranges; j->ids = ids; j->dL_dimg = dL_dimg;
+        j->g2d_out = part + (size_t)t * (size_t)(9 * n);
+    }
+    int rc = run_jobs(jobs, nth, render_bwd_worker);
+    for (int t = 0; t < nth; ++t)
+        for (int64_t k = 0; k < 9 * n; ++k) g2d[k] += part[(size_t)t * (size_t)(9 * n) + (size_t)k];
+    free(part);
+    return rc;
+}

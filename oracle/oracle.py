@@ -51,7 +51,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                               "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -146,8 +146,9 @@ def _scene_arrays(scene, begin=0, count=None):
             _f64(scene.opacity_logits[sl]), _f64(scene.sh[sl]))
 
 
-def project_view(scene, views, v, params: Params = None):
-    """Projection of the Gaussians view ``v`` sees (local indices)."""
+def project_view(scene, views, v, params: Params = None, threads: int = 1):
+    """Projection of the Gaussians view ``v`` sees (local indices); with
+    threads > 1 the same work split over that many threads (for timing)."""
     params = params or Params()
     b, c = int(views.gauss_begin[v]), int(views.gauss_count[v])
     means, ls, q, lg, sh = _scene_arrays(scene, b, c)
@@ -157,10 +158,14 @@ def project_view(scene, views, v, params: Params = None):
                r_real=np.zeros(n), clamped=np.zeros((n, 3), np.int32), ext=np.zeros((n, 2)))
     cam = view_camera(views, v)
     prm = params.c()
-    lib().or_project(ctypes.c_int64(n), ctypes.c_int(scene.sh_degree), _p(means), _p(ls), _p(q), _p(lg),
-                     _p(sh), ctypes.byref(cam), ctypes.byref(prm),
-                     _p(out["xy"]), _p(out["depth"]), _p(out["conic"]), _p(out["cov"]), _p(out["opac"]),
-                     _p(out["rgb"]), _p(out["radius"]), _p(out["r_real"]), _p(out["clamped"]), _p(out["ext"]))
+    args = (ctypes.c_int64(n), ctypes.c_int(scene.sh_degree), _p(means), _p(ls), _p(q), _p(lg),
+            _p(sh), ctypes.byref(cam), ctypes.byref(prm),
+            _p(out["xy"]), _p(out["depth"]), _p(out["conic"]), _p(out["cov"]), _p(out["opac"]),
+            _p(out["rgb"]), _p(out["radius"]), _p(out["r_real"]), _p(out["clamped"]), _p(out["ext"]))
+    if threads > 1:
+        lib().or_project_mt(*args, ctypes.c_int(threads))
+    else:
+        lib().or_project(*args)
     return out
 
 
@@ -206,8 +211,9 @@ def bins_for_render(proj, W, H, TW, TH, params: Params = None):
     return bin_view(proj["xy"][:, 0], proj["xy"][:, 1], r, proj["depth"], W, H, TW, TH, ext)
 
 
-def render_view(proj, W, H, TW=16, TH=16, params: Params = None, bins=None, mask=None):
-    """mask: optional [H,W] bool; only those pixels are computed (others 0)."""
+def render_view(proj, W, H, TW=16, TH=16, params: Params = None, bins=None, mask=None, threads: int = 1):
+    """mask: optional [H,W] bool; only those pixels are computed (others 0).
+    threads > 1: rows of tiles interleaved over that many threads (timing)."""
     params = params or Params()
     if bins is None:
         bins = bins_for_render(proj, W, H, TW, TH, params)
@@ -218,14 +224,18 @@ def render_view(proj, W, H, TW=16, TH=16, params: Params = None, bins=None, mask
     fl = np.zeros((H, W), np.int32)
     prm = params.c()
     m = None if mask is None else np.ascontiguousarray(mask, np.uint8)
-    lib().or_render(_p(proj["xy"]), _p(proj["conic"]), _p(proj["opac"]), _p(proj["rgb"]),
-                    _p(proj["radius"]), _p(proj["r_real"]), _p(proj["depth"]), W, H, TW, TH,
-                    _p(np.ascontiguousarray(ranges)), _p(np.ascontiguousarray(ids)), ctypes.byref(prm),
-                    None if m is None else _p(m), _p(img), _p(T), _p(nc), _p(fl))
+    args = (_p(proj["xy"]), _p(proj["conic"]), _p(proj["opac"]), _p(proj["rgb"]),
+            _p(proj["radius"]), _p(proj["r_real"]), _p(proj["depth"]), W, H, TW, TH,
+            _p(np.ascontiguousarray(ranges)), _p(np.ascontiguousarray(ids)), ctypes.byref(prm),
+            None if m is None else _p(m), _p(img), _p(T), _p(nc), _p(fl))
+    if threads > 1:
+        lib().or_render_mt(*args, ctypes.c_int(threads))
+    else:
+        lib().or_render(*args)
     return dict(image=img, T=T, n_contrib=nc, flags=fl)
 
 
-def render_bwd_view(proj, W, H, dL_dimg, TW=16, TH=16, params: Params = None, bins=None):
+def render_bwd_view(proj, W, H, dL_dimg, TW=16, TH=16, params: Params = None, bins=None, threads: int = 1):
     params = params or Params()
     if bins is None:
         bins = bins_for_render(proj, W, H, TW, TH, params)
@@ -233,14 +243,19 @@ def render_bwd_view(proj, W, H, dL_dimg, TW=16, TH=16, params: Params = None, bi
     n = proj["xy"].shape[0]
     g2d = np.zeros((n, 9))
     prm = params.c()
-    lib().or_render_bwd(ctypes.c_int64(n), _p(proj["xy"]), _p(proj["conic"]), _p(proj["opac"]),
-                        _p(proj["rgb"]), _p(proj["radius"]), _p(proj["depth"]), W, H, TW, TH,
-                        _p(np.ascontiguousarray(ranges)), _p(np.ascontiguousarray(ids)), ctypes.byref(prm),
-                        _p(_f64(dL_dimg)), _p(g2d))
+    args = (ctypes.c_int64(n), _p(proj["xy"]), _p(proj["conic"]), _p(proj["opac"]),
+            _p(proj["rgb"]), _p(proj["radius"]), _p(proj["depth"]), W, H, TW, TH,
+            _p(np.ascontiguousarray(ranges)), _p(np.ascontiguousarray(ids)), ctypes.byref(prm),
+            _p(_f64(dL_dimg)), _p(g2d))
+    if threads > 1:
+        if lib().or_render_bwd_mt(*args, ctypes.c_int(threads)) != 0:
+            raise MemoryError("or_render_bwd_mt: per-thread scratch")
+    else:
+        lib().or_render_bwd(*args)
     return g2d
 
 
-def project_bwd_view(scene, views, v, g2d, params: Params = None):
+def project_bwd_view(scene, views, v, g2d, params: Params = None, threads: int = 1):
     """Raw-parameter gradients of the Gaussians view ``v`` sees (local
     indices) and the view's dL/dR [9], dL/dt [3]."""
     params = params or Params()
@@ -253,10 +268,14 @@ def project_bwd_view(scene, views, v, g2d, params: Params = None):
     gt = np.zeros(3)
     cam = view_camera(views, v)
     prm = params.c()
-    lib().or_project_bwd(ctypes.c_int64(c), ctypes.c_int(scene.sh_degree), _p(means), _p(ls), _p(q), _p(lg),
-                         _p(sh), ctypes.byref(cam), ctypes.byref(prm), _p(_f64(g2d)),
-                         _p(out["means"]), _p(out["log_scales"]), _p(out["quats"]),
-                         _p(out["opacity_logits"]), _p(out["sh"]), _p(gR), _p(gt))
+    args = (ctypes.c_int64(c), ctypes.c_int(scene.sh_degree), _p(means), _p(ls), _p(q), _p(lg),
+            _p(sh), ctypes.byref(cam), ctypes.byref(prm), _p(_f64(g2d)),
+            _p(out["means"]), _p(out["log_scales"]), _p(out["quats"]),
+            _p(out["opacity_logits"]), _p(out["sh"]), _p(gR), _p(gt))
+    if threads > 1:
+        lib().or_project_bwd_mt(*args, ctypes.c_int(threads))
+    else:
+        lib().or_project_bwd(*args)
     return out, gR, gt
 
 
@@ -273,25 +292,28 @@ def pose_twist(viewmat, gR, gt):
 # whole-path helpers
 # ---------------------------------------------------------------------------
 
-def forward(scene, views, TW=16, TH=16, params: Params = None, masks=None):
+def forward(scene, views, TW=16, TH=16, params: Params = None, masks=None, threads: int = 1):
     """Per view: projection, tile lists and rendering. Returns a list of dicts
     with keys proj, bins, image [3,H,W], T, n_contrib, flags. masks: optional
-    per-view [H,W] bool arrays restricting the rendered pixels."""
+    per-view [H,W] bool arrays restricting the rendered pixels. threads > 1
+    splits projection and rendering over that many threads (for timing; the
+    binning stays single-threaded)."""
     params = params or Params()
     out = []
     for v in range(views.n):
         W, H = int(views.width[v]), int(views.height[v])
-        proj = project_view(scene, views, v, params)
+        proj = project_view(scene, views, v, params, threads)
         bins = bins_for_render(proj, W, H, TW, TH, params)
-        r = render_view(proj, W, H, TW, TH, params, bins, None if masks is None else masks[v])
+        r = render_view(proj, W, H, TW, TH, params, bins, None if masks is None else masks[v], threads)
         r.update(proj=proj, bins=bins)
         out.append(r)
     return out
 
 
-def backward(scene, views, fwd, dL_dimgs, TW=16, TH=16, params: Params = None):
+def backward(scene, views, fwd, dL_dimgs, TW=16, TH=16, params: Params = None, threads: int = 1):
     """Gradients of sum_v <dL_dimgs[v], image_v> w.r.t. every raw parameter
-    (global indexing) and every view's R, t (dL_dRt [V,12]) and twist [V,6]."""
+    (global indexing) and every view's R, t (dL_dRt [V,12]) and twist [V,6];
+    threads > 1 as in forward()."""
     params = params or Params()
     K = (scene.sh_degree + 1) ** 2
     N = scene.n
@@ -303,9 +325,9 @@ def backward(scene, views, fwd, dL_dimgs, TW=16, TH=16, params: Params = None):
     for v in range(views.n):
         W, H = int(views.width[v]), int(views.height[v])
         f = fwd[v]
-        g2d = render_bwd_view(f["proj"], W, H, dL_dimgs[v], TW, TH, params, f["bins"])
+        g2d = render_bwd_view(f["proj"], W, H, dL_dimgs[v], TW, TH, params, f["bins"], threads)
         g2ds.append(g2d)
-        gv, gR, gt = project_bwd_view(scene, views, v, g2d, params)
+        gv, gR, gt = project_bwd_view(scene, views, v, g2d, params, threads)
         b, c = int(views.gauss_begin[v]), int(views.gauss_count[v])
         for k in grads:
             grads[k][b:b + c] += gv[k]
