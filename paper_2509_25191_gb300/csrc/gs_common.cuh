@@ -333,6 +333,14 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 // make this thread's generic shared-memory writes visible to bulk copies
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only),
+// tracked per thread; cp_async_wait_all makes this thread's copies visible
+// to this thread
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // 16-byte chunk c of row r of a box staged with the 128-byte swizzle (rows
 // of 128 bytes) or the 64-byte swizzle (rows of 64 bytes): the hardware XORs
 // the chunk index with address bits 7..9 (7..8), so a thread reading chunk c

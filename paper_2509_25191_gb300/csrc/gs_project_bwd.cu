@@ -2,11 +2,13 @@
 // parameters and camera poses.
 //
 // One thread per Gaussian (fixed grid, grid-stride), looping over the views of
-// its scene: the Gaussian's parameters are read once, its gradients are summed
-// over views in registers and written once (overwritten, or added to the
-// caller's values when the configuration accumulates). For degree-3 SH the
-// block's SH rows and first-view 2D-gradient rows arrive by tensor copies and
-// its SH-coefficient gradients leave by tensor stores (see PbStage). Each view's pose
+// its scene: the Gaussian's parameters are read once (for one-view calls only
+// if it has a nonzero 2D gradient: see LAZY), its gradients are summed over
+// views in registers and written once (overwritten, or added to the caller's
+// values when the configuration accumulates). For degree-3 SH the block's
+// first-view 2D-gradient rows arrive by a tensor copy, the SH rows are staged
+// in shared memory, and the block's SH-coefficient gradients leave by tensor
+// stores (see PbStage). Each view's pose
 // gradient (dL/dR, dL/dt; Section 3.4 needs it for the pose residuals) is
 // summed over a warp with shuffles, kept per warp in shared memory, and
 // written as one partial per block; k_pose_reduce then sums the partials in a
@@ -32,10 +34,12 @@ __device__ __forceinline__ void put(float *p, float v, bool acc) { *p = acc ? *p
 constexpr int PB_WARPS = PB_THREADS / 32;
 
 // Staging of a block's 128 Gaussians on the degree-3 path: the SH rows arrive
-// by two tensor copies (a 32-float box with the 128-byte swizzle and a
-// 16-float box with the 64-byte swizzle: a thread reads its own row 16 bytes
-// at a time without bank conflicts), and the SH-coefficient gradients are
-// summed over views in the same layout and leave by two tensor stores.
+// as a 32-float box with the 128-byte swizzle and a 16-float box with the
+// 64-byte swizzle (a thread reads its own row 16 bytes at a time without bank
+// conflicts) -- by two tensor copies for the whole block, or (LAZY) copied
+// into the same layout by each contributing Gaussian's thread -- and the
+// SH-coefficient gradients are summed over views in the same layout and leave
+// by two tensor stores.
 struct PbStage {
     float4 shA[PB_THREADS * 8];
     float4 shB[PB_THREADS * 4];
@@ -45,7 +49,13 @@ struct PbStage {
     unsigned long long bar;
 };
 
-template <int DEG, bool GAUSS, bool TMA>
+// LAZY: read a Gaussian's parameters (and stage its SH row) only if some view
+// gives it a nonzero 2D gradient, found by a first pass over its 2D-gradient
+// rows. It pays where few Gaussians contribute (one view of a dense scene:
+// most Gaussians are hidden behind saturated pixels); with many views most
+// Gaussians contribute somewhere and the block-wide tensor copies of the SH
+// rows are faster, so the launch chooses LAZY for one-view calls.
+template <int DEG, bool GAUSS, bool TMA, bool LAZY>
 __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
     const Launch L, const float *__restrict__ means, const float *__restrict__ log_scales,
     const float *__restrict__ quats, const float *__restrict__ logits, const float *__restrict__ sh,
@@ -104,9 +114,11 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                 if (GAUSS) bulk_wait_read_all();
                 if (full) {
                     fence_async_smem();
-                    mbar_expect_tx(&S[0].bar, PB_THREADS * ((acc_rows ? 96 : 48) + 12) * 4);
-                    tma_load_2d(S[0].shA, &tm_shA, 0, row0, &S[0].bar);
-                    tma_load_2d(S[0].shB, &tm_shB, 32, row0, &S[0].bar);
+                    mbar_expect_tx(&S[0].bar, PB_THREADS * ((acc_rows ? 48 : 0) + (LAZY ? 0 : 48) + 12) * 4);
+                    if (!LAZY) {
+                        tma_load_2d(S[0].shA, &tm_shA, 0, row0, &S[0].bar);
+                        tma_load_2d(S[0].shB, &tm_shB, 32, row0, &S[0].bar);
+                    }
                     const int srow = (int)(L.v[v_first].slot_base + base - L.s[scene_of_thread(L, base)].thread_base);
                     tma_load_2d(S[0].g2d, &tm_g2d, 0, srow, &S[0].bar);
                     if (acc_rows) {
@@ -116,7 +128,7 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                 }
             }
             __syncthreads();
-            if (!full && valid) {
+            if (!LAZY && !full && valid) {
                 // a partial iteration stages its rows itself, in the same layout
                 const float4 *src = reinterpret_cast<const float4 *>(sh + 48LL * i);
 #pragma unroll
@@ -135,32 +147,17 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
             }
         }
 
+        // The Gaussian's parameters are read, and its activations formed, only
+        // if some view gives it a nonzero 2D gradient: most Gaussians of a
+        // dense scene are hidden behind saturated pixels in every view and
+        // only get (zero) gradients written. Otherwise the values below give
+        // exact zeros in the gradient formulas.
         float mx = 0.f, my = 0.f, mz = 0.f, sc[3] = {0.f, 0.f, 0.f}, qn[4] = {1.f, 0.f, 0.f, 0.f}, qlen = 1.f;
         float Rq[9], M[9], S00 = 0, S01 = 0, S02 = 0, S11 = 0, S12 = 0, S22 = 0, opac = 0.f;
+        bool loaded = false;
         // SH coefficients are read per view where needed (L1-resident or
         // staged), not held in registers
         const float *f = sh + (long long)3 * K * (valid ? i : 0);
-        if (valid) {
-            mx = means[3 * i]; my = means[3 * i + 1]; mz = means[3 * i + 2];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) sc[a] = expf(log_scales[3 * i + a]);
-            const float4 q = reinterpret_cast<const float4 *>(quats)[i];
-            qlen = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-            const float iq = 1.f / qlen;
-            qn[0] = q.x * iq; qn[1] = q.y * iq; qn[2] = q.z * iq; qn[3] = q.w * iq;
-            opac = 1.f / (1.f + expf(-logits[i]));
-        }
-        quat_rot(qn[0], qn[1], qn[2], qn[3], Rq);
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) M[3 * a + b] = Rq[3 * a + b] * sc[b];
-        S00 = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
-        S01 = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
-        S02 = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
-        S11 = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
-        S12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
-        S22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
 
         // accumulators over views
         float gm[3] = {0.f, 0.f, 0.f}, go = 0.f;
@@ -189,9 +186,67 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                     return;
                 }
             } else {
-                __syncthreads();   // the partial iteration's rows are staged
+                __syncthreads();   // the partial iteration's gradient rows are initialised
             }
         }
+
+        // does any view give this Gaussian a nonzero 2D gradient? (the first
+        // view's rows are staged; the loop below reads them all again)
+        if (!LAZY) loaded = valid;
+        if (LAZY && valid) {
+            for (int v = vb; v < ve && !loaded; ++v) {
+                const long long slot = L.v[v].slot_base + li;
+                const bool staged = TMA && full && v == v_first;
+                const float4 a4 = staged ? S[0].g2d[3 * r] : grad2d[3 * slot];
+                const float4 b4 = staged ? S[0].g2d[3 * r + 1] : grad2d[3 * slot + 1];
+                const float c0 = staged ? S[0].g2d[3 * r + 2].x : grad2d[3 * slot + 2].x;
+                // nonzero iff some value has nonzero magnitude bits
+                const unsigned int bits = __float_as_uint(a4.x) | __float_as_uint(a4.y) | __float_as_uint(a4.z) |
+                                          __float_as_uint(a4.w) | __float_as_uint(b4.x) | __float_as_uint(b4.y) |
+                                          __float_as_uint(b4.z) | __float_as_uint(b4.w) | __float_as_uint(c0);
+                loaded = (bits & 0x7fffffffu) != 0u;
+            }
+        }
+        // only the loads are conditional; the activations are formed from the
+        // loaded values or from defaults that make every gradient term zero
+        float l3[3] = {0.f, 0.f, 0.f}, lg = 0.f;
+        float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
+        if (loaded) {
+            mx = means[3 * i]; my = means[3 * i + 1]; mz = means[3 * i + 2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) l3[a] = log_scales[3 * i + a];
+            q = reinterpret_cast<const float4 *>(quats)[i];
+            lg = logits[i];
+            if constexpr (TMA && LAZY) {
+                // this thread's SH row into its swizzled staging row (read only
+                // by this thread), by asynchronous copies
+                const float4 *src = reinterpret_cast<const float4 *>(sh + 48LL * i);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) cp_async16(&S[0].shA[swz128(r, c)], src + c);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) cp_async16(&S[0].shB[swz64(r, c)], src + 8 + c);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sc[a] = loaded ? expf(l3[a]) : 0.f;
+        qlen = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+        {
+            const float iq = 1.f / qlen;
+            qn[0] = q.x * iq; qn[1] = q.y * iq; qn[2] = q.z * iq; qn[3] = q.w * iq;
+        }
+        opac = loaded ? 1.f / (1.f + expf(-lg)) : 0.f;
+        quat_rot(qn[0], qn[1], qn[2], qn[3], Rq);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) M[3 * a + b] = Rq[3 * a + b] * sc[b];
+        S00 = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+        S01 = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+        S02 = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+        S11 = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+        S12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+        S22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+        if constexpr (TMA && LAZY) cp_async_wait_all();
 
         for (int v = wvb; v < wve; ++v) {
             float pg[12];
@@ -392,7 +447,8 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
             }
         }
 
-        if (valid && GAUSS) {
+        // (with accumulation a Gaussian without a gradient has nothing to add)
+        if (valid && GAUSS && (loaded || !L.accumulate)) {
             // Sigma = M M^T: dL/dM = 2 GS M (GS symmetric)
             const float GSf[9] = {GS00, GS01, GS02, GS01, GS11, GS12, GS02, GS12, GS22};
             float gs[3] = {0.f, 0.f, 0.f}, GRq[9];
@@ -491,15 +547,17 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
     CUtensorMap ma, mb, ga, gb, m2;
     memset(&ma, 0, sizeof ma); memset(&mb, 0, sizeof mb); memset(&ga, 0, sizeof ga); memset(&gb, 0, sizeof gb);
     memset(&m2, 0, sizeof m2);
+    // one-view calls read only the contributing Gaussians' parameters (see LAZY)
+    const bool lazy = L.n_views == 1;
     // degree 3 with 16-byte aligned SH rows and gradient rows: the staged
     // path, unless the configuration turns tensor copies off. The pose-only
     // backward reads SH rows only for Gaussians with a nonzero 2D gradient,
     // which the per-thread path does (measured faster there: 46 vs 63 us at
     // 1M Gaussians)
-    bool tma = want_gauss && deg == 3 && L.use_tma && ((uintptr_t)g->sh & 15u) == 0 &&
-               g->n < 0x7fffffffLL &&
-               encode_tmap_2d(&ma, g->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
-               encode_tmap_2d(&mb, g->sh, 48, (uint64_t)g->n, 192, 16, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_64B);
+    bool tma = want_gauss && deg == 3 && L.use_tma && ((uintptr_t)g->sh & 15u) == 0 && g->n < 0x7fffffffLL &&
+               (lazy ||
+                (encode_tmap_2d(&ma, g->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
+                 encode_tmap_2d(&mb, g->sh, 48, (uint64_t)g->n, 192, 16, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_64B)));
     if (tma)
         tma = L.n_slots < 0x7fffffffLL &&
               encode_tmap_2d(&m2, grad2d, 12, (uint64_t)L.n_slots, 48, 12, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_NONE);
@@ -507,24 +565,32 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
         tma = ((uintptr_t)out->sh & 15u) == 0 &&
               encode_tmap_2d(&ga, out->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
               encode_tmap_2d(&gb, out->sh, 48, (uint64_t)g->n, 192, 16, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_64B);
-#define GS_PB(D, G, T)                                                                                             \
-    k_project_bwd<D, G, T><<<nblk, PB_THREADS, dyn, st>>>(                                                         \
+#define GS_PB(D, G, T, Z)                                                                                          \
+    k_project_bwd<D, G, T, Z><<<nblk, PB_THREADS, dyn, st>>>(                                                      \
         L, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, viewmats, intr, p, g2, out->means,        \
         out->log_scales, out->quats, out->opacity_logits, out->sh, out->pose_partials, ma, mb, ga, gb, m2, status)
     if (want_gauss) {
         switch (deg) {
-        case 0: GS_PB(0, true, false); break;
-        case 1: GS_PB(1, true, false); break;
-        case 2: GS_PB(2, true, false); break;
-        case 3: if (tma) GS_PB(3, true, true); else GS_PB(3, true, false); break;
+        case 0: if (lazy) GS_PB(0, true, false, true); else GS_PB(0, true, false, false); break;
+        case 1: if (lazy) GS_PB(1, true, false, true); else GS_PB(1, true, false, false); break;
+        case 2: if (lazy) GS_PB(2, true, false, true); else GS_PB(2, true, false, false); break;
+        case 3:
+            if (tma) {
+                if (lazy) GS_PB(3, true, true, true); else GS_PB(3, true, true, false);
+            } else {
+                if (lazy) GS_PB(3, true, false, true); else GS_PB(3, true, false, false);
+            }
+            break;
         default: return GS_ERR_UNSUPPORTED;
         }
     } else {
+        // the pose-only backward reads a Gaussian's parameters only in its
+        // contributing views already (per-thread path)
         switch (deg) {
-        case 0: GS_PB(0, false, false); break;
-        case 1: GS_PB(1, false, false); break;
-        case 2: GS_PB(2, false, false); break;
-        case 3: GS_PB(3, false, false); break;
+        case 0: GS_PB(0, false, false, false); break;
+        case 1: GS_PB(1, false, false, false); break;
+        case 2: GS_PB(2, false, false, false); break;
+        case 3: GS_PB(3, false, false, false); break;
         default: return GS_ERR_UNSUPPORTED;
         }
     }
