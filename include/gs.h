@@ -126,7 +126,8 @@ typedef struct gs_bins {
     uint32_t *ids;        /* [capacity] slot of each instance, same order as keys */
     uint64_t *keys_tmp;   /* [capacity] scratch for tiles too large for on-chip sorting */
     int32_t *tile_order;  /* [T] work order: tiles by decreasing instance count */
-    int32_t *tile_scratch;/* [T] scratch (per-tile counters) */
+    int32_t *tile_scratch;/* [5T] scratch (per-tile counters, then the runs of large tiles that
+                             are sorted in pieces) */
     int32_t *counters;    /* [GS_NUM_COUNTERS] scratch; counters[0] = instances after the call;
                              int64 at counters+8: pixel-Gaussian pairs evaluated by gs_render_fwd,
                              +10: composited by it, +12/+14: the same for gs_rasterize_bwd */

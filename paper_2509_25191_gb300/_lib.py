@@ -243,7 +243,7 @@ class Bins:
         i32 = dict(dtype=torch.int32, device=device)
         self.tile_ranges = torch.empty(max(1, self.n_tiles) * 2, **i32)
         self.tile_order = torch.empty(max(1, self.n_tiles), **i32)
-        self.tile_scratch = torch.empty(max(1, self.n_tiles), **i32)
+        self.tile_scratch = torch.empty(max(1, 5 * self.n_tiles), **i32)
         self.counters = torch.zeros(GS_NUM_COUNTERS, **i32)
         cap = max(1, self.capacity)
         self.keys = torch.empty(cap, dtype=torch.int64, device=device)

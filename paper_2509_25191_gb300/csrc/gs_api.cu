@@ -268,7 +268,7 @@ static size_t ws_layout(const gs_views *vw, const gs_config *cfg, int64_t n, int
         sizeof(uint32_t) * (size_t)c,                            // ids
         sizeof(uint64_t) * (size_t)c,                            // keys_tmp
         sizeof(int32_t) * (size_t)(T > 0 ? T : 1),               // tile_order
-        sizeof(int32_t) * (size_t)(T > 0 ? T : 1),               // tile_scratch
+        sizeof(int32_t) * 5 * (size_t)(T > 0 ? T : 1),           // tile_scratch
         sizeof(int32_t) * GS_NUM_COUNTERS,                       // counters
         sizeof(int32_t) * (size_t)(px > 0 ? px : 1),             // last_contrib
         sizeof(float) * GS_GRAD2D_FLOATS * (size_t)(P > 0 ? P : 1),                      // grad2d

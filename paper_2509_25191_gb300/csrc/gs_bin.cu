@@ -18,14 +18,13 @@
 //                  check, and a work order of tiles by decreasing count
 //   k_bin_scatter  writes keys inside the reserved ranges, placement by
 //                  shared-memory atomics
-//   k_sort_tiles   persistent, largest tiles first; radix sort on chip
-//                  (a tile above 4096 instances is first partitioned by
-//                  depth, and runs of partitions are sorted on chip)
+//   k_split_large  tiles far above the sort's work per block: partitioned
+//                  by depth into runs of bins, listed for the sort
+//   k_sort_tiles   persistent, one queue: the runs, then the other tiles
+//                  largest first; radix sort on chip
 #include "gs_common.cuh"
 
 namespace gsk {
-
-constexpr int LARGE_BUCKET = 13;        // bucket of counts >= 4096 (chunked sort)
 
 // Slots are processed in chunks of BIN_CHUNK per block. Within a chunk, the
 // tile counts of each view segment are first gathered in a shared-memory
@@ -218,19 +217,18 @@ __global__ void __launch_bounds__(1024) k_bin_scan(const Launch L, long long cap
     if (lane == 0) atomicMax(counters + CNT_MAX_TILE, m);
     __syncthreads();
     if (tid == 0) {
-        int acc = 0, large = 0;
+        int acc = 0;
         for (int b = 33; b >= 0; --b) {   // decreasing counts first
             s_base[b] = acc;
             acc += s_hist[b];
-            if (b >= LARGE_BUCKET) large += s_hist[b];
         }
         counters[CNT_INSTANCES] = (int)min(total, 0x7fffffffLL);
         counters[CNT_ABORT] = abort ? 1 : 0;
         counters[CNT_Q_FWD] = 0;
         counters[CNT_Q_BWD] = 0;
         counters[CNT_Q_SORT] = 0;
-        counters[CNT_Q_SORT_L] = 0;
-        counters[CNT_LARGE_TILES] = large;
+        counters[CNT_RUN_RES] = 0;
+        counters[CNT_Q_SPLIT] = 0;
         if (abort && status) {
             status[0] = too_many ? GS_ERR_OVERFLOW : GS_ERR_CAPACITY;
             status[1] = (int)(total & 0xffffffffLL);
@@ -419,6 +417,7 @@ __device__ void radix_sort_tile(SortSmem &S, const unsigned long long *src, unsi
     if (threadIdx.x == 0) { S.kmin = 0xffffffffu; S.kmax = 0u; }
     __syncthreads();
     unsigned int lmin = 0xffffffffu, lmax = 0u;
+#pragma unroll 4
     for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
         const unsigned long long k = src[st + i];
         const unsigned int d = (unsigned int)(k >> 32);
@@ -427,8 +426,12 @@ __device__ void radix_sort_tile(SortSmem &S, const unsigned long long *src, unsi
         lmin = min(lmin, d);
         lmax = max(lmax, d);
     }
-    atomicMin(&S.kmin, lmin);
-    atomicMax(&S.kmax, lmax);
+    lmin = __reduce_min_sync(0xffffffffu, lmin);
+    lmax = __reduce_max_sync(0xffffffffu, lmax);
+    if (lane == 0) {
+        atomicMin(&S.kmin, lmin);
+        atomicMax(&S.kmax, lmax);
+    }
     __syncthreads();
     // Radix-sort a 16-bit monotone compression of the depth bits,
     // (bits - kmin) >> shift, then order each run of equal compressed keys by
@@ -572,22 +575,271 @@ __device__ void sort_segment_merge(SortSmem &S, unsigned long long *keys, unsign
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_tiles(const Launch L, const int2 *__restrict__ ranges,
+// Large tiles (above SORT_CAP instances) are cut into runs of consecutive
+// depth bins that are sorted independently, so that one large tile is sorted
+// by many blocks at once (sorted by its own block, the largest tile alone set
+// the sort's length). k_split_large partitions each large tile by the top 8
+// bits of (depth bits - tile minimum) into keys_tmp (bins in depth order) and
+// appends its runs -- stretches of consecutive bins of about SORT_SPLIT_RUN
+// keys (see list_runs) -- to a list of (start, length) pairs. k_sort_tiles,
+// launched after it, takes the runs first and then the other tiles, largest
+// first, from one queue. A large tile whose runs do not fit the list is left
+// whole and sorted by one block.
+constexpr int SORT_SPLIT_RUN = 2048;
+constexpr int SPLIT_THREADS = 1024;   // a large tile's partition: a few keys per thread
+
+// partition of the large tile [r0, r0 + n) of keys into keys_tmp by the top 8
+// bits of its depth range; moff[0..256] receives the bin offsets (relative to
+// r0). mcnt is 256 words of scratch, part SORT_WARPS words. Whole block of NT
+// (>= 256) threads; ends with the keys_tmp writes visible to the block.
+template <int NT>
+__device__ void partition_tile(const unsigned long long *__restrict__ keys, unsigned long long *__restrict__ keys_tmp,
+                               int r0, int n, unsigned int *mcnt, unsigned int *moff, unsigned int *part,
+                               unsigned int *kmin_s, unsigned int *kmax_s) {
+    static_assert(NT >= 256 && NT % 32 == 0, "one thread per bin in the scan");
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        *kmin_s = 0xffffffffu;
+        *kmax_s = 0u;
+    }
+    for (int b = tid; b < 256; b += NT) mcnt[b] = 0;
+    __syncthreads();
+    {
+        unsigned int lmin = 0xffffffffu, lmax = 0u;
+#pragma unroll 4
+        for (int i = tid; i < n; i += NT) {
+            const unsigned int d = (unsigned int)(keys[r0 + i] >> 32);
+            lmin = min(lmin, d);
+            lmax = max(lmax, d);
+        }
+        lmin = __reduce_min_sync(0xffffffffu, lmin);
+        lmax = __reduce_max_sync(0xffffffffu, lmax);
+        if (lane == 0) {
+            atomicMin(kmin_s, lmin);
+            atomicMax(kmax_s, lmax);
+        }
+    }
+    __syncthreads();
+    const unsigned int kmin = *kmin_s, range = *kmax_s - kmin;
+    const int nbits = range ? 32 - __clz(range) : 0;
+    const int mshift = nbits > 8 ? nbits - 8 : 0;
+#pragma unroll 4
+    for (int i = tid; i < n; i += NT)
+        atomicAdd(&mcnt[(((unsigned int)(keys[r0 + i] >> 32)) - kmin) >> mshift], 1u);
+    __syncthreads();
+    // exclusive scan of the 256 bin counts, thread b < 256 owning bin b; the
+    // offsets become the scatter cursors
+    unsigned int c = 0u, incl = 0u;
+    if (tid < 256) {
+        c = mcnt[tid];
+        incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) part[wid] = incl;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const unsigned int w = lane < SORT_WARPS ? part[lane] : 0u;
+        unsigned int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < SORT_WARPS) part[lane] = wi - w;
+    }
+    __syncthreads();
+    if (tid < 256) {
+        const unsigned int excl = part[wid] + incl - c;
+        moff[tid] = excl;
+        mcnt[tid] = excl;
+        if (tid == 255) moff[256] = excl + c;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int i = tid; i < n; i += NT) {
+        const unsigned long long k = keys[r0 + i];
+        const unsigned int b = (((unsigned int)(k >> 32)) - kmin) >> mshift;
+        keys_tmp[r0 + atomicAdd(&mcnt[b], 1u)] = k;
+    }
+    __syncthreads();   // the block's global writes are visible to the block after the barrier
+}
+
+// end of the run that starts at bin b0 (exclusive): the longest stretch of
+// bins from b0 holding at most `limit` keys, at least one bin
+__device__ __forceinline__ int run_end(const unsigned int *moff, int b0, int limit) {
+    int b1 = b0 + 1;
+    while (b1 < 256 && moff[b1 + 1] - moff[b0] <= (unsigned int)limit) ++b1;
+    return b1;
+}
+
+struct SplitSmem {
+    unsigned int mcnt[256];
+    unsigned int moff[257];
+    unsigned int part[SORT_WARPS];
+    unsigned int starts[257];   // run starts (relative to the tile), then the end
+    unsigned int wmax[SORT_WARPS], wcnt[SORT_WARPS];
+    unsigned int kmin, kmax;
+    int item, base, k;
+};
+
+// Runs of a partitioned tile, one thread per bin: a non-empty bin starts a run
+// if it is the first, if its start lies in another SORT_SPLIT_RUN window of
+// the tile than the previous non-empty bin's start, or if it or that bin holds
+// more than half a window (so a large bin is a run of its own). A run then
+// holds at most two windows' worth of keys unless one bin is larger.
+constexpr int SPLIT_SHIFT = 11;   // log2(SORT_SPLIT_RUN)
+static_assert((1 << SPLIT_SHIFT) == SORT_SPLIT_RUN, "window of the run rule");
+__device__ void list_runs(SplitSmem &S) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    unsigned int o = 0u, sz = 0u, ps = 0u;
+    if (tid < 256) {
+        o = S.moff[tid];
+        sz = S.moff[tid + 1] - o;
+        // start of the previous non-empty bin: exclusive max-scan of the
+        // non-empty bins' starts (plus one, so that "none" is 0)
+        const unsigned int mine = sz ? o + 1u : 0u;
+        unsigned int incl = mine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl = max(incl, t);
+        }
+        if (lane == 31) S.wmax[wid] = incl;
+        ps = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) ps = 0u;
+    }
+    __syncthreads();
+    bool start = false;
+    if (tid < 256) {
+        for (int w = 0; w < wid; ++w) ps = max(ps, S.wmax[w]);
+        if (sz) {
+            if (ps == 0u) {
+                start = true;   // the first non-empty bin (start 0)
+            } else {
+                const unsigned int prev = ps - 1u;
+                start = (o >> SPLIT_SHIFT) != (prev >> SPLIT_SHIFT) || sz > (unsigned int)(SORT_SPLIT_RUN / 2) ||
+                        o - prev > (unsigned int)(SORT_SPLIT_RUN / 2);
+            }
+        }
+        const unsigned int bal = __ballot_sync(0xffffffffu, start);
+        if (lane == 0) S.wcnt[wid] = __popc(bal);
+        S.part[wid] = bal;   // (only read back by this warp)
+    }
+    __syncthreads();
+    if (tid < 256) {
+        unsigned int j = __popc(S.part[wid] & ((1u << lane) - 1u));
+        for (int w = 0; w < wid; ++w) j += S.wcnt[w];
+        if (start) S.starts[j] = o;
+        if (tid == 255) {
+            const unsigned int k = j + (start ? 1u : 0u);
+            S.k = (int)k;
+            S.starts[k] = S.moff[256];
+        }
+    }
+    __syncthreads();
+}
+
+// Partition the large tiles (the head of the work order: decreasing count
+// buckets) and list their runs. A tile is split only if it is large against
+// the sort's share of work per block: above SORT_CAP instances and above half
+// of (instances / sort blocks) -- a tile below that is not the sort's last
+// item to finish, and where most tiles are large (many views of a dense
+// scene) splitting them only adds a pass. runq holds (start, length) int
+// pairs, at most run_cap of them; flags[t] = -1 marks tile t as split (flags
+// is the scatter's cursor array, non-negative until then).
+__global__ void __launch_bounds__(SPLIT_THREADS) k_split_large(const int2 *__restrict__ ranges,
+                                                              const int *__restrict__ order, int n_tiles,
+                                                              unsigned long long *__restrict__ keys,
+                                                              unsigned long long *__restrict__ keys_tmp,
+                                                              unsigned int *__restrict__ ids,
+                                                              int *__restrict__ counters, int *__restrict__ flags,
+                                                              int *__restrict__ runq, int run_cap, int sort_blocks) {
+    __shared__ SplitSmem S;
+    if (counters[CNT_ABORT]) return;
+    const int thr = max(SORT_CAP + 1, (int)((long long)counters[CNT_INSTANCES] / (2LL * sort_blocks)));
+    const int thr_bucket = count_bucket(thr);
+    for (;;) {
+        if (threadIdx.x == 0) S.item = atomicAdd(counters + CNT_Q_SPLIT, 1);
+        __syncthreads();
+        const int item = S.item;
+        __syncthreads();
+        if (item >= n_tiles) break;
+        const int t = order[item];
+        const int2 r = ranges[t];
+        const int n = r.y - r.x;
+        if (count_bucket(n) < thr_bucket) break;   // the order is by count bucket: no tile to split follows
+        if (n < thr) continue;
+        partition_tile<SPLIT_THREADS>(keys, keys_tmp, r.x, n, S.mcnt, S.moff, S.part, &S.kmin, &S.kmax);
+        list_runs(S);
+        const int k = S.k;
+        if (threadIdx.x == 0) {
+            // one atomic add per tile (a compare-and-swap loop would retry once
+            // per competing block); pairs past run_cap do not exist, so a
+            // reservation that does not fit whole marks its pairs below
+            // run_cap empty and the tile is sorted whole
+            int base = atomicAdd(counters + CNT_RUN_RES, k);
+            if (base + k > run_cap) {
+                for (int j = base; j < run_cap; ++j) runq[2 * j + 1] = 0;
+                base = -1;
+            } else {
+                flags[t] = -1;
+            }
+            S.base = base;
+        }
+        __syncthreads();
+        const int base = S.base;
+        if (base >= 0) {
+            for (int j = threadIdx.x; j < k; j += SPLIT_THREADS) {
+                runq[2 * (base + j)] = r.x + (int)S.starts[j];
+                runq[2 * (base + j) + 1] = (int)(S.starts[j + 1] - S.starts[j]);
+            }
+        }
+        __syncthreads();   // starts, k and base are read before the next item
+    }
+}
+
+// Persistent, one queue: items [0, R) are the runs listed by k_split_large
+// (R = the pairs reserved, at most run_cap; empty pairs are skipped), then the
+// tiles in work order (largest first); split tiles are skipped.
+__global__ void __launch_bounds__(SORT_THREADS, 3) k_sort_tiles(const Launch L, const int2 *__restrict__ ranges,
                                                              const int *__restrict__ order,
                                                              unsigned long long *__restrict__ keys,
                                                              unsigned long long *__restrict__ keys_tmp,
                                                              unsigned int *__restrict__ ids,
-                                                             int *__restrict__ counters) {
+                                                             int *__restrict__ counters,
+                                                             const int *__restrict__ flags,
+                                                             const int *__restrict__ runq, int run_cap) {
     extern __shared__ __align__(16) unsigned char sort_smem[];
     SortSmem &S = *reinterpret_cast<SortSmem *>(sort_smem);
     if (counters[CNT_ABORT]) return;
+    const int R = min(counters[CNT_RUN_RES], run_cap);
     for (;;) {
         if (threadIdx.x == 0) S.item = atomicAdd(counters + CNT_Q_SORT, 1);
         __syncthreads();
         const int item = S.item;
         __syncthreads();
-        if (item >= L.n_tiles) break;
-        const int2 r = ranges[order[item]];
+        if (item < R) {
+            const int st = runq[2 * item], len = runq[2 * item + 1];
+            if (len == 0) continue;   // a slot of a reservation that did not fit
+            if (len == 1) {
+                if (threadIdx.x == 0) {
+                    const unsigned long long k = keys_tmp[st];
+                    keys[st] = k;
+                    ids[st] = (unsigned int)(k & 0xffffffffu);
+                }
+                continue;
+            }
+            if (len <= SORT_CAP) radix_sort_tile(S, keys_tmp, keys, ids, st, len, true);
+            else sort_segment_merge(S, keys, keys_tmp, ids, st, len);
+            continue;
+        }
+        if (item - R >= L.n_tiles) break;
+        const int t = order[item - R];
+        const int2 r = ranges[t];
         const int n = r.y - r.x;
         if (n <= 1) {
             if (n == 1 && threadIdx.x == 0) ids[r.x] = (unsigned int)(keys[r.x] & 0xffffffffu);
@@ -597,75 +849,13 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_tiles(const Launch L, con
             radix_sort_tile(S, keys, keys, ids, r.x, n, true);
             continue;
         }
-        // Large tile: one partition pass by the top 8 bits of (depth bits -
-        // tile minimum) into keys_tmp (bins in depth order), then runs of
-        // consecutive bins that fit on chip are sorted as one segment each
-        // into keys; a single bin larger than that takes the chunk-and-merge
-        // path. The result is the same (depth, slot) order.
-        if (threadIdx.x == 0) {
-            S.kmin = 0xffffffffu;
-            S.kmax = 0u;
-        }
-        unsigned int *mcnt = &S.hist[0][0];   // 256 counters, then cursors
-        for (int b = threadIdx.x; b < 256; b += SORT_THREADS) mcnt[b] = 0;
-        __syncthreads();
-        {
-            unsigned int lmin = 0xffffffffu, lmax = 0u;
-            for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
-                const unsigned int d = (unsigned int)(keys[r.x + i] >> 32);
-                lmin = min(lmin, d);
-                lmax = max(lmax, d);
-            }
-            atomicMin(&S.kmin, lmin);
-            atomicMax(&S.kmax, lmax);
-        }
-        __syncthreads();
-        const unsigned int kmin = S.kmin, range = S.kmax - S.kmin;
-        const int nbits = range ? 32 - __clz(range) : 0;
-        const int mshift = nbits > 8 ? nbits - 8 : 0;
-        for (int i = threadIdx.x; i < n; i += SORT_THREADS)
-            atomicAdd(&mcnt[(((unsigned int)(keys[r.x + i] >> 32)) - kmin) >> mshift], 1u);
-        __syncthreads();
-        {
-            // exclusive scan of the 256 bin counts, thread b owning bin b; the
-            // offsets become the scatter cursors
-            const int b = threadIdx.x, lane = b & 31, wid = b >> 5;
-            const unsigned int c = mcnt[b];
-            unsigned int incl = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            if (lane == 31) S.part[wid] = incl;
-            __syncthreads();
-            if (wid == 0) {
-                const unsigned int w = lane < SORT_WARPS ? S.part[lane] : 0u;
-                unsigned int wi = w;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned int t = __shfl_up_sync(0xffffffffu, wi, o);
-                    if (lane >= o) wi += t;
-                }
-                if (lane < SORT_WARPS) S.part[lane] = wi - w;
-            }
-            __syncthreads();
-            const unsigned int excl = S.part[wid] + incl - c;
-            S.moff[b] = excl;
-            mcnt[b] = excl;
-            if (b == 255) S.moff[256] = excl + c;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
-            const unsigned long long k = keys[r.x + i];
-            const unsigned int b = (((unsigned int)(k >> 32)) - kmin) >> mshift;
-            keys_tmp[r.x + atomicAdd(&mcnt[b], 1u)] = k;
-        }
-        __syncthreads();   // the block's global writes are visible to the block after the barrier
+        if (flags[t] < 0) continue;   // split: its runs were items of this queue
+        // a large tile left whole: partition, then sort runs of bins that fit
+        // on chip one after another (a single bin larger than that takes the
+        // chunk-and-merge path). The result is the same (depth, slot) order.
+        partition_tile<SORT_THREADS>(keys, keys_tmp, r.x, n, &S.hist[0][0], S.moff, S.part, &S.kmin, &S.kmax);
         for (int b0 = 0; b0 < 256;) {
-            // the longest run of bins from b0 that fits on chip (at least one bin)
-            int b1 = b0 + 1;
-            while (b1 < 256 && S.moff[b1 + 1] - S.moff[b0] <= (unsigned int)SORT_CAP) ++b1;
+            const int b1 = run_end(S.moff, b0, SORT_CAP);
             const int s0 = (int)S.moff[b0], len = (int)(S.moff[b1] - S.moff[b0]);
             if (len == 1 && threadIdx.x == 0) {
                 const unsigned long long k = keys_tmp[r.x + s0];
@@ -684,6 +874,8 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_tiles(const Launch L, con
 
 int launch_bin_sort(const Launch &L, const float *proj, const gs_bins *b, int32_t *status, cudaStream_t st) {
     const float4 *p = reinterpret_cast<const float4 *>(proj);
+    // tile_scratch [5T]: the tile cursors (then the split flags), then up to
+    // 2T (start, length) runs of split large tiles
     if (cudaMemsetAsync(b->tile_scratch, 0, sizeof(int) * (size_t)L.n_tiles, st) != cudaSuccess) return GS_ERR_CUDA;
     if (cudaMemsetAsync(b->counters, 0, sizeof(int) * GS_NUM_COUNTERS, st) != cudaSuccess) return GS_ERR_CUDA;
     const long long nb = (L.n_slots + BIN_CHUNK - 1) / BIN_CHUNK;
@@ -729,10 +921,15 @@ int launch_bin_sort(const Launch &L, const float *proj, const gs_bins *b, int32_
             per_sm = 1;
         sort_blocks = per_sm * num_sms();
     }
-    k_sort_tiles<<<sort_blocks, SORT_THREADS, smem, st>>>(
-        L, reinterpret_cast<const int2 *>(b->tile_ranges), b->tile_order,
-        reinterpret_cast<unsigned long long *>(b->keys), reinterpret_cast<unsigned long long *>(b->keys_tmp),
-        b->ids, b->counters);
+    const int2 *ranges = reinterpret_cast<const int2 *>(b->tile_ranges);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(b->keys);
+    unsigned long long *keys_tmp = reinterpret_cast<unsigned long long *>(b->keys_tmp);
+    int *runq = b->tile_scratch + L.n_tiles;
+    k_split_large<<<num_sms(), SPLIT_THREADS, 0, st>>>(ranges, b->tile_order, (int)L.n_tiles, keys, keys_tmp,
+                                                          b->ids, b->counters, b->tile_scratch, runq,
+                                                          2 * (int)L.n_tiles, sort_blocks);
+    k_sort_tiles<<<sort_blocks, SORT_THREADS, smem, st>>>(L, ranges, b->tile_order, keys, keys_tmp, b->ids,
+                                                          b->counters, b->tile_scratch, runq, 2 * (int)L.n_tiles);
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 

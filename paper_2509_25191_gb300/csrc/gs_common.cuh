@@ -53,9 +53,9 @@ enum {
     CNT_Q_FWD = 2,       // work queue heads
     CNT_Q_BWD = 3,
     CNT_Q_SORT = 4,
-    CNT_LARGE_TILES = 5, // tiles (at the head of tile_order) needing the large sort
+    CNT_RUN_RES = 5,     // runs of split large tiles listed for the sort
     CNT_MAX_TILE = 6,    // largest per-tile count
-    CNT_Q_SORT_L = 7     // queue head of the large-tile sort
+    CNT_Q_SPLIT = 7      // queue head of the large-tile split
 };
 
 // ---------------------------------------------------------------------------

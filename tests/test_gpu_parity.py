@@ -275,29 +275,55 @@ def test_binning_equal_depths_bit_exact(n):
     assert dt < 2.0   # a sanity bound only
 
 
-def test_binning_large_tiles_bit_exact():
-    """Tiles of > 2047 and > 16384 instances take the large-tile sort and
-    the merge path; the result must still equal the oracle's."""
-    rng = np.random.default_rng(11)
-    n, W, H = 60000, 64, 48
+def _large_tile_records(kind):
+    """Projected records with crowded tiles. "fallback": a 64x48 view (12
+    tiles of 16x16) with one tile of > 60000 instances, more runs than the
+    view's run list (2 per tile) holds, so one block sorts it whole
+    (partition, then runs and the chunk-and-merge path). "split": a 256x192
+    view (192 tiles) with three tiles of ~7000 instances whose runs all fit
+    the list and are sorted by any block."""
+    if kind == "fallback":
+        rng, n, W, H, spots, per, side = np.random.default_rng(11), 80000, 64, 48, ((17, 17),), 60000, 13
+    else:
+        rng, n, W, H, spots, per, side = (np.random.default_rng(12), 40000, 256, 192,
+                                          ((36, 36), (164, 100), (100, 148)), 7000, 8)
     r = np.zeros((n, 16), np.float32)
-    r[:, 0] = rng.uniform(0, 64, n)
-    r[:, 1] = rng.uniform(0, 48, n)
+    r[:, 0] = rng.uniform(0, W, n)
+    r[:, 1] = rng.uniform(0, H, n)
     r[:, 11] = rng.integers(1, 3, n)
     r[:, 14] = rng.uniform(1.0, 9.0, n).astype(np.float32)
     r[:, 2] = r[:, 11] * rng.uniform(0.3, 1.0, n)
     r[:, 3] = r[:, 11]
-    r[:40000, 0] = rng.uniform(17, 30, 40000)   # one very crowded tile column
-    r[:40000, 1] = rng.uniform(17, 30, 40000)
+    for c, (x0, y0) in enumerate(spots):
+        sl = slice(c * per, (c + 1) * per)
+        r[sl, 0] = rng.uniform(x0, x0 + side, per)
+        r[sl, 1] = rng.uniform(y0, y0 + side, per)
+    return r, W, H
+
+
+@pytest.mark.parametrize("kind", ["split", "fallback"])
+def test_binning_large_tiles_bit_exact(kind):
+    """Tiles of > 4096 instances: split into runs of depth bins sorted by
+    any block, or (too many runs for the list) sorted whole by one block.
+    The result must still equal the oracle's."""
+    r, W, H = _large_tile_records(kind)
+    n = r.shape[0]
     vw = synth.Views(np.zeros((1, 12), np.float32), np.ones((1, 4), np.float32), np.array([W], np.int32),
                      np.array([H], np.int32), np.array([0]), np.array([n]))
     views = _lib.Views.from_synth(vw)
     cfg = _lib.config(tile=(16, 16))
     rr, kk, ii = O.bin_view(r[:, 0], r[:, 1], r[:, 11].astype(np.int32), r[:, 14], W, H, 16, 16, ext=r[:, 2:4])
-    assert (rr[:, 1] - rr[:, 0]).max() > 16384
+    counts = rr[:, 1] - rr[:, 0]
+    T = len(counts)
+    if kind == "split":
+        assert (counts > 4096).sum() == 3 and counts.max() < 2 * 4096   # at most ~8 runs each: 24 <= T
+    else:
+        assert counts.max() > 16384 and -(-counts.max() // 2048) > 2 * T   # at least 30 runs: more than 2T
     bins = _lib.Bins(views.num_tiles(cfg), len(ii))
-    _lib.gs_bin_sort(views, cfg, torch.as_tensor(r).cuda(), bins, _lib.new_status())
+    status = _lib.new_status()
+    _lib.gs_bin_sort(views, cfg, torch.as_tensor(r).cuda(), bins, status)
     torch.cuda.synchronize()
+    assert status[0].item() == 0
     assert np.array_equal(bins.tile_ranges.cpu().numpy().reshape(-1, 2), rr)
     assert np.array_equal(bins.keys.cpu().numpy().view(np.uint64), kk)
     assert np.array_equal(bins.ids.cpu().numpy().view(np.uint32).astype(np.int64), ii)
