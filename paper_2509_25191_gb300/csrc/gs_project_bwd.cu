@@ -1,11 +1,11 @@
 // Backward of the projection: per-slot 2D gradients -> raw Gaussian
 // parameters and camera poses.
 //
-// One thread per Gaussian (fixed grid, grid-stride), looping over the views of
-// its scene: the Gaussian's parameters are read once (for one-view calls only
-// if it has a nonzero 2D gradient: see LAZY), its gradients are summed over
-// views in registers and written once (overwritten, or added to the caller's
-// values when the configuration accumulates). For degree-3 SH the block's
+// One thread per Gaussian (fixed grid, grid-stride; for one-view calls one
+// thread per Gaussian with a nonzero 2D gradient: see COMPACT), looping over
+// the views of its scene: the Gaussian's parameters are read once, its
+// gradients are summed over views in registers and written once (overwritten,
+// or added to the caller's values when the configuration accumulates). For degree-3 SH the block's
 // first-view 2D-gradient rows arrive by a tensor copy, the SH rows are staged
 // in shared memory, and the block's SH-coefficient gradients leave by tensor
 // stores (see PbStage). Each view's pose
@@ -36,10 +36,9 @@ constexpr int PB_WARPS = PB_THREADS / 32;
 // Staging of a block's 128 Gaussians on the degree-3 path: the SH rows arrive
 // as a 32-float box with the 128-byte swizzle and a 16-float box with the
 // 64-byte swizzle (a thread reads its own row 16 bytes at a time without bank
-// conflicts) -- by two tensor copies for the whole block, or (LAZY) copied
-// into the same layout by each contributing Gaussian's thread -- and the
-// SH-coefficient gradients are summed over views in the same layout and leave
-// by two tensor stores.
+// conflicts) by two tensor copies for the whole block, and the SH-coefficient
+// gradients are summed over views in the same layout and leave by two tensor
+// stores.
 struct PbStage {
     float4 shA[PB_THREADS * 8];
     float4 shB[PB_THREADS * 4];
@@ -49,13 +48,67 @@ struct PbStage {
     unsigned long long bar;
 };
 
-// LAZY: read a Gaussian's parameters (and stage its SH row) only if some view
-// gives it a nonzero 2D gradient, found by a first pass over its 2D-gradient
-// rows. It pays where few Gaussians contribute (one view of a dense scene:
-// most Gaussians are hidden behind saturated pixels); with many views most
-// Gaussians contribute somewhere and the block-wide tensor copies of the SH
-// rows are faster, so the launch chooses LAZY for one-view calls.
-template <int DEG, bool GAUSS, bool TMA, bool LAZY>
+// COMPACT (one-view calls): most Gaussians of a dense scene get no 2D
+// gradient in one view (they are hidden behind saturated pixels), and a
+// thread per Gaussian left most lanes idle. Instead each block takes a
+// contiguous range of Gaussians, finds those with a nonzero 2D-gradient row
+// (PB_SUB at a time, listed in shared memory in an order fixed by their
+// indices) and runs the chain over the list with full warps. The others'
+// parameter gradients are zeroed by the launch beforehand (or, accumulating,
+// left as they are). The pose partials stay per block over a fixed range, so
+// the pose gradient is deterministic. With several views most Gaussians
+// contribute somewhere and the block-wide tensor copies are faster.
+constexpr int PB_SUB = 1024;   // Gaussians compacted at a time (8 per thread)
+
+// List the Gaussians (thread indices) in [g0, g1) with a nonzero 2D-gradient
+// row in their (single) view into s_list; returns the count. Thread t checks
+// g0 + j * PB_THREADS + t (coalesced rows) and lists its hits in j order
+// after those of lower threads. Whole block; starts and ends with a barrier.
+__device__ __forceinline__ int compact_range(const Launch &L, const float4 *__restrict__ grad2d, long long g0,
+                                             long long g1, int *s_list, int *s_wsum) {
+    constexpr int PER = PB_SUB / PB_THREADS;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();   // the previous list has been read
+    unsigned int hits = 0u;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const long long g = g0 + (long long)j * PB_THREADS + threadIdx.x;
+        if (g < g1) {
+            const int sc = scene_of_thread(L, g);
+            const long long slot = L.v[L.s[sc].v_begin].slot_base + (g - L.s[sc].thread_base);
+            const float4 a4 = grad2d[3 * slot], b4 = grad2d[3 * slot + 1];
+            const float c0 = reinterpret_cast<const float *>(grad2d)[12 * slot + 8];
+            // nonzero iff some value has nonzero magnitude bits
+            const unsigned int bits = __float_as_uint(a4.x) | __float_as_uint(a4.y) | __float_as_uint(a4.z) |
+                                      __float_as_uint(a4.w) | __float_as_uint(b4.x) | __float_as_uint(b4.y) |
+                                      __float_as_uint(b4.z) | __float_as_uint(b4.w) | __float_as_uint(c0);
+            if (bits & 0x7fffffffu) hits |= 1u << j;
+        }
+    }
+    const int cnt = __popc(hits);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_wsum[wid] = incl;
+    __syncthreads();
+    int at = incl - cnt, total = 0;
+#pragma unroll
+    for (int w = 0; w < PB_WARPS; ++w) {
+        const int ws = s_wsum[w];
+        if (w < wid) at += ws;
+        total += ws;
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j)
+        if (hits >> j & 1u) s_list[at++] = j * PB_THREADS + (int)threadIdx.x;
+    __syncthreads();
+    return total;
+}
+
+template <int DEG, bool GAUSS, bool TMA, bool COMPACT>
 __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
     const Launch L, const float *__restrict__ means, const float *__restrict__ log_scales,
     const float *__restrict__ quats, const float *__restrict__ logits, const float *__restrict__ sh,
@@ -69,6 +122,7 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int GP = 3 * K + 1;   // odd row pitch: conflict-free column access
     static_assert(!TMA || DEG == 3, "the staged path is for 48-float SH rows");
+    static_assert(!(TMA && COMPACT), "the compacted path reads rows per thread");
     // per-warp pose partials [PB_WARPS][n_views][12] (dynamic: sized by the launch)
     extern __shared__ float s_pose[];
     // per-thread SH-coefficient gradients, summed over views here and written
@@ -76,6 +130,8 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
     __shared__ float s_gf[GAUSS && !TMA ? PB_THREADS * GP : 1];
     __shared__ long long s_row[GAUSS && !TMA ? PB_THREADS : 1];
     __shared__ __align__(1024) PbStage S[1];   // (removed by the compiler where unused)
+    __shared__ int s_list[COMPACT ? PB_SUB : 1];   // offsets from the range's current start
+    __shared__ int s_wsum[PB_WARPS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nv = L.n_views;
     for (int i = threadIdx.x; i < PB_WARPS * nv * 12; i += PB_THREADS) s_pose[i] = 0.f;
@@ -85,9 +141,35 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
     const int r = threadIdx.x;   // this thread's row of the staging boxes
 
     const long long stride = (long long)gridDim.x * PB_THREADS;
-    for (long long base = (long long)blockIdx.x * PB_THREADS; base < L.n_threads; base += stride) {
-        const long long gid = base + threadIdx.x;
-        const bool valid = gid < L.n_threads;
+    // COMPACT: this block's range [c_next, c_end), the current list of c_cnt
+    // offsets from c_at, and how far it has been taken
+    long long c_next = 0, c_end = 0, c_at = 0;
+    int c_cnt = 0, c_pos = 0;
+    if constexpr (COMPACT) {
+        const long long per = (L.n_threads + gridDim.x - 1) / gridDim.x;
+        c_next = min((long long)L.n_threads, (long long)blockIdx.x * per);
+        c_end = min((long long)L.n_threads, c_next + per);
+    }
+    for (long long base = (long long)blockIdx.x * PB_THREADS;; base += stride) {
+        long long gid;
+        bool valid;
+        if constexpr (COMPACT) {
+            while (c_pos >= c_cnt && c_next < c_end) {   // (uniform over the block)
+                const long long g1 = min(c_end, c_next + PB_SUB);
+                c_cnt = compact_range(L, grad2d, c_next, g1, s_list, s_wsum);
+                c_at = c_next;
+                c_next = g1;
+                c_pos = 0;
+            }
+            if (c_pos >= c_cnt) break;
+            valid = c_pos + (int)threadIdx.x < c_cnt;
+            gid = valid ? c_at + s_list[c_pos + threadIdx.x] : 0;
+            c_pos += PB_THREADS;
+        } else {
+            if (base >= L.n_threads) break;
+            gid = base + threadIdx.x;
+            valid = gid < L.n_threads;
+        }
         const int s = valid ? scene_of_thread(L, gid) : 0;
         const long long li = valid ? gid - L.s[s].thread_base : 0;
         const long long i = L.s[s].g_begin + li;
@@ -114,11 +196,9 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                 if (GAUSS) bulk_wait_read_all();
                 if (full) {
                     fence_async_smem();
-                    mbar_expect_tx(&S[0].bar, PB_THREADS * ((acc_rows ? 48 : 0) + (LAZY ? 0 : 48) + 12) * 4);
-                    if (!LAZY) {
-                        tma_load_2d(S[0].shA, &tm_shA, 0, row0, &S[0].bar);
-                        tma_load_2d(S[0].shB, &tm_shB, 32, row0, &S[0].bar);
-                    }
+                    mbar_expect_tx(&S[0].bar, PB_THREADS * ((acc_rows ? 48 : 0) + 48 + 12) * 4);
+                    tma_load_2d(S[0].shA, &tm_shA, 0, row0, &S[0].bar);
+                    tma_load_2d(S[0].shB, &tm_shB, 32, row0, &S[0].bar);
                     const int srow = (int)(L.v[v_first].slot_base + base - L.s[scene_of_thread(L, base)].thread_base);
                     tma_load_2d(S[0].g2d, &tm_g2d, 0, srow, &S[0].bar);
                     if (acc_rows) {
@@ -128,7 +208,7 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
                 }
             }
             __syncthreads();
-            if (!LAZY && !full && valid) {
+            if (!full && valid) {
                 // a partial iteration stages its rows itself, in the same layout
                 const float4 *src = reinterpret_cast<const float4 *>(sh + 48LL * i);
 #pragma unroll
@@ -190,23 +270,8 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
             }
         }
 
-        // does any view give this Gaussian a nonzero 2D gradient? (the first
-        // view's rows are staged; the loop below reads them all again)
-        if (!LAZY) loaded = valid;
-        if (LAZY && valid) {
-            for (int v = vb; v < ve && !loaded; ++v) {
-                const long long slot = L.v[v].slot_base + li;
-                const bool staged = TMA && full && v == v_first;
-                const float4 a4 = staged ? S[0].g2d[3 * r] : grad2d[3 * slot];
-                const float4 b4 = staged ? S[0].g2d[3 * r + 1] : grad2d[3 * slot + 1];
-                const float c0 = staged ? S[0].g2d[3 * r + 2].x : grad2d[3 * slot + 2].x;
-                // nonzero iff some value has nonzero magnitude bits
-                const unsigned int bits = __float_as_uint(a4.x) | __float_as_uint(a4.y) | __float_as_uint(a4.z) |
-                                          __float_as_uint(a4.w) | __float_as_uint(b4.x) | __float_as_uint(b4.y) |
-                                          __float_as_uint(b4.z) | __float_as_uint(b4.w) | __float_as_uint(c0);
-                loaded = (bits & 0x7fffffffu) != 0u;
-            }
-        }
+        // (listed Gaussians of the compacted path all have a gradient)
+        loaded = valid;
         // only the loads are conditional; the activations are formed from the
         // loaded values or from defaults that make every gradient term zero
         float l3[3] = {0.f, 0.f, 0.f}, lg = 0.f;
@@ -217,15 +282,6 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
             for (int a = 0; a < 3; ++a) l3[a] = log_scales[3 * i + a];
             q = reinterpret_cast<const float4 *>(quats)[i];
             lg = logits[i];
-            if constexpr (TMA && LAZY) {
-                // this thread's SH row into its swizzled staging row (read only
-                // by this thread), by asynchronous copies
-                const float4 *src = reinterpret_cast<const float4 *>(sh + 48LL * i);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) cp_async16(&S[0].shA[swz128(r, c)], src + c);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) cp_async16(&S[0].shB[swz64(r, c)], src + 8 + c);
-            }
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) sc[a] = loaded ? expf(l3[a]) : 0.f;
@@ -246,7 +302,6 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
         S11 = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
         S12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
         S22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
-        if constexpr (TMA && LAZY) cp_async_wait_all();
 
         for (int v = wvb; v < wve; ++v) {
             float pg[12];
@@ -547,17 +602,18 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
     CUtensorMap ma, mb, ga, gb, m2;
     memset(&ma, 0, sizeof ma); memset(&mb, 0, sizeof mb); memset(&ga, 0, sizeof ga); memset(&gb, 0, sizeof gb);
     memset(&m2, 0, sizeof m2);
-    // one-view calls read only the contributing Gaussians' parameters (see LAZY)
-    const bool lazy = L.n_views == 1;
-    // degree 3 with 16-byte aligned SH rows and gradient rows: the staged
-    // path, unless the configuration turns tensor copies off. The pose-only
-    // backward reads SH rows only for Gaussians with a nonzero 2D gradient,
-    // which the per-thread path does (measured faster there: 46 vs 63 us at
-    // 1M Gaussians)
-    bool tma = want_gauss && deg == 3 && L.use_tma && ((uintptr_t)g->sh & 15u) == 0 && g->n < 0x7fffffffLL &&
-               (lazy ||
-                (encode_tmap_2d(&ma, g->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
-                 encode_tmap_2d(&mb, g->sh, 48, (uint64_t)g->n, 192, 16, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_64B)));
+    // one-view calls run the chain over the Gaussians with a nonzero 2D
+    // gradient only (see COMPACT); the others' gradients are zeroed here
+    const bool compact = L.n_views == 1;
+    // several views, degree 3 with 16-byte aligned SH rows and gradient rows:
+    // the staged path, unless the configuration turns tensor copies off. The
+    // pose-only backward reads SH rows only for Gaussians with a nonzero 2D
+    // gradient, which the per-thread path does (measured faster there: 46 vs
+    // 63 us at 1M Gaussians)
+    bool tma = !compact && want_gauss && deg == 3 && L.use_tma && ((uintptr_t)g->sh & 15u) == 0 &&
+               g->n < 0x7fffffffLL &&
+               encode_tmap_2d(&ma, g->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
+               encode_tmap_2d(&mb, g->sh, 48, (uint64_t)g->n, 192, 16, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_64B);
     if (tma)
         tma = L.n_slots < 0x7fffffffLL &&
               encode_tmap_2d(&m2, grad2d, 12, (uint64_t)L.n_slots, 48, 12, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_NONE);
@@ -565,21 +621,29 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
         tma = ((uintptr_t)out->sh & 15u) == 0 &&
               encode_tmap_2d(&ga, out->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
               encode_tmap_2d(&gb, out->sh, 48, (uint64_t)g->n, 192, 16, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_64B);
+    if (compact && want_gauss && !L.accumulate && g->n > 0) {
+        const int K = (deg + 1) * (deg + 1);
+        const size_t n = (size_t)g->n;
+        if (cudaMemsetAsync(out->means, 0, sizeof(float) * 3 * n, st) ||
+            cudaMemsetAsync(out->log_scales, 0, sizeof(float) * 3 * n, st) ||
+            cudaMemsetAsync(out->quats, 0, sizeof(float) * 4 * n, st) ||
+            cudaMemsetAsync(out->opacity_logits, 0, sizeof(float) * n, st) ||
+            cudaMemsetAsync(out->sh, 0, sizeof(float) * 3 * K * n, st))
+            return GS_ERR_CUDA;
+    }
 #define GS_PB(D, G, T, Z)                                                                                          \
     k_project_bwd<D, G, T, Z><<<nblk, PB_THREADS, dyn, st>>>(                                                      \
         L, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, viewmats, intr, p, g2, out->means,        \
         out->log_scales, out->quats, out->opacity_logits, out->sh, out->pose_partials, ma, mb, ga, gb, m2, status)
     if (want_gauss) {
         switch (deg) {
-        case 0: if (lazy) GS_PB(0, true, false, true); else GS_PB(0, true, false, false); break;
-        case 1: if (lazy) GS_PB(1, true, false, true); else GS_PB(1, true, false, false); break;
-        case 2: if (lazy) GS_PB(2, true, false, true); else GS_PB(2, true, false, false); break;
+        case 0: if (compact) GS_PB(0, true, false, true); else GS_PB(0, true, false, false); break;
+        case 1: if (compact) GS_PB(1, true, false, true); else GS_PB(1, true, false, false); break;
+        case 2: if (compact) GS_PB(2, true, false, true); else GS_PB(2, true, false, false); break;
         case 3:
-            if (tma) {
-                if (lazy) GS_PB(3, true, true, true); else GS_PB(3, true, true, false);
-            } else {
-                if (lazy) GS_PB(3, true, false, true); else GS_PB(3, true, false, false);
-            }
+            if (compact) GS_PB(3, true, false, true);
+            else if (tma) GS_PB(3, true, true, false);
+            else GS_PB(3, true, false, false);
             break;
         default: return GS_ERR_UNSUPPORTED;
         }
@@ -587,10 +651,10 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
         // the pose-only backward reads a Gaussian's parameters only in its
         // contributing views already (per-thread path)
         switch (deg) {
-        case 0: GS_PB(0, false, false, false); break;
-        case 1: GS_PB(1, false, false, false); break;
-        case 2: GS_PB(2, false, false, false); break;
-        case 3: GS_PB(3, false, false, false); break;
+        case 0: if (compact) GS_PB(0, false, false, true); else GS_PB(0, false, false, false); break;
+        case 1: if (compact) GS_PB(1, false, false, true); else GS_PB(1, false, false, false); break;
+        case 2: if (compact) GS_PB(2, false, false, true); else GS_PB(2, false, false, false); break;
+        case 3: if (compact) GS_PB(3, false, false, true); else GS_PB(3, false, false, false); break;
         default: return GS_ERR_UNSUPPORTED;
         }
     }
