@@ -288,8 +288,9 @@ int gs_pose_grad(const gs_views *views, const float *pose_partials, int n_blocks
                  float *dL_dviewmat, float *dL_dtwist, void *stream);
 
 /* Mean L1 photometric loss (Section 3.1 photometric supervision) and its
- * gradient: loss DEVICE [1] = mean |image - target| (overwritten),
- * dL_dimage DEVICE [count] = sign(image - target) / count. */
+ * gradient: loss DEVICE [1] = mean |image - target| (overwritten; block
+ * partials are added with atomics, so its last bits depend on their order),
+ * dL_dimage DEVICE [count] = sign(image - target) / count (deterministic). */
 int gs_l1_loss(const float *image, const float *target, int64_t count, float *loss,
                float *dL_dimage, void *stream);
 
