@@ -383,9 +383,8 @@ int gs_project_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *c
         return GS_ERR_ARG;
     if (!aligned16(grad2d) || (want_gaussian_grads && g->n > 0 && !aligned16(out->quats))) return GS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (want_gaussian_grads && !L.accumulate && L.n_views != 1) {
+    if (want_gaussian_grads && !L.accumulate) {
         // Gaussians outside every view's range still get (zero) gradients
-        // (one-view calls zero every gradient in launch_project_bwd)
         long long covered = 0;
         for (int a = 0; a < L.n_scenes; ++a) covered += L.s[a].g_count;
         if (covered != g->n && g->n > 0) {
@@ -600,7 +599,7 @@ extern "C" int gs_project_bwd_noalloc(const gs_gaussians *g, const gs_views *vw,
     cudaStream_t st = (cudaStream_t)stream;
     float *scratch = nullptr;
     if ((rc = noalloc_scratch(st, &scratch))) return rc;
-    if (want_gaussian_grads && !L.accumulate && L.n_views != 1) {   // (one view: see gs_project_bwd)
+    if (want_gaussian_grads && !L.accumulate) {
         long long covered = 0;
         for (int a = 0; a < L.n_scenes; ++a) covered += L.s[a].g_count;
         if (covered != g->n && g->n > 0) {

@@ -53,11 +53,13 @@ struct PbStage {
 // thread per Gaussian left most lanes idle. Instead each block takes a
 // contiguous range of Gaussians, finds those with a nonzero 2D-gradient row
 // (PB_SUB at a time, listed in shared memory in an order fixed by their
-// indices) and runs the chain over the list with full warps. The others'
-// parameter gradients are zeroed by the launch beforehand (or, accumulating,
-// left as they are). The pose partials stay per block over a fixed range, so
-// the pose gradient is deterministic. With several views most Gaussians
-// contribute somewhere and the block-wide tensor copies are faster.
+// indices) and runs the chain over the list with full warps. Each range's
+// parameter-gradient rows are zeroed by its block, coalesced, when the range
+// is listed, and the listed Gaussians' rows written again after a barrier
+// (accumulating, the others are left as they are). The pose partials stay
+// per block over a fixed range, so the pose gradient is deterministic. With
+// several views most Gaussians contribute somewhere and the block-wide
+// tensor copies are faster.
 constexpr int PB_SUB = 1024;   // Gaussians compacted at a time (8 per thread)
 
 // List the Gaussians (thread indices) in [g0, g1) with a nonzero 2D-gradient
@@ -106,6 +108,29 @@ __device__ __forceinline__ int compact_range(const Launch &L, const float4 *__re
         if (hits >> j & 1u) s_list[at++] = j * PB_THREADS + (int)threadIdx.x;
     __syncthreads();
     return total;
+}
+
+// Zero the parameter-gradient rows of Gaussians [i0, i0 + cnt) (K SH
+// coefficients per colour channel) with the whole block, coalesced; float4
+// stores where a span is 16-byte aligned and a whole number of float4.
+__device__ __forceinline__ void zero_span(float *__restrict__ p, long long count) {
+    if (((uintptr_t)p & 15u) == 0 && (count & 3) == 0) {
+        float4 *q = reinterpret_cast<float4 *>(p);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (long long e = threadIdx.x; e < (count >> 2); e += PB_THREADS) q[e] = z;
+    } else {
+        for (long long e = threadIdx.x; e < count; e += PB_THREADS) p[e] = 0.f;
+    }
+}
+template <int K>
+__device__ __forceinline__ void zero_rows(long long i0, long long cnt, float *__restrict__ g_means,
+                                          float *__restrict__ g_log_scales, float *__restrict__ g_quats,
+                                          float *__restrict__ g_logits, float *__restrict__ g_sh) {
+    zero_span(g_means + 3 * i0, 3 * cnt);
+    zero_span(g_log_scales + 3 * i0, 3 * cnt);
+    zero_span(g_quats + 4 * i0, 4 * cnt);
+    zero_span(g_logits + i0, cnt);
+    zero_span(g_sh + 3LL * K * i0, 3LL * K * cnt);
 }
 
 template <int DEG, bool GAUSS, bool TMA, bool COMPACT>
@@ -157,6 +182,15 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
             while (c_pos >= c_cnt && c_next < c_end) {   // (uniform over the block)
                 const long long g1 = min(c_end, c_next + PB_SUB);
                 c_cnt = compact_range(L, grad2d, c_next, g1, s_list, s_wsum);
+                if (GAUSS && !L.accumulate) {
+                    // this range's rows, zero; the listed Gaussians' rows are
+                    // written again below by this block, after a barrier (one
+                    // view: the range's Gaussians are contiguous)
+                    const int sc = scene_of_thread(L, c_next);
+                    zero_rows<K>(L.s[sc].g_begin + (c_next - L.s[sc].thread_base), g1 - c_next, g_means,
+                                 g_log_scales, g_quats, g_logits, g_sh);
+                    __syncthreads();
+                }
                 c_at = c_next;
                 c_next = g1;
                 c_pos = 0;
@@ -603,7 +637,7 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
     memset(&ma, 0, sizeof ma); memset(&mb, 0, sizeof mb); memset(&ga, 0, sizeof ga); memset(&gb, 0, sizeof gb);
     memset(&m2, 0, sizeof m2);
     // one-view calls run the chain over the Gaussians with a nonzero 2D
-    // gradient only (see COMPACT); the others' gradients are zeroed here
+    // gradient only (see COMPACT); each block zeroes its range's rows first
     const bool compact = L.n_views == 1;
     // several views, degree 3 with 16-byte aligned SH rows and gradient rows:
     // the staged path, unless the configuration turns tensor copies off. The
@@ -621,16 +655,6 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
         tma = ((uintptr_t)out->sh & 15u) == 0 &&
               encode_tmap_2d(&ga, out->sh, 48, (uint64_t)g->n, 192, 32, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_128B) &&
               encode_tmap_2d(&gb, out->sh, 48, (uint64_t)g->n, 192, 16, PB_THREADS, CU_TENSOR_MAP_SWIZZLE_64B);
-    if (compact && want_gauss && !L.accumulate && g->n > 0) {
-        const int K = (deg + 1) * (deg + 1);
-        const size_t n = (size_t)g->n;
-        if (cudaMemsetAsync(out->means, 0, sizeof(float) * 3 * n, st) ||
-            cudaMemsetAsync(out->log_scales, 0, sizeof(float) * 3 * n, st) ||
-            cudaMemsetAsync(out->quats, 0, sizeof(float) * 4 * n, st) ||
-            cudaMemsetAsync(out->opacity_logits, 0, sizeof(float) * n, st) ||
-            cudaMemsetAsync(out->sh, 0, sizeof(float) * 3 * K * n, st))
-            return GS_ERR_CUDA;
-    }
 #define GS_PB(D, G, T, Z)                                                                                          \
     k_project_bwd<D, G, T, Z><<<nblk, PB_THREADS, dyn, st>>>(                                                      \
         L, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, viewmats, intr, p, g2, out->means,        \
