@@ -329,6 +329,43 @@ def test_binning_large_tiles_bit_exact(kind):
     assert np.array_equal(bins.ids.cpu().numpy().view(np.uint32).astype(np.int64), ii)
 
 
+def test_binning_split_tiles_across_views_bit_exact():
+    """Two views with crowded tiles in one call: the split tiles of both views
+    share the run list and the sort's queue; each view's lists must equal the
+    oracle's (slots offset by the view's slot base)."""
+    ra, W, H = _large_tile_records("split")
+    rb, _, _ = _large_tile_records("split")
+    rb = rb.copy()
+    rb[:, 0] = W - rb[:, 0]          # mirrored: crowded tiles elsewhere in the second view
+    rb[:, 14] = rb[:, 14][::-1]      # other depths
+    na, nb = ra.shape[0], rb.shape[0]
+    vw = synth.Views(np.zeros((2, 12), np.float32), np.ones((2, 4), np.float32), np.array([W, W], np.int32),
+                     np.array([H, H], np.int32), np.array([0, na]), np.array([na, nb]))
+    views = _lib.Views.from_synth(vw)
+    cfg = _lib.config(tile=(16, 16))
+    refs = [O.bin_view(r[:, 0], r[:, 1], r[:, 11].astype(np.int32), r[:, 14], W, H, 16, 16, ext=r[:, 2:4])
+            for r in (ra, rb)]
+    assert all((rr[:, 1] - rr[:, 0]).max() > 4096 for rr, _, _ in refs)
+    n_inst = sum(len(ii) for _, _, ii in refs)
+    bins = _lib.Bins(views.num_tiles(cfg), n_inst)
+    status = _lib.new_status()
+    _lib.gs_bin_sort(views, cfg, torch.as_tensor(np.concatenate([ra, rb])).cuda(), bins, status)
+    torch.cuda.synchronize()
+    assert status[0].item() == 0 and bins.counters[0].item() == n_inst
+    ranges = bins.tile_ranges.cpu().numpy().reshape(-1, 2).astype(np.int64)
+    keys = bins.keys.cpu().numpy().view(np.uint64)
+    ids = bins.ids.cpu().numpy().view(np.uint32).astype(np.int64)
+    base = 0
+    for v, (rr, kk, ii) in enumerate(refs):
+        tb, sb = views.tile_base(cfg, v), views.slot_base(v)
+        assert np.array_equal(ranges[tb:tb + rr.shape[0]] - base, rr)
+        sl = slice(base, base + len(ii))
+        assert np.array_equal(ids[sl] - sb, ii.astype(np.int64))
+        assert np.array_equal(keys[sl], (kk & np.uint64(0xffffffff00000000)) | ((kk & np.uint64(0xffffffff)) +
+                                                                              np.uint64(sb)))
+        base += len(ii)
+
+
 # ---------------------------------------------------------------------------
 # rendering
 # ---------------------------------------------------------------------------
