@@ -29,13 +29,13 @@
  *     device (instance capacity exceeded) are written to the caller's DEVICE
  *     status word int32[4] = {code, detail_lo, detail_hi, 0}; the caller reads
  *     it at a point of its choosing (gs_status_read). Kernels never trap; the
- *     only waits are the projection kernels' bounded waits for their own
+ *     only waits are the forward projection's bounded waits for its own
  *     tensor copies (GS_ERR_TIMEOUT if one runs out; gs_check_bounded_wait
  *     makes one run out on purpose, for tests of this path). When the status
  *     word is non-zero after a call, that call's outputs are undefined.
  *   - The enqueued work depends only on the arguments: no environment
  *     variable or global setting steers it (gs_config.use_tma selects the
- *     projection kernels' staging).
+ *     forward projection's staging).
  *   - float32 everywhere. Quaternions are (w,x,y,z). Cameras are
  *     world->camera rigid transforms with OpenCV axes (x right, y down,
  *     z forward); a pixel (u,v) has its centre at (u+0.5, v+0.5).
@@ -83,9 +83,9 @@ typedef struct gs_config {
     int accumulate_grads; /* [0] 0: the backward overwrites the raw-parameter gradients (gs_grads.means ..
                              .sh); nonzero: it adds to them (+=), so gradients of several calls (views,
                              losses) sum in the caller's buffers, which the caller zeroes first */
-    int use_tma;          /* [1] nonzero: the projection kernels stage degree-3 SH rows, records and
-                             gradient rows by tensor copies where the layout allows; 0: per-thread loads
-                             and stores. The results are the same bit for bit. */
+    int use_tma;          /* [1] nonzero: the forward projection stages degree-3 SH rows and records by
+                             tensor copies where the layout allows; 0: per-thread loads and stores. The
+                             results are the same bit for bit. */
     int fwd_batch;        /* [2] Gaussians each thread stages per shared-memory batch in gs_render_fwd:
                              1, 2 or 4 (a batch is fwd_batch x tile_w x tile_h / 2 Gaussians) */
     int bwd_batch;        /* [1] the same for gs_rasterize_bwd: 1 or 2. Neither changes the image; the
@@ -262,15 +262,15 @@ int gs_render_bwd(const gs_gaussians *g, const gs_views *views, const gs_config 
  * set it must hold what gs_render_fwd wrote for this image with these bins,
  * and each pixel's replay ends at its last composited Gaussian (the result is
  * the same as without it). gs_project_bwd chains grad2d to the raw
- * parameters (overwritten, or added with cfg->accumulate_grads; the staged
- * degree-3 path adds each view's SH-coefficient gradient to the running
- * value, so with several views per Gaussian the sum is rounded in that
- * order) and the pose partials (always overwritten). With degree-3 SH, want_gaussian_grads and
- * cfg->use_tma, gs_project_bwd stages each block's SH rows, first-view
- * 2D-gradient rows and SH-gradient rows by tensor copies (grads->sh must then
- * be 16-byte aligned, else the per-thread path runs); a bounded wait for one
- * that runs out sets status = {GS_ERR_TIMEOUT, block}, and that block writes
- * zero pose partials. */
+ * parameters (overwritten, or added with cfg->accumulate_grads; a
+ * Gaussian's terms are summed over its views in ascending order, then
+ * written or added once) and the pose partials (always overwritten). With
+ * one view it runs the chain only for the Gaussians with a nonzero 2D
+ * gradient and writes zeros for the others (accumulating, leaves them as
+ * they are); with several views it runs the chains per block either by
+ * each Gaussian's thread or over per-view lists of the Gaussians with a
+ * gradient, whichever takes fewer warp runs (the pose partials' grouping
+ * follows that choice and is deterministic). */
 int gs_rasterize_bwd(const gs_views *views, const gs_config *cfg, const float *proj, const gs_bins *bins,
                      const float *image, const float *dL_dimage, float *grad2d, int32_t *status,
                      void *stream);
