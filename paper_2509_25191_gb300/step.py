@@ -14,7 +14,9 @@ count above the capacity is reported in the device status word and
 
 With ``slots=2`` the step keeps two copies of its per-step inputs (target
 images and view matrices, and with ``slot_gaussians=True`` the Gaussian
-parameters too) and captures one graph per copy, sharing every other buffer:
+parameters too) and of its results (``loss_slots``, ``dviewmat_slots``,
+``dtwist_slots``; ``loss`` and ``dviewmat`` are slot 0's) and captures one
+graph per slot, sharing every other buffer:
 a training loop writes step k+1's inputs into the other slot (e.g. by an
 asynchronous host-to-device copy on another stream) while step k runs, and
 replays ``replay(k % 2)``. Gaussian slots are separate tensors (slot 0 is
@@ -72,10 +74,14 @@ class GraphStep:
         self.image = torch.empty(views.num_image_floats(), device=dev)
         self.dimg = torch.empty_like(self.image)
         # l1: [mean L1]; l1_dssim: [total, mean L1, 1 - mean SSIM]
-        self.loss = torch.empty(1 if loss == "l1" else 3, device=dev)
+        # the step's results (loss, pose gradient) are kept per input slot, so
+        # that a loop can read step k's back while step k+1 runs
+        self.loss_slots = [torch.empty(1 if loss == "l1" else 3, device=dev) for _ in range(slots)]
+        self.loss = self.loss_slots[0]
         self.grads = Grads(g.n, g.sh_degree, views.num_slots(), views.n, dev, want_gaussian_grads)
-        self.dviewmat = torch.empty(views.n, 12, device=dev)
-        self.dtwist = torch.empty(views.n, 6, device=dev)
+        self.dviewmat_slots = [torch.empty(views.n, 12, device=dev) for _ in range(slots)]
+        self.dtwist_slots = [torch.empty(views.n, 6, device=dev) for _ in range(slots)]
+        self.dviewmat, self.dtwist = self.dviewmat_slots[0], self.dtwist_slots[0]
         self.graph = None
         self.graphs = []
         if capture:
@@ -96,15 +102,16 @@ class GraphStep:
         _lib.gs_render_fwd(v, cfg, self.proj, b, self.image, st)
         rec()
         if self.loss_kind == "l1":
-            _lib.gs_l1_loss(self.image, target, self.loss, self.dimg)
+            _lib.gs_l1_loss(self.image, target, self.loss_slots[slot], self.dimg)
         else:
-            _lib.gs_l1_dssim_loss(v, self.image, target, self.loss, self.dimg, self.lam)
+            _lib.gs_l1_dssim_loss(v, self.image, target, self.loss_slots[slot], self.dimg, self.lam)
         rec()
         _lib.gs_rasterize_bwd(v, cfg, self.proj, b, self.image, self.dimg, self.grads.grad2d, st)
         rec()
         _lib.gs_project_bwd(g, v, cfg, self.proj, self.grads, self.want, st)
         rec()
-        _lib.gs_pose_grad(v, self.grads.pose_partials, self.grads.n_blocks, self.dviewmat, self.dtwist)
+        _lib.gs_pose_grad(v, self.grads.pose_partials, self.grads.n_blocks, self.dviewmat_slots[slot],
+                          self.dtwist_slots[slot])
         rec()
 
     def capture(self):

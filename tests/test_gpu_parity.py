@@ -643,8 +643,10 @@ def test_bounded_wait_runs_out_and_reports():
 
 def test_graph_step_input_slots():
     """A two-slot GraphStep captures one graph per input slot (target, view
-    matrices and Gaussian parameters) over shared buffers; replaying a slot
-    gives the results of a single-slot step built on that slot's inputs."""
+    matrices and Gaussian parameters) over shared buffers, with the loss and
+    pose gradient kept per slot; replaying a slot gives the results of a
+    single-slot step built on that slot's inputs, and leaves the other
+    slot's results as they were."""
     from paper_2509_25191_gb300.step import GraphStep
     sc, vw = CASES["clustered_sh3"]()
     g = _lib.Gaussians.from_scene(sc)
@@ -665,8 +667,10 @@ def test_graph_step_input_slots():
     got = []
     for sl in (0, 1, 0):
         step.replay(sl)
-        got.append((step.loss.clone(), step.dviewmat.clone(), step.image.clone(), step.grads.means.clone(),
-                    step.grads.opacity_logits.clone()))
+        got.append((step.loss_slots[sl].clone(), step.dviewmat_slots[sl].clone(), step.image.clone(),
+                    step.grads.means.clone(), step.grads.opacity_logits.clone()))
+    # slot 1's results survive the last replay of slot 0
+    assert torch.equal(step.loss_slots[1], got[1][0]) and torch.equal(step.dviewmat_slots[1], got[1][1])
     views1 = _lib.Views(vm1, views.intrinsics, views.width, views.height, views.gauss_begin, views.gauss_count)
     refs = []
     for gg, vv, tt in ((g, views, t0), (g1, views1, t1)):
