@@ -830,10 +830,21 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
     k_project_bwd<D, G, Z><<<nblk, PB_THREADS, dyn, st>>>(                                                         \
         L, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, viewmats, intr, p, g2, out->means,        \
         out->log_scales, out->quats, out->opacity_logits, out->sh, out->pose_partials)
+    // (the per-view pose partials of up to GS_MAX_VIEWS views take the
+    // several-view kernel to the default 48 KB of shared memory per block)
 #define GS_PBV(D)                                                                                                  \
-    k_project_bwd_views<D><<<nblk, PB_THREADS, dyn, st>>>(                                                         \
-        L, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, viewmats, intr, p, g2, out->means,        \
-        out->log_scales, out->quats, out->opacity_logits, out->sh, out->pose_partials)
+    do {                                                                                                           \
+        static bool big_smem = false;                                                                              \
+        if (!big_smem) {                                                                                           \
+            if (cudaFuncSetAttribute(k_project_bwd_views<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                                     (int)(PB_WARPS * GS_MAX_VIEWS * 12 * sizeof(float))) != cudaSuccess)          \
+                return GS_ERR_CUDA;                                                                                \
+            big_smem = true;                                                                                       \
+        }                                                                                                          \
+        k_project_bwd_views<D><<<nblk, PB_THREADS, dyn, st>>>(                                                     \
+            L, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, viewmats, intr, p, g2, out->means,    \
+            out->log_scales, out->quats, out->opacity_logits, out->sh, out->pose_partials);                       \
+    } while (0)
     if (want_gauss && !compact) {
         switch (deg) {
         case 0: GS_PBV(0); break;
