@@ -463,9 +463,9 @@ int gs_ga_weights(const float *dist, int64_t n, int n_bins, double alpha, uint32
  * process exits. The pose partials of one call need V * gs_pose_blocks(n) *
  * 12 floats; a call beyond that returns GS_ERR_TOO_LARGE before enqueuing
  * anything. Every call shares the one array and leaves its contents behind
- * (each call overwrites all the partials it reads, a block whose bounded
- * copy wait runs out with zeros, so nothing needs clearing; the outputs of
- * a call that sets the status word are undefined): calls that overlap on
+ * (each call overwrites all the partials it reads, so nothing needs
+ * clearing; the outputs of a call that sets the status word are
+ * undefined): calls that overlap on
  * the GPU (other streams, other host threads on the same device) race and
  * must be serialised by the caller. An uncaptured call looks up the array's
  * device address with the current device's context (so a context that was
