@@ -294,9 +294,8 @@ __device__ __forceinline__ void gauss_epilogue(long long i, bool acc, const floa
 // parameter-gradient rows are zeroed by its block, coalesced, when the range
 // is listed, and the listed Gaussians' rows written again after a barrier
 // (accumulating, the others are left as they are). The pose partials stay
-// per block over a fixed range, so the pose gradient is deterministic. With
-// several views most Gaussians contribute somewhere and the block-wide
-// tensor copies are faster.
+// per block over a fixed range, so the pose gradient is deterministic.
+// Several views take k_project_bwd_views, which compacts per view.
 constexpr int PB_SUB = 1024;   // Gaussians compacted at a time (8 per thread)
 
 // List the Gaussians (thread indices) in [g0, g1) with a nonzero 2D-gradient
