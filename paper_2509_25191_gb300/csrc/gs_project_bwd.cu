@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
 // take its views in ascending order (as in k_project_bwd), so its gradients
 // are the same bit for bit; the pose partial of a view is summed per warp
 // over the list (fixed by the Gaussians' indices), then per block.
-constexpr int PB_LIST_VIEW_COST = 2;   // a view's listing and barriers, in chain runs of a warp
+constexpr int PB_LIST_VIEW_COST = 3;   // a view's listing and barriers, in chain runs of a warp (measured: 1-4)
 template <int DEG>
 __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd_views(
     const Launch L, const float *__restrict__ means, const float *__restrict__ log_scales,

@@ -435,7 +435,20 @@ def test_tile_size_invariance_bit_exact():
 
 @pytest.mark.parametrize("case", list(CASES))
 def test_backward_parity(case):
-    sc, vw = CASES[case]()
+    _backward_parity(*CASES[case]())
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_backward_parity_several_views_low_degree(deg):
+    """The several-view projection backward at SH degrees 0-2 (the SH
+    gradients leave one float per store for degrees 0 and 2, 16 bytes per
+    store for degree 1): 4 orbit views of a clustered scene."""
+    sc = synth.cluster_scene(5, 20000, sh_degree=deg)
+    vw = synth._views(synth.orbit_viewmats(4), 1000.0 * 200 / 979.0, 200, 112, 0, sc.n)
+    _backward_parity(sc, vw)
+
+
+def _backward_parity(sc, vw):
     bg = (0.3, 0.1, 0.2)
     rast, g, views, image, proj = gpu_forward(sc, vw, bg=bg)
     ref = oracle_forward(sc, vw, bg=bg)
