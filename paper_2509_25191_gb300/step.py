@@ -39,7 +39,18 @@ from .autograd import Rasterizer
 
 
 class GraphStep:
-    KERNELS_PER_STEP = 11   # project 1, bin/sort 5, render 1, loss 1, raster bwd 1, projection bwd 1, pose 1
+    # project 1, bin/sort 5 (count, scan, scatter, split, sort), render 1,
+    # raster bwd 1, projection bwd 1, pose 1; the loss adds 1 (L1) or 2 (L1 + D-SSIM)
+    KERNELS_FIXED = 10
+
+    def kernels_per_step(self) -> int:
+        """Kernels of this library that one step launches: the fixed ten, the
+        loss kernels, and the tile ordering by forward replay length that the
+        raster backward runs first when the image has fewer than 16 tiles per SM."""
+        loss = 1 if self.loss_kind == "l1" else 2
+        sms = torch.cuda.get_device_properties(self.g.means.device).multi_processor_count
+        order = 1 if 0 < self.bins.n_tiles < 16 * sms else 0
+        return self.KERNELS_FIXED + loss + order
 
     def __init__(self, g: Gaussians, views: Views, target, tile=(16, 16), headroom=1.25, capture=True,
                  want_gaussian_grads=True, loss="l1", lam=0.2, slots=1, slot_gaussians=False, capacity=None,
