@@ -22,9 +22,11 @@
 //   S_i = sum_{j>i} c_j alpha_j T_j + T_final bg = image - sum_{j<=i} c_j alpha_j T_j,
 // so that dL/dalpha_i = T_i (c_i . g) - (S_i . g) / (1 - alpha_i).
 // Per-Gaussian gradients (mean2D, 2D covariance, opacity, colour) are summed over a
-// warp through a shared-memory transpose (each of 27 lanes adds one value over
-// a third of the warp), over the block in shared memory, and added to the
-// per-slot grad2d record with one vector atomic per float4.
+// warp through a shared-memory transpose: a warp writes the 9 values of up to
+// three consecutive visits as rows of a per-warp buffer (one column per lane),
+// then 27 lanes each add one row with 16-byte loads; then over the block in
+// shared memory, and into the per-slot grad2d record with one vector atomic
+// per float4.
 // Both kernels run a thread's two pixels through packed float2 arithmetic
 // (f32x2 fma/mul/add, one instruction for both), branch-free: a pixel that
 // does not composite a Gaussian contributes zeros.
@@ -190,6 +192,13 @@ __device__ __forceinline__ void stage_batch(const Launch &L, const float4 *__res
 // terms (8 B) and the per-Gaussian gradient sums (9 floats).
 constexpr int FWD_STAGE_BYTES = 52;
 constexpr int BWD_STAGE_BYTES = 96;
+// The backward's per-warp reduction buffer: RED_SLOTS visits x 9 values as
+// rows of 32 lane columns, row pitch RED_PITCH floats (16-byte aligned rows;
+// the 4-float pad puts the 8 lanes of a quarter-warp reading 16 bytes of 8
+// different rows on 8 disjoint groups of 4 banks).
+constexpr int RED_SLOTS = 3;
+constexpr int RED_PITCH = 36;
+constexpr int RED_WARP_FLOATS = RED_SLOTS * 9 * RED_PITCH;
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, const float4 *__restrict__ proj,
@@ -316,27 +325,29 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
                                                             const float *__restrict__ dL_dimage,
                                                             const int *__restrict__ last_contrib,
                                                             float4 *__restrict__ grad2d) {
-    // the staged batch (L.bwd_batch Gaussians per thread) in dynamic shared
-    // memory: positions, conics, colours, the conic's A and D (natural-log
-    // units), warp masks and the per-Gaussian gradient sums (pitch 9, odd:
-    // no bank conflicts)
+    // dynamic shared memory: the per-warp reduction buffers, then the staged
+    // batch (L.bwd_batch Gaussians per thread): positions, conics, colours,
+    // the conic's A and D (natural-log units), the per-Gaussian gradient sums
+    // (pitch 9, odd: no bank conflicts) and warp masks
     constexpr int BS = TW * TH / 2;
     const int NB = L.bwd_batch * BS;
     extern __shared__ float4 s_dyn[];
-    float4 *s_xy = s_dyn, *s_con = s_xy + NB, *s_rgb = s_con + NB;
+    float *s_red = reinterpret_cast<float *>(s_dyn);
+    float4 *s_xy = s_dyn + (BS / 32) * RED_WARP_FLOATS / 4, *s_con = s_xy + NB, *s_rgb = s_con + NB;
     float2 *s_ad = reinterpret_cast<float2 *>(s_rgb + NB);
     float *s_g = reinterpret_cast<float *>(s_ad + NB);
     unsigned int *s_mask = reinterpret_cast<unsigned int *>(s_g + 9 * NB);
-    __shared__ float s_red[BS / 32][32 * 9];   // per warp: the lanes' 9 values, pitch 9
     __shared__ int s_item;
     if (counters[CNT_ABORT]) return;
     const int lane = threadIdx.x & 31;
     const unsigned int wbit = 1u << (threadIdx.x >> 5);
-    float *rb = s_red[threadIdx.x >> 5];
-    // the warp sum of value j: lane 9p + j (p < 3) adds lanes p, p + 3, ...,
-    // then lanes j + 9 and j + 18 hand their parts to lane j (the pitch-9 rows
-    // put the 27 reading lanes on 27 different banks at every step)
-    const int red_j = lane % 9, red_p = lane / 9;
+    // this warp's buffer: row 9 s + j holds value j of the warp's pending
+    // visit s (s < RED_SLOTS), column l that of lane l
+    float *rb = s_red + (threadIdx.x >> 5) * RED_WARP_FLOATS;
+    // at a flush, lane 9 s + j (j < 9) adds row 9 s + j: value j of pending
+    // visit s, whose staged index lane s holds
+    const int red_j = lane % 9, red_s = lane / 9;
+    const float4 *red_row = reinterpret_cast<const float4 *>(rb + lane * RED_PITCH);
     for (int k = threadIdx.x; k < NB; k += BS)
         for (int c = 0; c < 9; ++c) s_g[9 * k + c] = 0.f;
     for (;;) {
@@ -380,6 +391,30 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
         const float2 PCY = make_float2(ti.pcy0, ti.pcy0 + 4.f);
         float2 T = f2(1.f), CG = f2(0.f);
         unsigned int n_eval = 0, n_comp = 0;
+        // the warp's pending visits (warp-uniform) and, in lane s, the staged
+        // index of pending visit s
+        int npend = 0, kpend = 0;
+        // add the pending visits' rows to their Gaussians' sums in s_g (each
+        // row over the 32 lanes: two f32x2 chains over 8 16-byte loads, then
+        // the two lanes of the pair)
+        auto flush = [&]() {
+            __syncwarp();
+            const int kk = __shfl_sync(0xffffffffu, kpend, red_s);
+            if (lane < 9 * npend) {
+                float4 v = red_row[0];
+                float2 sa = make_float2(v.x, v.y), sb = make_float2(v.z, v.w);
+#pragma unroll
+                for (int i = 1; i < 8; ++i) {
+                    v = red_row[i];
+                    sa = __fadd2_rn(sa, make_float2(v.x, v.y));
+                    sb = __fadd2_rn(sb, make_float2(v.z, v.w));
+                }
+                sa = __fadd2_rn(sa, sb);
+                atomicAdd(&s_g[9 * kk + red_j], sa.x + sa.y);
+            }
+            npend = 0;
+            __syncwarp();   // the buffer is free for the next visits
+        };
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
             if (__syncthreads_count(LAST ? b0 >= endm : done0 && done1) == BS) break;
             stage_batch<TW, TH>(L, proj, ids, b0, r.y, L.bwd_batch, ti, s_xy, s_con, s_rgb, s_mask);
@@ -457,25 +492,24 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
                     const float2 g0 = __fmul2_rn(dp, v0), g1 = __fmul2_rn(dp, v1);
                     const float2 g2 = __fmul2_rn(g0, v0), g3 = __fmul2_rn(g0, v1), g4 = __fmul2_rn(g1, v1);
                     if (__any_sync(0xffffffffu, cp0 || cp1)) {
-                        // gradient of this thread's pixels w.r.t. (x, y, a, b, c, o, r, g, b)
-                        float gv[9] = {g0.x + g0.y, g1.x + g1.y, g2.x + g2.y, g3.x + g3.y, g4.x + g4.y,
-                                       g5.x + g5.y, g6.x + g6.y, g7.x + g7.y, g8.x + g8.y};
-#pragma unroll
-                        for (int c = 0; c < 9; ++c) rb[lane * 9 + c] = gv[c];
-                        __syncwarp();
-                        float acc = 0.f;
-                        if (lane < 27) {
-#pragma unroll
-                            for (int i = 0; i < 11; ++i)
-                                if (red_p + 3 * i < 32) acc += rb[(red_p + 3 * i) * 9 + red_j];
-                        }
-                        const float t1 = __shfl_sync(0xffffffffu, acc, (lane + 9) & 31);
-                        const float t2 = __shfl_sync(0xffffffffu, acc, (lane + 18) & 31);
-                        if (lane < 9) atomicAdd(&s_g[9 * k + lane], acc + t1 + t2);
-                        __syncwarp();   // the buffer is free for the next Gaussian
+                        // gradient of this thread's pixels w.r.t. (x, y, a, b, c, o, r, g, b),
+                        // as column `lane` of the next pending visit's rows
+                        float *wr = rb + npend * (9 * RED_PITCH) + lane;
+                        wr[0 * RED_PITCH] = g0.x + g0.y;
+                        wr[1 * RED_PITCH] = g1.x + g1.y;
+                        wr[2 * RED_PITCH] = g2.x + g2.y;
+                        wr[3 * RED_PITCH] = g3.x + g3.y;
+                        wr[4 * RED_PITCH] = g4.x + g4.y;
+                        wr[5 * RED_PITCH] = g5.x + g5.y;
+                        wr[6 * RED_PITCH] = g6.x + g6.y;
+                        wr[7 * RED_PITCH] = g7.x + g7.y;
+                        wr[8 * RED_PITCH] = g8.x + g8.y;
+                        kpend = lane == npend ? k : kpend;
+                        if (++npend == RED_SLOTS) flush();
                     }
                 }
             }
+            if (npend) flush();   // (warp-uniform) before the batch's sums leave
             __syncthreads();
             // flush this batch's per-Gaussian sums
             for (int h = 0; h < L.bwd_batch; ++h) {
@@ -548,7 +582,8 @@ template <int TW, int TH, bool COUNT, bool LAST>
 static int launch_bwd_c(const Launch &L, const float *proj, const gs_bins *b, const float *image,
                         const float *dL_dimage, float *grad2d, cudaStream_t st) {
     static int blocks_per_sm[5];
-    const size_t smem = (size_t)BWD_STAGE_BYTES * L.bwd_batch * (TW * TH / 2);
+    const size_t smem = (size_t)BWD_STAGE_BYTES * L.bwd_batch * (TW * TH / 2) +
+                        sizeof(float) * RED_WARP_FLOATS * (TW * TH / 64);
     const int grid = min(num_sms() * raster_blocks_per_sm(k_render_bwd<TW, TH, COUNT, LAST>, TW * TH / 2, smem,
                                                           L.bwd_batch, blocks_per_sm),
                          max(1, L.n_tiles));
