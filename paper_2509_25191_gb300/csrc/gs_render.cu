@@ -235,18 +235,22 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
         const int2 r = abort ? make_int2(0, 0) : ranges[tile];
         // lane .x = pixel (px, py0), lane .y = pixel (px, py0 + 4)
         float2 T = f2(1.f), CR = f2(0.f), CG = f2(0.f), CB = f2(0.f);
-        bool done0 = !ti.in0, done1 = !ti.in1;
+        // per pixel the alpha threshold it still composites at: alpha_min,
+        // or +inf once the pixel has stopped (or lies outside the image), so
+        // that the alpha test also excludes stopped pixels
+        const float amin = L.alpha_min, INF = __int_as_float(0x7f800000);
+        float am0 = ti.in0 ? amin : INF, am1 = ti.in1 ? amin : INF;
         int end0 = r.x, end1 = r.x;   // one past the last composited instance
         const float2 PCY = make_float2(ti.pcy0, ti.pcy0 + 4.f);
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
-            if (__syncthreads_count(done0 && done1) == BS) break;
+            if (__syncthreads_count(am0 == INF && am1 == INF) == BS) break;
             stage_batch<TW, TH>(L, proj, ids, b0, r.y, L.fwd_batch, ti, s_xy, s_con, s_rgb, s_mask);
             __syncthreads();
             const int nb = min(NB, r.y - b0);
             // the warp walks only the staged Gaussians that may reach its patch:
             // 32 masks per ballot, then the set bits in order
             for (int k0 = 0; k0 < nb; k0 += 32) {
-                if (__all_sync(0xffffffffu, done0 && done1)) break;
+                if (__all_sync(0xffffffffu, am0 == INF && am1 == INF)) break;
                 unsigned int hits = __ballot_sync(0xffffffffu, k0 + lane < nb && (s_mask[k0 + lane] & wbit));
                 while (hits) {
                     const int k = k0 + __ffs(hits) - 1;
@@ -259,23 +263,23 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
                     const float2 p2 = __ffma2_rn(f2(con.x), __fmul2_rn(u, u), __fmul2_rn(f2(con.z), __fmul2_rn(dy, dy)));
                     const float2 oG = __fmul2_rn(f2(con.w), make_float2(ex2_approx(p2.x), ex2_approx(p2.y)));
                     const float a0 = fminf(oG.x, L.alpha_max), a1 = fminf(oG.y, L.alpha_max);
-                    const bool ok0 = col && !done0 && fabsf(dy.x) <= xy.w && a0 >= L.alpha_min;
-                    const bool ok1 = col && !done1 && fabsf(dy.y) <= xy.w && a1 >= L.alpha_min;
+                    const bool ok0 = col && fabsf(dy.x) <= xy.w && a0 >= am0;
+                    const bool ok1 = col && fabsf(dy.y) <= xy.w && a1 >= am1;
                     if (!__any_sync(0xffffffffu, ok0 || ok1)) continue;
                     // the Gaussian that would bring T below t_min is not composited
                     // and the pixel stops; otherwise C += c alpha T, T *= 1 - alpha
                     const float2 Tn = __fmul2_rn(T, __fadd2_rn(f2(1.f), make_float2(-a0, -a1)));
                     const bool st0 = ok0 && Tn.x < L.t_min, st1 = ok1 && Tn.y < L.t_min;
                     const bool cp0 = ok0 && !st0, cp1 = ok1 && !st1;
-                    done0 = done0 || st0;
-                    done1 = done1 || st1;
+                    am0 = st0 ? INF : am0;
+                    am1 = st1 ? INF : am1;
                     end0 = cp0 ? b0 + k + 1 : end0;
                     end1 = cp1 ? b0 + k + 1 : end1;
-                    // weight and transmittance through a 0/1 mask (T (1 - alpha M) is
-                    // T (1 - alpha) bit for bit when M = 1, T when M = 0)
-                    const float2 Mcp = make_float2(cp0 ? 1.f : 0.f, cp1 ? 1.f : 0.f);
-                    const float2 w = __fmul2_rn(__fmul2_rn(make_float2(a0, a1), Mcp), T);
-                    T = __fmul2_rn(T, __ffma2_rn(make_float2(-a0, -a1), Mcp, f2(1.f)));
+                    // weight and transmittance through the composited alpha (alpha, or 0
+                    // for a pixel that does not composite: T (1 - 0) is T bit for bit)
+                    const float2 ac = make_float2(cp0 ? a0 : 0.f, cp1 ? a1 : 0.f);
+                    const float2 w = __fmul2_rn(ac, T);
+                    T = __fmul2_rn(T, __fadd2_rn(f2(1.f), make_float2(-ac.x, -ac.y)));
                     const float4 c = s_rgb[k];
                     CR = __ffma2_rn(f2(c.x), w, CR);
                     CG = __ffma2_rn(f2(c.y), w, CG);
