@@ -421,6 +421,8 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
         };
         for (int b0 = r.x; b0 < r.y; b0 += NB) {
             if (__syncthreads_count(LAST ? b0 >= endm : done0 && done1) == BS) break;
+            // LAST: the pixels' ends relative to this batch
+            const int e0 = end0 - b0, e1 = end1 - b0;
             stage_batch<TW, TH>(L, proj, ids, b0, r.y, L.bwd_batch, ti, s_xy, s_con, s_rgb, s_mask);
             for (int h = 0; h < L.bwd_batch; ++h) {
                 const int k = threadIdx.x + h * BS;
@@ -446,32 +448,45 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
                     const float2 p2 = __ffma2_rn(f2(con.x), __fmul2_rn(u, u), __fmul2_rn(f2(con.z), __fmul2_rn(dy, dy)));
                     const float2 G = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
                     const float2 oG = __fmul2_rn(f2(con.w), G);
-                    const bool cl0 = oG.x > L.alpha_max, cl1 = oG.y > L.alpha_max;
-                    const float a0 = cl0 ? L.alpha_max : oG.x, a1 = cl1 ? L.alpha_max : oG.y;
-                    const bool live0 = LAST ? b0 + k < end0 : !done0, live1 = LAST ? b0 + k < end1 : !done1;
+                    const float a0 = fminf(oG.x, L.alpha_max), a1 = fminf(oG.y, L.alpha_max);
+                    const bool live0 = LAST ? k < e0 : !done0, live1 = LAST ? k < e1 : !done1;
                     const bool ev0 = col && live0 && fabsf(dy.x) <= xy.w, ev1 = col && live1 && fabsf(dy.y) <= xy.w;
                     const bool ok0 = ev0 && a0 >= L.alpha_min, ok1 = ev1 && a1 >= L.alpha_min;
                     if (COUNT) n_eval += (unsigned int)ev0 + (unsigned int)ev1;
                     if (!__any_sync(0xffffffffu, ok0 || ok1)) continue;
                     // transmittance: the pixel stops before a Gaussian that would
                     // bring T below t_min; otherwise the Gaussian is composited
-                    // (with LAST no such Gaussian comes before the pixel's end)
-                    const float2 oma = __fadd2_rn(f2(1.f), make_float2(-a0, -a1));
-                    const float2 Tn = __fmul2_rn(T, oma);
-                    const bool st0 = !LAST && ok0 && Tn.x < L.t_min, st1 = !LAST && ok1 && Tn.y < L.t_min;
-                    const bool cp0 = ok0 && !st0, cp1 = ok1 && !st1;
-                    if (!LAST) {
+                    // (with LAST no such Gaussian comes before the pixel's end).
+                    // ac = the composited alpha (alpha, or 0 for a pixel that does not
+                    // composite, whose T (1 - 0) is T bit for bit); oma = 1 - ac
+                    bool cp0, cp1;
+                    float2 ac, oma, Tn;
+                    if constexpr (LAST) {
+                        cp0 = ok0;
+                        cp1 = ok1;
+                        ac = make_float2(cp0 ? a0 : 0.f, cp1 ? a1 : 0.f);
+                        oma = __fadd2_rn(f2(1.f), make_float2(-ac.x, -ac.y));
+                        Tn = __fmul2_rn(T, oma);
+                    } else {
+                        const float2 om = __fadd2_rn(f2(1.f), make_float2(-a0, -a1));
+                        const float2 Tt = __fmul2_rn(T, om);
+                        const bool st0 = ok0 && Tt.x < L.t_min, st1 = ok1 && Tt.y < L.t_min;
+                        cp0 = ok0 && !st0;
+                        cp1 = ok1 && !st1;
                         done0 = done0 || st0;
                         done1 = done1 || st1;
+                        ac = make_float2(cp0 ? a0 : 0.f, cp1 ? a1 : 0.f);
+                        oma = om;   // (enters only terms that are zero where nothing is composited)
+                        Tn = make_float2(cp0 ? Tt.x : T.x, cp1 ? Tt.y : T.y);
                     }
                     if (COUNT) n_comp += (unsigned int)cp0 + (unsigned int)cp1;
                     // gradients; a pixel that does not composite contributes zeros
                     // (its weight and its alpha factors are zero)
                     const float4 c = s_rgb[k];
                     const float2 ad = s_ad[k];
-                    const float2 w = __fmul2_rn(make_float2(cp0 ? a0 : 0.f, cp1 ? a1 : 0.f), T);
+                    const float2 w = __fmul2_rn(ac, T);
                     const float2 Told = T;
-                    T = make_float2(cp0 ? Tn.x : T.x, cp1 ? Tn.y : T.y);
+                    T = Tn;
                     const float2 g6 = __fmul2_rn(w, GR), g7 = __fmul2_rn(w, GG), g8 = __fmul2_rn(w, GB);
                     // c.g, and C.g accumulated through this Gaussian; S.g = image.g - C.g,
                     // dL/dalpha = T (c.g) - (S.g) / (1 - alpha) (1 - alpha >= 0.01, so
@@ -487,10 +502,11 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
                     // v v^T / 2, i.e. (v0^2/2, v0 v1, v1^2/2) for (a, b, c); summing these
                     // well-scaled terms avoids the ill-conditioned conic -> covariance
                     // conversion of summed conic gradients. The halves of the (a) and (c)
-                    // sums are applied once, at the flush.
-                    const bool un0 = cp0 && !cl0, un1 = cp1 && !cl1;
+                    // sums are applied once, at the flush. Gu = G where the pixel composites
+                    // an unclamped alpha, else 0; d alpha / d power = o Gu.
+                    const bool un0 = cp0 && oG.x <= L.alpha_max, un1 = cp1 && oG.y <= L.alpha_max;
                     const float2 g5 = __fmul2_rn(dla, make_float2(un0 ? G.x : 0.f, un1 ? G.y : 0.f));
-                    const float2 dp = __fmul2_rn(dla, make_float2(un0 ? a0 : 0.f, un1 ? a1 : 0.f));
+                    const float2 dp = __fmul2_rn(f2(con.w), g5);
                     const float2 v0 = __fmul2_rn(f2(ad.x), u);
                     const float2 v1 = __ffma2_rn(v0, f2(con.y), __fmul2_rn(f2(ad.y), dy));
                     const float2 g0 = __fmul2_rn(dp, v0), g1 = __fmul2_rn(dp, v1);
