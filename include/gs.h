@@ -137,6 +137,14 @@ typedef struct gs_bins {
                              tile's start if none). gs_render_fwd writes it; gs_rasterize_bwd, given the
                              same bins, then stops each pixel there instead of replaying its list to
                              the end. 4 bytes per pixel: an index, not a stored transmittance. */
+    int32_t *tile_work;   /* optional [T] (NULL = none), used with last_contrib when the call has fewer
+                             than 16 tiles per SM: per tile, the replay length of the last gs_render_fwd
+                             on these bins (the largest last-contributor offset of its pixels). Kept
+                             across calls: gs_render_fwd takes its tiles longest first by these values
+                             (a value <= 0 counts as the tile's instance count) and overwrites them;
+                             gs_rasterize_bwd takes its tiles in the same way. Only the order in which
+                             the persistent blocks take the tiles depends on it, never a result, so any
+                             contents are safe (zero it once for a count-ordered first call). */
 } gs_bins;
 #define GS_NUM_COUNTERS 16
 
@@ -175,7 +183,7 @@ int gs_pose_blocks(int64_t n);
 
 /* One caller buffer for every scratch array of a forward + backward step over
  * these views: the tile lists of gs_bins (tile_ranges, keys, ids, keys_tmp,
- * tile_order, tile_scratch, counters, last_contrib for `capacity` tile
+ * tile_order, tile_scratch, counters, last_contrib, tile_work for `capacity` tile
  * instances) and the backward's grad2d [P,12] and pose_partials [V,
  * gs_pose_blocks(n_gaussians), 12]. gs_workspace_size returns its size in
  * bytes (0 for invalid arguments); gs_workspace_carve fills bins (all of its

@@ -63,7 +63,8 @@ class gs_views(ctypes.Structure):
 class gs_bins(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int64), ("tile_ranges", ctypes.c_void_p), ("keys", ctypes.c_void_p),
                 ("ids", ctypes.c_void_p), ("keys_tmp", ctypes.c_void_p), ("tile_order", ctypes.c_void_p),
-                ("tile_scratch", ctypes.c_void_p), ("counters", ctypes.c_void_p), ("last_contrib", ctypes.c_void_p)]
+                ("tile_scratch", ctypes.c_void_p), ("counters", ctypes.c_void_p), ("last_contrib", ctypes.c_void_p),
+                ("tile_work", ctypes.c_void_p)]
 
 
 class gs_adam_group(ctypes.Structure):
@@ -236,7 +237,9 @@ class Views:
 class Bins:
     """Caller-owned tile-list buffers (device). With pixels > 0 the per-pixel
     last-contributor record is kept too (the forward writes it, the backward
-    ends each pixel's replay there)."""
+    ends each pixel's replay there), and the per-tile work record (each
+    forward orders its tiles by the previous forward's replay lengths and
+    writes its own)."""
 
     def __init__(self, n_tiles, capacity, device="cuda", pixels=0):
         self.n_tiles, self.capacity, self.pixels = int(n_tiles), int(capacity), int(pixels)
@@ -250,13 +253,14 @@ class Bins:
         self.keys_tmp = torch.empty(cap, dtype=torch.int64, device=device)
         self.ids = torch.empty(cap, dtype=torch.int32, device=device)
         self.last_contrib = torch.empty(self.pixels, **i32) if self.pixels > 0 else None
+        self.tile_work = torch.zeros(max(1, self.n_tiles), **i32) if self.pixels > 0 else None
 
     def c(self, last=True) -> gs_bins:
         """The C struct; last=False leaves the last-contributor record out
         (NULL), e.g. for a backward whose forward wrote another image."""
         return gs_bins(self.capacity, _ptr(self.tile_ranges), _ptr(self.keys), _ptr(self.ids), _ptr(self.keys_tmp),
                        _ptr(self.tile_order), _ptr(self.tile_scratch), _ptr(self.counters),
-                       _ptr(self.last_contrib) if last else None)
+                       _ptr(self.last_contrib) if last else None, _ptr(self.tile_work) if last else None)
 
 
 class Grads:

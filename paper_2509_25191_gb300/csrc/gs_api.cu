@@ -256,13 +256,13 @@ int64_t gs_pixel_base(const gs_views *vw, int v) {
 int gs_pose_blocks(int64_t n) { return pose_blocks(n); }
 
 // Pieces of the step workspace, in this order, each at a 256-byte boundary.
-static size_t ws_layout(const gs_views *vw, const gs_config *cfg, int64_t n, int64_t cap, size_t off[10]) {
+static size_t ws_layout(const gs_views *vw, const gs_config *cfg, int64_t n, int64_t cap, size_t off[11]) {
     if (!vw || !cfg || vw->n_views < 1 || vw->n_views > GS_MAX_VIEWS || !vw->width || !vw->height ||
         !vw->gauss_count || n < 0 || cap < 0 || cfg->tile_w < 1 || cfg->tile_h < 1)
         return 0;
     const int64_t T = gs_num_tiles(vw, cfg), P = gs_num_slots(vw), px = gs_num_image_floats(vw) / 3;
     const int64_t c = cap > 0 ? cap : 1;
-    const size_t sizes[10] = {
+    const size_t sizes[11] = {
         sizeof(int32_t) * 2 * (size_t)(T > 0 ? T : 1),           // tile_ranges
         sizeof(uint64_t) * (size_t)c,                            // keys
         sizeof(uint32_t) * (size_t)c,                            // ids
@@ -271,10 +271,11 @@ static size_t ws_layout(const gs_views *vw, const gs_config *cfg, int64_t n, int
         sizeof(int32_t) * 5 * (size_t)(T > 0 ? T : 1),           // tile_scratch
         sizeof(int32_t) * GS_NUM_COUNTERS,                       // counters
         sizeof(int32_t) * (size_t)(px > 0 ? px : 1),             // last_contrib
+        sizeof(int32_t) * (size_t)(T > 0 ? T : 1),               // tile_work
         sizeof(float) * GS_GRAD2D_FLOATS * (size_t)(P > 0 ? P : 1),                      // grad2d
         sizeof(float) * 12 * (size_t)vw->n_views * (size_t)pose_blocks(n)};              // pose_partials
     size_t at = 0;
-    for (int k = 0; k < 10; ++k) {
+    for (int k = 0; k < 11; ++k) {
         off[k] = at;
         at += (sizes[k] + 255) & ~(size_t)255;
     }
@@ -282,13 +283,13 @@ static size_t ws_layout(const gs_views *vw, const gs_config *cfg, int64_t n, int
 }
 
 size_t gs_workspace_size(const gs_views *vw, const gs_config *cfg, int64_t n_gaussians, int64_t capacity) {
-    size_t off[10];
+    size_t off[11];
     return ws_layout(vw, cfg, n_gaussians, capacity, off);
 }
 
 int gs_workspace_carve(const gs_views *vw, const gs_config *cfg, int64_t n_gaussians, int64_t capacity, void *ws,
                        size_t ws_bytes, gs_bins *bins, gs_grads *grads) {
-    size_t off[10];
+    size_t off[11];
     const size_t need = ws_layout(vw, cfg, n_gaussians, capacity, off);
     if (!need || !ws || ws_bytes < need || ((uintptr_t)ws & 255u) || !bins || !grads) return GS_ERR_ARG;
     char *b = static_cast<char *>(ws);
@@ -301,8 +302,9 @@ int gs_workspace_carve(const gs_views *vw, const gs_config *cfg, int64_t n_gauss
     bins->tile_scratch = reinterpret_cast<int32_t *>(b + off[5]);
     bins->counters = reinterpret_cast<int32_t *>(b + off[6]);
     bins->last_contrib = reinterpret_cast<int32_t *>(b + off[7]);
-    grads->grad2d = reinterpret_cast<float *>(b + off[8]);
-    grads->pose_partials = reinterpret_cast<float *>(b + off[9]);
+    bins->tile_work = reinterpret_cast<int32_t *>(b + off[8]);
+    grads->grad2d = reinterpret_cast<float *>(b + off[9]);
+    grads->pose_partials = reinterpret_cast<float *>(b + off[10]);
     return GS_OK;
 }
 

@@ -578,62 +578,38 @@ static int raster_blocks_per_sm(K kernel, int threads, size_t smem, int batch, i
 static bool order_by_work(const Launch &L, const gs_bins *b) {
     return b->last_contrib && L.n_tiles > 0 && L.n_tiles < 16LL * num_sms();
 }
+// where the forward records the replay lengths: the caller's kept record,
+// else tile_scratch (this call only)
+static int *work_record(const gs_bins *b) { return b->tile_work ? b->tile_work : b->tile_scratch; }
 
-template <int TW, int TH>
-static int launch_fwd_t(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st) {
-    static int blocks_per_sm[5];
-    const size_t smem = (size_t)FWD_STAGE_BYTES * L.fwd_batch * (TW * TH / 2);
-    const int grid = min(num_sms() * raster_blocks_per_sm(k_render_fwd<TW, TH>, TW * TH / 2, smem, L.fwd_batch,
-                                                          blocks_per_sm),
-                         max(1, L.n_tiles));
-    // every call walks all tiles again: reset this kernel's work-queue head
-    if (cudaMemsetAsync(b->counters + CNT_Q_FWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
-    // with the last-contributor record and few tiles per SM, also each
-    // tile's replay length for the backward's work order (in tile_scratch,
-    // free after the sort)
-    k_render_fwd<TW, TH><<<grid, TW * TH / 2, smem, st>>>(L, reinterpret_cast<const float4 *>(proj),
-                                                       reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
-                                                       b->tile_order, b->counters, image, b->last_contrib,
-                                                       order_by_work(L, b) ? b->tile_scratch : nullptr);
-    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
-}
-
-template <int TW, int TH, bool COUNT, bool LAST>
-static int launch_bwd_c(const Launch &L, const float *proj, const gs_bins *b, const float *image,
-                        const float *dL_dimage, float *grad2d, cudaStream_t st) {
-    static int blocks_per_sm[5];
-    const size_t smem = (size_t)BWD_STAGE_BYTES * L.bwd_batch * (TW * TH / 2) +
-                        sizeof(float) * RED_WARP_FLOATS * (TW * TH / 64);
-    const int grid = min(num_sms() * raster_blocks_per_sm(k_render_bwd<TW, TH, COUNT, LAST>, TW * TH / 2, smem,
-                                                          L.bwd_batch, blocks_per_sm),
-                         max(1, L.n_tiles));
-    if (cudaMemsetAsync(b->counters + CNT_Q_BWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
-    k_render_bwd<TW, TH, COUNT, LAST><<<grid, TW * TH / 2, smem, st>>>(
-        L, reinterpret_cast<const float4 *>(proj), reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
-        b->tile_order, b->counters, image, dL_dimage, b->last_contrib, reinterpret_cast<float4 *>(grad2d));
-    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
-}
-
-// The backward's work order: the tiles by decreasing replay length (the
-// forward's record), so that the longest replays start first and the
-// persistent blocks finish together (ordered by instance count, the blocks
-// of the 32x32 backward on the 1M-Gaussian view were busy 86 % of the
-// kernel's time on average, the busiest 99 %). One block; 1024 buckets of
-// the length, 32 per octave; order within a bucket is unspecified (no result
-// depends on the order).
+// The work order of a raster kernel: the tiles by decreasing predicted work,
+// so that the longest start first and the persistent blocks finish together
+// (ordered by instance count, the blocks of the 32x32 backward on the
+// 1M-Gaussian view were busy 86 % of the kernel's time on average, the
+// busiest 99 %). The prediction is a recorded replay length, or with
+// `ranges` given and nothing recorded (<= 0) the tile's instance count. One
+// block; 1024 buckets of the prediction, 32 per octave; order within a bucket
+// is unspecified (no result depends on the order).
 __device__ __forceinline__ int work_bucket(int w) {
     if (w <= 0) return 0;
     const int e = 31 - __clz(w);
     return min(1023, e * 32 + ((w >> max(0, e - 5)) & 31));
 }
-__global__ void __launch_bounds__(1024) k_order_by_work(const int *__restrict__ work, int n_tiles,
+__global__ void __launch_bounds__(1024) k_order_by_work(const int *__restrict__ work,
+                                                       const int2 *__restrict__ ranges, int n_tiles,
                                                        int *__restrict__ order) {
     __shared__ int s_cnt[1024];
     __shared__ int s_part[32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    auto predicted = [&](int t) {
+        const int w = work[t];
+        if (w > 0 || !ranges) return w;
+        const int2 r = ranges[t];
+        return r.y - r.x;
+    };
     s_cnt[tid] = 0;
     __syncthreads();
-    for (int t = tid; t < n_tiles; t += 1024) atomicAdd(&s_cnt[work_bucket(work[t])], 1);
+    for (int t = tid; t < n_tiles; t += 1024) atomicAdd(&s_cnt[work_bucket(predicted(t))], 1);
     __syncthreads();
     // exclusive scan over the buckets from the longest down: thread i owns
     // bucket 1023 - i
@@ -659,16 +635,59 @@ __global__ void __launch_bounds__(1024) k_order_by_work(const int *__restrict__ 
     __syncthreads();
     s_cnt[1023 - tid] = s_part[wid] + incl - c;   // the bucket's first position
     __syncthreads();
-    for (int t = tid; t < n_tiles; t += 1024) order[atomicAdd(&s_cnt[work_bucket(work[t])], 1)] = t;
+    for (int t = tid; t < n_tiles; t += 1024) order[atomicAdd(&s_cnt[work_bucket(predicted(t))], 1)] = t;
+}
+
+template <int TW, int TH>
+static int launch_fwd_t(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st) {
+    static int blocks_per_sm[5];
+    const size_t smem = (size_t)FWD_STAGE_BYTES * L.fwd_batch * (TW * TH / 2);
+    const int grid = min(num_sms() * raster_blocks_per_sm(k_render_fwd<TW, TH>, TW * TH / 2, smem, L.fwd_batch,
+                                                          blocks_per_sm),
+                         max(1, L.n_tiles));
+    // every call walks all tiles again: reset this kernel's work-queue head
+    if (cudaMemsetAsync(b->counters + CNT_Q_FWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
+    // with the last-contrib record and few tiles per SM, also each tile's
+    // replay length for the backward's work order: into the kept work record
+    // (after taking this forward's order from the previous one's lengths,
+    // the instance count where none is recorded; the sort no longer needs
+    // tile_order), else into tile_scratch (free after the sort)
+    const bool ordered = order_by_work(L, b);
+    if (ordered && b->tile_work) {
+        k_order_by_work<<<1, 1024, 0, st>>>(b->tile_work, reinterpret_cast<const int2 *>(b->tile_ranges),
+                                            (int)L.n_tiles, b->tile_order);
+        if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
+    }
+    k_render_fwd<TW, TH><<<grid, TW * TH / 2, smem, st>>>(L, reinterpret_cast<const float4 *>(proj),
+                                                       reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
+                                                       b->tile_order, b->counters, image, b->last_contrib,
+                                                       ordered ? work_record(b) : nullptr);
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+template <int TW, int TH, bool COUNT, bool LAST>
+static int launch_bwd_c(const Launch &L, const float *proj, const gs_bins *b, const float *image,
+                        const float *dL_dimage, float *grad2d, cudaStream_t st) {
+    static int blocks_per_sm[5];
+    const size_t smem = (size_t)BWD_STAGE_BYTES * L.bwd_batch * (TW * TH / 2) +
+                        sizeof(float) * RED_WARP_FLOATS * (TW * TH / 64);
+    const int grid = min(num_sms() * raster_blocks_per_sm(k_render_bwd<TW, TH, COUNT, LAST>, TW * TH / 2, smem,
+                                                          L.bwd_batch, blocks_per_sm),
+                         max(1, L.n_tiles));
+    if (cudaMemsetAsync(b->counters + CNT_Q_BWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
+    k_render_bwd<TW, TH, COUNT, LAST><<<grid, TW * TH / 2, smem, st>>>(
+        L, reinterpret_cast<const float4 *>(proj), reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
+        b->tile_order, b->counters, image, dL_dimage, b->last_contrib, reinterpret_cast<float4 *>(grad2d));
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
 template <int TW, int TH>
 static int launch_bwd_t(const Launch &L, const float *proj, const gs_bins *b, const float *image,
                         const float *dL_dimage, float *grad2d, cudaStream_t st) {
     if (b->last_contrib) {
-        // the forward recorded each tile's replay length in tile_scratch
+        // the forward recorded each tile's replay length
         if (order_by_work(L, b)) {
-            k_order_by_work<<<1, 1024, 0, st>>>(b->tile_scratch, (int)L.n_tiles, b->tile_order);
+            k_order_by_work<<<1, 1024, 0, st>>>(work_record(b), nullptr, (int)L.n_tiles, b->tile_order);
             if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
         }
         return L.count_pairs ? launch_bwd_c<TW, TH, true, true>(L, proj, b, image, dL_dimage, grad2d, st)

@@ -45,11 +45,12 @@ class GraphStep:
 
     def kernels_per_step(self) -> int:
         """Kernels of this library that one step launches: the fixed ten, the
-        loss kernels, and the tile ordering by forward replay length that the
-        raster backward runs first when the image has fewer than 16 tiles per SM."""
+        loss kernels, and, when the image has fewer than 16 tiles per SM, the
+        tile orderings by replay length that the raster forward (from the
+        previous forward's record) and the raster backward run first."""
         loss = 1 if self.loss_kind == "l1" else 2
         sms = torch.cuda.get_device_properties(self.g.means.device).multi_processor_count
-        order = 1 if 0 < self.bins.n_tiles < 16 * sms else 0
+        order = 2 if 0 < self.bins.n_tiles < 16 * sms else 0
         return self.KERNELS_FIXED + loss + order
 
     def __init__(self, g: Gaussians, views: Views, target, tile=(16, 16), headroom=1.25, capture=True,

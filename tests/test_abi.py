@@ -142,7 +142,8 @@ def test_workspace_layout_on_the_host():
     blocks = int(_lib.load().gs_pose_blocks(ctypes.c_int64(n)))
     pieces = [(bins.tile_ranges, 8 * T), (bins.keys, 8 * cap), (bins.ids, 4 * cap), (bins.keys_tmp, 8 * cap),
               (bins.tile_order, 4 * T), (bins.tile_scratch, 20 * T), (bins.counters, 4 * _lib.GS_NUM_COUNTERS),
-              (bins.last_contrib, 4 * views.pixels), (g2d, 4 * 12 * P), (pp, 4 * 12 * views.n * blocks)]
+              (bins.last_contrib, 4 * views.pixels), (bins.tile_work, 4 * T), (g2d, 4 * 12 * P),
+              (pp, 4 * 12 * views.n * blocks)]
     spans = sorted((p, p + nbytes) for p, nbytes in pieces)
     assert all(p % 256 == 0 and base <= p and e <= base + size for p, e in spans)
     assert all(spans[i][1] <= spans[i + 1][0] for i in range(len(spans) - 1))

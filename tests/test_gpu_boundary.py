@@ -158,6 +158,55 @@ def test_last_contributor_replay_equals_full_replay(case, tile):
         off += W * H
 
 
+@pytest.mark.parametrize("case", ["clustered_sh3", "orbit_4views", "uneven_3scenes"])
+def test_tile_work_record_orders_without_changing_results(case):
+    """The kept per-tile work record only orders the raster kernels' tiles:
+    whatever it holds (zeros, garbage, the previous forward's lengths) the
+    image is bit-identical and the 2D gradients agree up to float-atomic
+    order; after a forward it holds each tile's replay length, the largest
+    last-contributor offset of its pixels from the tile's start."""
+    sc, vw = CASES[case]()
+    tile = (16, 16)
+    rast, g, views, image, proj = gpu_forward(sc, vw, tile=tile)
+    b, cfg = rast.bins, rast.cfg
+    T = views.num_tiles(cfg)
+    assert b.tile_work is not None and 0 < T < 16 * torch.cuda.get_device_properties(0).multi_processor_count
+    up = torch.randn(views.num_image_floats(), device="cuda", generator=torch.Generator("cuda").manual_seed(8))
+    ref = torch.empty(max(1, views.num_slots()), _lib.GS_GRAD2D_FLOATS, device="cuda")
+    _lib.gs_rasterize_bwd(views, cfg, proj, b, image, up, ref)
+    R = ref.cpu().numpy()
+    gen = torch.Generator("cuda").manual_seed(9)
+    for fill in ("zeros", "garbage", "previous"):
+        if fill == "zeros":
+            b.tile_work.zero_()
+        elif fill == "garbage":
+            b.tile_work.copy_(torch.randint(-2 ** 31, 2 ** 31 - 1, b.tile_work.shape, generator=gen, device="cuda",
+                                            dtype=torch.int64).to(torch.int32))
+        img = torch.empty_like(image)
+        _lib.gs_render_fwd(views, cfg, proj, b, img, _lib.new_status())
+        gd = torch.empty_like(ref)
+        _lib.gs_rasterize_bwd(views, cfg, proj, b, img, up, gd)
+        torch.cuda.synchronize()
+        assert torch.equal(img, image), fill
+        D = gd.cpu().numpy()
+        assert np.linalg.norm(D - R) <= 1e-5 * np.linalg.norm(R) + 1e-30, fill
+    # the record left by the last forward
+    work = b.tile_work.cpu().numpy()[:T]
+    ranges = b.tile_ranges.cpu().numpy().reshape(-1, 2)
+    last = b.last_contrib.cpu().numpy()
+    expect = np.zeros(T, np.int64)
+    off = 0
+    tw, th = tile
+    for v in range(views.n):
+        W, H = int(vw.width[v]), int(vw.height[v])
+        Gx = (W + tw - 1) // tw
+        yy, xx = np.mgrid[0:H, 0:W]
+        t = (views.tile_base(cfg, v) + (yy // th) * Gx + xx // tw).ravel()
+        np.maximum.at(expect, t, last[off:off + W * H].astype(np.int64) - ranges[t, 0])
+        off += W * H
+    assert np.array_equal(work, expect)
+
+
 def test_workspace_step_equals_the_rasterizer():
     """A forward and backward whose tile lists, 2D gradients and pose
     partials are carved from one caller buffer give the Rasterizer's image
