@@ -275,10 +275,16 @@ int gs_render_bwd(const gs_gaussians *g, const gs_views *views, const gs_config 
  * written or added once) and the pose partials (always overwritten). With
  * one view it runs the chain only for the Gaussians with a nonzero 2D
  * gradient and writes zeros for the others (accumulating, leaves them as
- * they are); with several views it runs the chains per block either by
- * each Gaussian's thread or over per-view lists of the Gaussians with a
- * gradient, whichever takes fewer warp runs (the pose partials' grouping
- * follows that choice and is deterministic). */
+ * they are); that one-view call with parameter gradients is launched as a
+ * programmatic dependent of the kernel ahead of it on the stream (in a step,
+ * gs_rasterize_bwd's): its blocks may start in that kernel's tail and zero
+ * their parameter-gradient rows before waiting for it to finish, so the
+ * kernel ahead must not write the parameter-gradient outputs (nothing else
+ * it reads or writes is touched before the wait). With several views it
+ * runs the chains per block either by each Gaussian's thread or over
+ * per-view lists of the Gaussians with a gradient, whichever takes fewer
+ * warp runs (the pose partials' grouping follows that choice and is
+ * deterministic). */
 int gs_rasterize_bwd(const gs_views *views, const gs_config *cfg, const float *proj, const gs_bins *bins,
                      const float *image, const float *dL_dimage, float *grad2d, int32_t *status,
                      void *stream);

@@ -290,10 +290,12 @@ __device__ __forceinline__ void gauss_epilogue(long long i, bool acc, const floa
 // thread per Gaussian left most lanes idle. Instead each block takes a
 // contiguous range of Gaussians, finds those with a nonzero 2D-gradient row
 // (PB_SUB at a time, listed in shared memory in an order fixed by their
-// indices) and runs the chain over the list with full warps. Each range's
-// parameter-gradient rows are zeroed by its block, coalesced, when the range
-// is listed, and the listed Gaussians' rows written again after a barrier
-// (accumulating, the others are left as they are). The pose partials stay
+// indices) and runs the chain over the list with full warps. A block's
+// parameter-gradient rows are zeroed by the block, coalesced, before
+// anything else (launched as a programmatic dependent of the raster backward,
+// while that kernel's last blocks still run), and the listed Gaussians' rows
+// written again after a barrier (accumulating, the others are left as they
+// are). The pose partials stay
 // per block over a fixed range, so the pose gradient is deterministic.
 // Several views take k_project_bwd_views, which compacts per view.
 constexpr int PB_SUB = 1024;   // Gaussians compacted at a time (8 per thread)
@@ -401,7 +403,18 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
         const long long per = (L.n_threads + gridDim.x - 1) / gridDim.x;
         c_next = min((long long)L.n_threads, (long long)blockIdx.x * per);
         c_end = min((long long)L.n_threads, c_next + per);
+        if (GAUSS && !L.accumulate && c_next < c_end) {
+            // this block's rows, zero (one view: its Gaussians are contiguous);
+            // they depend on nothing the raster backward writes, so this runs
+            // before the wait below, on SMs the raster backward has left. The
+            // listed Gaussians' rows are written again after later barriers.
+            const int sc = scene_of_thread(L, c_next);
+            zero_rows<K>(L.s[sc].g_begin + (c_next - L.s[sc].thread_base), c_end - c_next, g_means, g_log_scales,
+                         g_quats, g_logits, g_sh);
+        }
     }
+    // the 2D gradients and everything else below come from the kernels ahead
+    grid_dependency_wait();
     for (long long base = (long long)blockIdx.x * PB_THREADS;; base += stride) {
         long long gid;
         bool valid;
@@ -409,15 +422,6 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
             while (c_pos >= c_cnt && c_next < c_end) {   // (uniform over the block)
                 const long long g1 = min(c_end, c_next + PB_SUB);
                 c_cnt = compact_range(L, grad2d, c_next, g1, s_list, s_wsum);
-                if (GAUSS && !L.accumulate) {
-                    // this range's rows, zero; the listed Gaussians' rows are
-                    // written again below by this block, after a barrier (one
-                    // view: the range's Gaussians are contiguous)
-                    const int sc = scene_of_thread(L, c_next);
-                    zero_rows<K>(L.s[sc].g_begin + (c_next - L.s[sc].thread_base), g1 - c_next, g_means,
-                                 g_log_scales, g_quats, g_logits, g_sh);
-                    __syncthreads();
-                }
                 c_at = c_next;
                 c_next = g1;
                 c_pos = 0;
@@ -829,6 +833,26 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
     k_project_bwd<D, G, Z><<<nblk, PB_THREADS, dyn, st>>>(                                                         \
         L, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, viewmats, intr, p, g2, out->means,        \
         out->log_scales, out->quats, out->opacity_logits, out->sh, out->pose_partials)
+    // one-view calls with parameter gradients: a programmatic dependent of the
+    // kernel ahead (the raster backward in a step), so that each block zeroes
+    // its rows while that kernel's tail still runs
+#define GS_PB_EARLY(D)                                                                                             \
+    do {                                                                                                           \
+        cudaLaunchConfig_t lc = {};                                                                                \
+        cudaLaunchAttribute at[1];                                                                                 \
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                                            \
+        at[0].val.programmaticStreamSerializationAllowed = 1;                                                     \
+        lc.gridDim = dim3(nblk);                                                                                   \
+        lc.blockDim = dim3(PB_THREADS);                                                                            \
+        lc.dynamicSmemBytes = dyn;                                                                                 \
+        lc.stream = st;                                                                                            \
+        lc.attrs = at;                                                                                             \
+        lc.numAttrs = 1;                                                                                           \
+        if (cudaLaunchKernelEx(&lc, k_project_bwd<D, true, true>, L, g->means, g->log_scales, g->quats,           \
+                               g->opacity_logits, g->sh, viewmats, intr, p, g2, out->means, out->log_scales,      \
+                               out->quats, out->opacity_logits, out->sh, out->pose_partials) != cudaSuccess)      \
+            return GS_ERR_CUDA;                                                                                    \
+    } while (0)
     // (the per-view pose partials of up to GS_MAX_VIEWS views take the
     // several-view kernel to the default 48 KB of shared memory per block)
 #define GS_PBV(D)                                                                                                  \
@@ -854,10 +878,10 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
         }
     } else if (want_gauss) {
         switch (deg) {
-        case 0: GS_PB(0, true, true); break;
-        case 1: GS_PB(1, true, true); break;
-        case 2: GS_PB(2, true, true); break;
-        case 3: GS_PB(3, true, true); break;
+        case 0: GS_PB_EARLY(0); break;
+        case 1: GS_PB_EARLY(1); break;
+        case 2: GS_PB_EARLY(2); break;
+        case 3: GS_PB_EARLY(3); break;
         default: return GS_ERR_UNSUPPORTED;
         }
     } else {
@@ -872,6 +896,7 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
         }
     }
 #undef GS_PB
+#undef GS_PB_EARLY
 #undef GS_PBV
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

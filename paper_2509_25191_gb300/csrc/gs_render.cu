@@ -342,6 +342,10 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
     float *s_g = reinterpret_cast<float *>(s_ad + NB);
     unsigned int *s_mask = reinterpret_cast<unsigned int *>(s_g + 9 * NB);
     __shared__ int s_item;
+    // the projection backward that follows (launched as a programmatic
+    // dependent) may start its blocks on SMs this kernel leaves in its tail:
+    // it zeroes its gradient rows there, then waits for this grid to finish
+    launch_dependents();
     if (counters[CNT_ABORT]) return;
     const int lane = threadIdx.x & 31;
     const unsigned int wbit = 1u << (threadIdx.x >> 5);
