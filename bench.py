@@ -288,8 +288,7 @@ def run_native(args, rank, world, local_rank):
     rast.check_status()
 
     # per-stage durations (CUDA events on the launching stream, eager calls)
-    names = ["gs_project", "gs_bin_sort", "gs_render_fwd", "gs_l1_loss", "gs_rasterize_bwd", "gs_project_bwd",
-             "gs_pose_grad"]
+    names = list(step.stages)
     acc = np.zeros(len(names))
     reps = 10
     for _ in range(reps):
@@ -434,7 +433,7 @@ def run_native(args, rank, world, local_rank):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     top = int(np.argmax(stage_ms))
     t_top = stage_ms[top] * 1e-3
-    if names[top] in ("gs_render_fwd", "gs_rasterize_bwd"):
+    if names[top] in ("gs_render_fwd", "gs_rasterize_bwd", "gs_rasterize_bwd_l1"):
         fwd = names[top] == "gs_render_fwd"
         ev_, co_ = (pairs[0], pairs[1]) if fwd else (pairs[2], pairs[3])
         flops = (FWD_FLOPS_EVAL if fwd else BWD_FLOPS_EVAL) * ev_
@@ -498,6 +497,9 @@ def run_native(args, rank, world, local_rank):
     step_bytes = algorithmic_bytes(g.n, g.sh_degree, views.num_slots(), n_inst, P, views.num_tiles(cfg))
     hbm_frac_step = step_bytes / (ms * 1e-3) / (peaks["hbm_gbs"] * 1e9)
     sb = stage_bytes(g.n, g.sh_degree, views.num_slots(), n_inst, P, views.num_tiles(cfg))
+    # (the raster backward with the L1 loss folded in reads the target where
+    # the plain one reads dL/dimage: the same bytes)
+    sb["gs_rasterize_bwd_l1"] = sb["gs_rasterize_bwd"]
     stage_frac = {n: {"algorithmic_bytes": int(sb[n]), "ms": round(float(t), 4),
                       "frac_of_hbm": round(sb[n] / (float(t) * 1e-3) / (peaks["hbm_gbs"] * 1e9), 4)}
                   for n, t in zip(names, stage_ms) if n in sb}
@@ -573,8 +575,7 @@ def batched_vs_plain(dev, tile, steps=20, plain_steps=5):
     # where each arm's time goes: eager per-stage events (the batched step's
     # calls once over all views; the plain arm's calls per view, summed)
     reps = 3
-    bn = ["gs_project", "gs_bin_sort", "gs_render_fwd", "gs_l1_loss", "gs_rasterize_bwd", "gs_project_bwd",
-          "gs_pose_grad"]
+    bn = list(gs.stages)
     bacc = np.zeros(len(bn))
     pacc = np.zeros(len(PlainStep.STAGES))
     for _ in range(reps):
@@ -741,8 +742,7 @@ def run_dense(dev, steps=10, n=6_000_000, n_views=300, batch=8):
         raise RuntimeError("capacity overflow during the dense step")
     ms = a.elapsed_time(b) / steps
     # where the rasterizer step's time goes (eager calls, per-stage events)
-    sn = ["gs_project", "gs_bin_sort", "gs_render_fwd", "gs_l1_loss", "gs_rasterize_bwd", "gs_project_bwd",
-          "gs_pose_grad"]
+    sn = list(step.stages)
     sacc = np.zeros(len(sn))
     for _ in range(3):
         ev = []

@@ -292,6 +292,20 @@ int gs_project_bwd(const gs_gaussians *g, const gs_views *views, const gs_config
                    const float *grad2d, const gs_grads *grads, int want_gaussian_grads, int32_t *status,
                    void *stream);
 
+/* gs_rasterize_bwd for the mean L1 photometric loss (Section 3.1 photometric
+ * supervision), with the loss folded in: the upstream gradient of each image
+ * value is sign(image - target) / count, count = gs_num_image_floats(views)
+ * (0 where they are equal; the value gs_l1_loss writes, bit for bit),
+ * formed in the kernel from image and target (DEVICE, same layout as image)
+ * instead of read from a dL_dimage buffer, which is neither needed nor
+ * written. loss DEVICE [1] is overwritten with mean |image - target| (block
+ * partials added with atomics, so its last bits depend on their order).
+ * grad2d as in gs_rasterize_bwd. Same errors as gs_rasterize_bwd; GS_ERR_ARG
+ * also for a NULL target or loss. */
+int gs_rasterize_bwd_l1(const gs_views *views, const gs_config *cfg, const float *proj, const gs_bins *bins,
+                        const float *image, const float *target, float *loss, float *grad2d, int32_t *status,
+                        void *stream);
+
 /* Reduce pose partials (Section 3.4 pose residuals): dL_dviewmat DEVICE
  * [V,12] = dL/dR (row-major) then dL/dt; dL_dtwist DEVICE [V,6] (may be NULL)
  * = gradient w.r.t. a left twist (rho, phi), T <- exp(xi^) T:

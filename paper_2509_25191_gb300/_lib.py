@@ -23,7 +23,7 @@ GS_NUM_COUNTERS = 16
 
 EXPORTED = ["gs_config_default", "gs_num_slots", "gs_slot_base", "gs_num_tiles", "gs_tile_base",
             "gs_num_image_floats", "gs_pixel_base", "gs_pose_blocks", "gs_project", "gs_bin_sort",
-            "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version",
+            "gs_render_fwd", "gs_render_bwd", "gs_rasterize_bwd", "gs_rasterize_bwd_l1", "gs_project_bwd", "gs_pose_grad", "gs_l1_loss", "gs_error_string", "gs_version",
             "gs_project_bwd_noalloc", "gs_sgld_adam_step", "gs_ga_select_pairs", "gs_ga_incidence",
             "gs_ga_epipolar", "gs_ga_weights_scratch_bytes", "gs_ga_weights", "gs_ga_step", "gs_l1_dssim_loss",
             "gs_check_bounded_wait", "gs_workspace_size", "gs_workspace_carve", "gs_status_read",
@@ -320,6 +320,15 @@ def gs_rasterize_bwd(views: Views, cfg: gs_config, proj, bins: Bins, image, dL_d
     _check(load().gs_rasterize_bwd(ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj),
                                    ctypes.byref(bins.c(use_last)), _ptr(image), _ptr(dL_dimage), _ptr(grad2d),
                                    _ptr(status), _stream(stream)), "gs_rasterize_bwd")
+
+
+def gs_rasterize_bwd_l1(views: Views, cfg: gs_config, proj, bins: Bins, image, target, loss, grad2d, status=None,
+                        stream=None, use_last=True):
+    """The raster backward of the mean L1 loss against target, the loss
+    folded in (loss[0] = mean |image - target|; no dL/dimage buffer)."""
+    _check(load().gs_rasterize_bwd_l1(ctypes.byref(views.c()), ctypes.byref(cfg), _ptr(proj),
+                                      ctypes.byref(bins.c(use_last)), _ptr(image), _ptr(target), _ptr(loss),
+                                      _ptr(grad2d), _ptr(status), _stream(stream)), "gs_rasterize_bwd_l1")
 
 
 def gs_project_bwd(g: Gaussians, views: Views, cfg: gs_config, proj, grads: Grads, want_gaussian_grads=True,

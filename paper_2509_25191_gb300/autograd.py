@@ -118,6 +118,20 @@ class Rasterizer:
         _lib.gs_pose_grad(views, grads.pose_partials, grads.n_blocks, dvm, dtw)
         return grads, dvm, dtw
 
+    def backward_l1(self, g: Gaussians, views: Views, proj, image, target, loss, want_gaussian_grads=True,
+                    grads: Grads = None, use_last=True):
+        """The backward of the mean L1 loss against target, with the loss
+        folded into the raster backward (loss[0] = mean |image - target|;
+        no dL/dimage buffer)."""
+        grads = grads or self.grads_buffers(g, views, want_gaussian_grads)
+        _lib.gs_rasterize_bwd_l1(views, self.cfg, proj, self.bins, image, target, loss, grads.grad2d, self.status,
+                                 use_last=use_last)
+        _lib.gs_project_bwd(g, views, self.cfg, proj, grads, want_gaussian_grads, self.status)
+        dvm = torch.empty(views.n, 12, dtype=torch.float32, device=proj.device)
+        dtw = torch.empty(views.n, 6, dtype=torch.float32, device=proj.device)
+        _lib.gs_pose_grad(views, grads.pose_partials, grads.n_blocks, dvm, dtw)
+        return grads, dvm, dtw
+
     def check_status(self):
         """Read the device status word (synchronises); raise on a device error."""
         st = self.status.cpu().numpy()

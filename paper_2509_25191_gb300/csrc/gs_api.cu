@@ -27,7 +27,7 @@ int launch_project(const Launch &L, int deg, const gs_gaussians *g, const float 
 int launch_bin_sort(const Launch &L, const float *proj, const gs_bins *b, int32_t *status, cudaStream_t st);
 int launch_render_fwd(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st);
 int launch_render_bwd(const Launch &L, const float *proj, const gs_bins *b, const float *image,
-                      const float *dL_dimage, float *grad2d, cudaStream_t st);
+                      const float *dL_dimage, const L1Loss &l1, float *grad2d, cudaStream_t st);
 int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const float *viewmats, const float *intr,
                        const float *proj, const float *grad2d, const gs_grads *out, int want_gauss, int nblk,
                        int32_t *status, cudaStream_t st);
@@ -368,7 +368,32 @@ int gs_rasterize_bwd(const gs_views *vw, const gs_config *cfg, const float *proj
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_FLOATS * (size_t)L.n_slots, st) != cudaSuccess)
         return GS_ERR_CUDA;
-    return launch_render_bwd(L, proj, b, image, dL_dimage, grad2d, st);
+    return launch_render_bwd(L, proj, b, image, dL_dimage, L1Loss{}, grad2d, st);
+}
+
+int gs_rasterize_bwd_l1(const gs_views *vw, const gs_config *cfg, const float *proj, const gs_bins *b,
+                        const float *image, const float *target, float *loss, float *grad2d, int32_t *status,
+                        void *stream) {
+    GS_TRACE();
+    Launch L;
+    int rc = build_launch(vw, cfg, L);
+    if (rc) return rc;
+    if (!b || !proj || !image || !target || !loss || !grad2d || !b->tile_ranges || !b->tile_order ||
+        !b->counters || !b->ids)
+        return GS_ERR_ARG;
+    if (!aligned16(grad2d)) return GS_ERR_ARG;
+    (void)status;   // the raster backward reports nothing on the device
+    const int64_t count = gs_num_image_floats(vw);
+    if (count < 1) return GS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_FLOATS * (size_t)L.n_slots, st) != cudaSuccess ||
+        cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess)
+        return GS_ERR_CUDA;
+    L1Loss l1;
+    l1.target = target;
+    l1.loss = loss;
+    l1.inv_n = 1.f / (float)count;
+    return launch_render_bwd(L, proj, b, image, nullptr, l1, grad2d, st);
 }
 
 int gs_project_bwd(const gs_gaussians *g, const gs_views *vw, const gs_config *cfg, const float *proj,

@@ -46,6 +46,15 @@ struct Launch {
     SceneDesc s[GS_MAX_VIEWS];
 };
 
+// The mean L1 loss folded into the raster backward: with target set, the
+// upstream gradient of each image value is sign(image - target) * inv_n and
+// the loss inv_n * sum |image - target| is added to *loss.
+struct L1Loss {
+    const float *target = nullptr;
+    float *loss = nullptr;
+    float inv_n = 0.f;
+};
+
 // counters[] slots
 enum {
     CNT_INSTANCES = 0,   // total tile instances

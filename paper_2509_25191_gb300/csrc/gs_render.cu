@@ -328,7 +328,9 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
                                                             const float *__restrict__ image,
                                                             const float *__restrict__ dL_dimage,
                                                             const int *__restrict__ last_contrib,
-                                                            float4 *__restrict__ grad2d) {
+                                                            float4 *__restrict__ grad2d,
+                                                            const float *__restrict__ l1_target,
+                                                            float *__restrict__ l1_loss, float l1_inv_n) {
     // dynamic shared memory: the per-warp reduction buffers, then the staged
     // batch (L.bwd_batch Gaussians per thread): positions, conics, colours,
     // the conic's A and D (natural-log units), the per-Gaussian gradient sums
@@ -342,6 +344,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
     float *s_g = reinterpret_cast<float *>(s_ad + NB);
     unsigned int *s_mask = reinterpret_cast<unsigned int *>(s_g + 9 * NB);
     __shared__ int s_item;
+    __shared__ float s_l1[BS / 32];
     // the projection backward that follows (launched as a programmatic
     // dependent) may start its blocks on SMs this kernel leaves in its tail:
     // it zeroes its gradient rows there, then waits for this grid to finish
@@ -358,6 +361,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
     const float4 *red_row = reinterpret_cast<const float4 *>(rb + lane * RED_PITCH);
     for (int k = threadIdx.x; k < NB; k += BS)
         for (int c = 0; c < 9; ++c) s_g[9 * k + c] = 0.f;
+    float l1_sum = 0.f;   // with l1_target: this thread's sum of |image - target|
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counters + CNT_Q_BWD, 1);
         __syncthreads();
@@ -371,7 +375,9 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
         const long long hw = (long long)vd.W * vd.H;
         // per pixel: upstream gradient g (one pair per channel), -image.g, and
         // the running colour dotted with g (the colour behind a Gaussian enters
-        // dL/dalpha only as S.g = image.g - C.g)
+        // dL/dalpha only as S.g = image.g - C.g). With l1_target, g is the mean
+        // L1 loss's gradient sign(image - target) / count, formed here (the
+        // value gs_l1_loss writes, bit for bit) instead of read
         float gg[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, ig[2] = {0.f, 0.f};
         bool done0 = !ti.in0, done1 = !ti.in1;
 #pragma unroll
@@ -380,8 +386,17 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
             const long long o = vd.pix_base + (long long)(ti.py0 + 4 * h) * vd.W + ti.px;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                gg[h][ch] = dL_dimage[o + ch * hw];
-                ig[h] = fmaf(image[o + ch * hw], gg[h][ch], ig[h]);
+                const float im = image[o + ch * hw];
+                float g;
+                if (l1_target) {
+                    const float d = im - l1_target[o + ch * hw];
+                    l1_sum += fabsf(d);
+                    g = d > 0.f ? l1_inv_n : (d < 0.f ? -l1_inv_n : 0.f);
+                } else {
+                    g = dL_dimage[o + ch * hw];
+                }
+                gg[h][ch] = g;
+                ig[h] = fmaf(im, g, ig[h]);
             }
         }
         done0 = done0 || (gg[0][0] == 0.f && gg[0][1] == 0.f && gg[0][2] == 0.f);
@@ -558,6 +573,19 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
         }
         if (COUNT) count_pairs(counters, 12, n_eval, n_comp);
     }
+    if (l1_loss) {
+        // the block's part of the loss: one atomic per block (the loss's last
+        // bits depend on their order)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l1_sum += __shfl_xor_sync(0xffffffffu, l1_sum, o);
+        if (lane == 0) s_l1[threadIdx.x >> 5] = l1_sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int w = 0; w < BS / 32; ++w) t += s_l1[w];
+            atomicAdd(l1_loss, t * l1_inv_n);
+        }
+    }
 }
 
 // Resident blocks per SM of a raster kernel at the launch's block and
@@ -671,7 +699,7 @@ static int launch_fwd_t(const Launch &L, const float *proj, const gs_bins *b, fl
 
 template <int TW, int TH, bool COUNT, bool LAST>
 static int launch_bwd_c(const Launch &L, const float *proj, const gs_bins *b, const float *image,
-                        const float *dL_dimage, float *grad2d, cudaStream_t st) {
+                        const float *dL_dimage, const L1Loss &l1, float *grad2d, cudaStream_t st) {
     static int blocks_per_sm[5];
     const size_t smem = (size_t)BWD_STAGE_BYTES * L.bwd_batch * (TW * TH / 2) +
                         sizeof(float) * RED_WARP_FLOATS * (TW * TH / 64);
@@ -681,24 +709,25 @@ static int launch_bwd_c(const Launch &L, const float *proj, const gs_bins *b, co
     if (cudaMemsetAsync(b->counters + CNT_Q_BWD, 0, sizeof(int), st) != cudaSuccess) return GS_ERR_CUDA;
     k_render_bwd<TW, TH, COUNT, LAST><<<grid, TW * TH / 2, smem, st>>>(
         L, reinterpret_cast<const float4 *>(proj), reinterpret_cast<const int2 *>(b->tile_ranges), b->ids,
-        b->tile_order, b->counters, image, dL_dimage, b->last_contrib, reinterpret_cast<float4 *>(grad2d));
+        b->tile_order, b->counters, image, dL_dimage, b->last_contrib, reinterpret_cast<float4 *>(grad2d), l1.target,
+        l1.loss, l1.inv_n);
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
 template <int TW, int TH>
 static int launch_bwd_t(const Launch &L, const float *proj, const gs_bins *b, const float *image,
-                        const float *dL_dimage, float *grad2d, cudaStream_t st) {
+                        const float *dL_dimage, const L1Loss &l1, float *grad2d, cudaStream_t st) {
     if (b->last_contrib) {
         // the forward recorded each tile's replay length
         if (order_by_work(L, b)) {
             k_order_by_work<<<1, 1024, 0, st>>>(work_record(b), nullptr, (int)L.n_tiles, b->tile_order);
             if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
         }
-        return L.count_pairs ? launch_bwd_c<TW, TH, true, true>(L, proj, b, image, dL_dimage, grad2d, st)
-                             : launch_bwd_c<TW, TH, false, true>(L, proj, b, image, dL_dimage, grad2d, st);
+        return L.count_pairs ? launch_bwd_c<TW, TH, true, true>(L, proj, b, image, dL_dimage, l1, grad2d, st)
+                             : launch_bwd_c<TW, TH, false, true>(L, proj, b, image, dL_dimage, l1, grad2d, st);
     }
-    return L.count_pairs ? launch_bwd_c<TW, TH, true, false>(L, proj, b, image, dL_dimage, grad2d, st)
-                         : launch_bwd_c<TW, TH, false, false>(L, proj, b, image, dL_dimage, grad2d, st);
+    return L.count_pairs ? launch_bwd_c<TW, TH, true, false>(L, proj, b, image, dL_dimage, l1, grad2d, st)
+                         : launch_bwd_c<TW, TH, false, false>(L, proj, b, image, dL_dimage, l1, grad2d, st);
 }
 
 int launch_render_fwd(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st) {
@@ -714,8 +743,8 @@ int launch_render_fwd(const Launch &L, const float *proj, const gs_bins *b, floa
 }
 
 int launch_render_bwd(const Launch &L, const float *proj, const gs_bins *b, const float *image,
-                      const float *dL_dimage, float *grad2d, cudaStream_t st) {
-#define GS_CALL_BWD(TW, TH) launch_bwd_t<TW, TH>(L, proj, b, image, dL_dimage, grad2d, st)
+                      const float *dL_dimage, const L1Loss &l1, float *grad2d, cudaStream_t st) {
+#define GS_CALL_BWD(TW, TH) launch_bwd_t<TW, TH>(L, proj, b, image, dL_dimage, l1, grad2d, st)
     if (L.tw == 16 && L.th == 16) return GS_CALL_BWD(16, 16);
     if (L.tw == 8 && L.th == 8) return GS_CALL_BWD(8, 8);
     if (L.tw == 16 && L.th == 8) return GS_CALL_BWD(16, 8);

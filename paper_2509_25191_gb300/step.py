@@ -1,7 +1,8 @@
 """One training step of the rasterizer, captured as a CUDA graph.
 
 A step over a batch of views is: gs_project -> gs_bin_sort -> gs_render_fwd
--> gs_l1_loss or gs_l1_dssim_loss (against the step's target images) -> gs_rasterize_bwd ->
+-> gs_rasterize_bwd_l1 (the mean L1 loss against the step's target images,
+folded into the raster backward) or gs_l1_dssim_loss -> gs_rasterize_bwd ->
 gs_project_bwd -> gs_pose_grad, i.e. the photometric supervision of
 Section 3.1 with gradients to every Gaussian parameter and to every view's
 pose (Section 3.4). All buffers are allocated once; the tile-instance
@@ -40,15 +41,25 @@ from .autograd import Rasterizer
 
 class GraphStep:
     # project 1, bin/sort 5 (count, scan, scatter, split, sort), render 1,
-    # raster bwd 1, projection bwd 1, pose 1; the loss adds 1 (L1) or 2 (L1 + D-SSIM)
+    # raster bwd 1, projection bwd 1, pose 1; the L1 loss is part of the raster
+    # backward, the L1 + D-SSIM loss adds 2 kernels
     KERNELS_FIXED = 10
+    # the calls of a step, in order (the stages of run()'s events)
+    STAGES = {"l1": ("gs_project", "gs_bin_sort", "gs_render_fwd", "gs_rasterize_bwd_l1", "gs_project_bwd",
+                     "gs_pose_grad"),
+              "l1_dssim": ("gs_project", "gs_bin_sort", "gs_render_fwd", "gs_l1_dssim_loss", "gs_rasterize_bwd",
+                           "gs_project_bwd", "gs_pose_grad")}
+
+    @property
+    def stages(self):
+        return self.STAGES[self.loss_kind]
 
     def kernels_per_step(self) -> int:
         """Kernels of this library that one step launches: the fixed ten, the
-        loss kernels, and, when the image has fewer than 16 tiles per SM, the
-        tile orderings by replay length that the raster forward (from the
-        previous forward's record) and the raster backward run first."""
-        loss = 1 if self.loss_kind == "l1" else 2
+        D-SSIM loss kernels, and, when the image has fewer than 16 tiles per
+        SM, the tile orderings by replay length that the raster forward (from
+        the previous forward's record) and the raster backward run first."""
+        loss = 0 if self.loss_kind == "l1" else 2
         sms = torch.cuda.get_device_properties(self.g.means.device).multi_processor_count
         order = 2 if 0 < self.bins.n_tiles < 16 * sms else 0
         return self.KERNELS_FIXED + loss + order
@@ -84,7 +95,8 @@ class GraphStep:
         self.cfg, self.bins, self.status = self.rast.cfg, self.rast.bins, self.rast.status
         self.proj = torch.empty(max(1, views.num_slots()), _lib.GS_RECORD_FLOATS, device=dev)
         self.image = torch.empty(views.num_image_floats(), device=dev)
-        self.dimg = torch.empty_like(self.image)
+        # dL/dimage of the L1 + D-SSIM loss (the L1 loss forms its own in the raster backward)
+        self.dimg = torch.empty_like(self.image) if loss == "l1_dssim" else None
         # l1: [mean L1]; l1_dssim: [total, mean L1, 1 - mean SSIM]
         # the step's results (loss, pose gradient) are kept per input slot, so
         # that a loop can read step k's back while step k+1 runs
@@ -114,12 +126,14 @@ class GraphStep:
         _lib.gs_render_fwd(v, cfg, self.proj, b, self.image, st)
         rec()
         if self.loss_kind == "l1":
-            _lib.gs_l1_loss(self.image, target, self.loss_slots[slot], self.dimg)
+            _lib.gs_rasterize_bwd_l1(v, cfg, self.proj, b, self.image, target, self.loss_slots[slot],
+                                     self.grads.grad2d, st)
+            rec()
         else:
             _lib.gs_l1_dssim_loss(v, self.image, target, self.loss_slots[slot], self.dimg, self.lam)
-        rec()
-        _lib.gs_rasterize_bwd(v, cfg, self.proj, b, self.image, self.dimg, self.grads.grad2d, st)
-        rec()
+            rec()
+            _lib.gs_rasterize_bwd(v, cfg, self.proj, b, self.image, self.dimg, self.grads.grad2d, st)
+            rec()
         _lib.gs_project_bwd(g, v, cfg, self.proj, self.grads, self.want, st)
         rec()
         _lib.gs_pose_grad(v, self.grads.pose_partials, self.grads.n_blocks, self.dviewmat_slots[slot],
@@ -183,7 +197,7 @@ class PlainStep:
         dev = g.means.device
         self.loss = torch.empty(1, device=dev)
 
-    STAGES = ("project", "bin_sort", "render_fwd", "loss", "backward")
+    STAGES = ("project", "bin_sort", "render_fwd", "backward_l1")
 
     def run(self, events=None):
         """The views one after another; with ``events`` (a list), an event is
@@ -199,8 +213,5 @@ class PlainStep:
             rec()
             image = rast.render(vv, proj, bins)
             rec()
-            dimg = torch.empty_like(image)
-            _lib.gs_l1_loss(image, tgt, self.loss, dimg)
-            rec()
-            rast.backward(self.g, vv, proj, image, dimg)
+            rast.backward_l1(self.g, vv, proj, image, tgt, self.loss)
             rec()

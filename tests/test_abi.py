@@ -56,6 +56,7 @@ def test_cuda_calls_fail_cleanly_with_bad_arguments():
     assert lib.gs_project(None, None, None, None, None, None) == _lib.GS_ERR_ARG
     assert lib.gs_pose_grad(None, None, 0, None, None, None) == _lib.GS_ERR_ARG
     assert lib.gs_l1_loss(None, None, ctypes.c_int64(-1), None, None, None) == _lib.GS_ERR_ARG
+    assert lib.gs_rasterize_bwd_l1(None, None, None, None, None, None, None, None, None, None) == _lib.GS_ERR_ARG
 
 
 def test_tile_shapes_on_the_host():

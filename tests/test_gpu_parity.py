@@ -627,6 +627,34 @@ def test_l1_loss_kernel():
     assert np.array_equal(grad.cpu().numpy(), (np.sign(d) / d.size).astype(np.float32))
 
 
+@pytest.mark.parametrize("case", ["small_2k", "clustered_sh3", "orbit_4views", "uneven_3scenes"])
+def test_raster_backward_with_the_l1_loss_folded_in(case):
+    """gs_rasterize_bwd_l1 forms the mean L1 loss's gradient in the raster
+    backward: its 2D gradients equal gs_l1_loss followed by gs_rasterize_bwd
+    up to the order of float atomics, and its loss the mean absolute
+    difference (some image values equal to the target: zero gradient)."""
+    sc, vw = CASES[case]()
+    rast, g, views, image, proj = gpu_forward(sc, vw)
+    target = torch.rand(image.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(11))
+    target[::7] = image[::7]
+    n_slots = max(1, views.num_slots())
+    loss_a, loss_b = torch.empty(1, device="cuda"), torch.empty(1, device="cuda")
+    dimg = torch.empty_like(image)
+    a = torch.empty(n_slots, _lib.GS_GRAD2D_FLOATS, device="cuda")
+    b = torch.empty_like(a)
+    _lib.gs_l1_loss(image, target, loss_a, dimg)
+    _lib.gs_rasterize_bwd(views, rast.cfg, proj, rast.bins, image, dimg, a)
+    _lib.gs_rasterize_bwd_l1(views, rast.cfg, proj, rast.bins, image, target, loss_b, b)
+    torch.cuda.synchronize()
+    d = (image - target).double().cpu().numpy()
+    assert abs(loss_b.item() - np.abs(d).mean()) <= 1e-6 * max(1.0, np.abs(d).mean())
+    assert abs(loss_b.item() - loss_a.item()) <= 1e-6 * loss_a.item()
+    A, B = a.cpu().numpy(), b.cpu().numpy()
+    assert np.abs(A).max() > 0
+    assert np.linalg.norm(B - A) <= 1e-5 * np.linalg.norm(A)
+    assert np.abs(B - A).max() <= 1e-5 * np.abs(A).max()
+
+
 def test_bounded_wait_runs_out_and_reports():
     """The projection kernels' bounded wait, on a copy barrier that nothing
     completes, gives up after about a second and reports GS_ERR_TIMEOUT in
