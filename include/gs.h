@@ -90,6 +90,14 @@ typedef struct gs_config {
                              1, 2 or 4 (a batch is fwd_batch x tile_w x tile_h / 2 Gaussians) */
     int bwd_batch;        /* [1] the same for gs_rasterize_bwd: 1 or 2. Neither changes the image; the
                              2D gradients change only in the order of their float additions. */
+    int overlap_prev;     /* [0] nonzero: gs_rasterize_bwd(_l1) and the one-view gs_project_bwd with
+                             parameter gradients are launched as programmatic dependents of the kernel
+                             ahead of them on the stream, and zero their accumulators (the 2D gradients
+                             and the L1 loss; the parameter-gradient rows) while that kernel's last
+                             blocks still run, waiting for it before anything else. The caller
+                             guarantees that the kernel ahead neither reads nor writes those outputs
+                             (true in a step: gs_render_fwd, then gs_rasterize_bwd_l1, then
+                             gs_project_bwd); 0: every kernel starts after the work ahead of it. */
 } gs_config;
 
 /* Gaussians (all DEVICE, float32, contiguous). Several scenes may be
@@ -275,12 +283,9 @@ int gs_render_bwd(const gs_gaussians *g, const gs_views *views, const gs_config 
  * written or added once) and the pose partials (always overwritten). With
  * one view it runs the chain only for the Gaussians with a nonzero 2D
  * gradient and writes zeros for the others (accumulating, leaves them as
- * they are); that one-view call with parameter gradients is launched as a
- * programmatic dependent of the kernel ahead of it on the stream (in a step,
- * gs_rasterize_bwd's): its blocks may start in that kernel's tail and zero
- * their parameter-gradient rows before waiting for it to finish, so the
- * kernel ahead must not write the parameter-gradient outputs (nothing else
- * it reads or writes is touched before the wait). With several views it
+ * they are); with cfg->overlap_prev that one-view call with parameter
+ * gradients zeroes those rows in the tail of the kernel ahead (see
+ * gs_config.overlap_prev). With several views it
  * runs the chains per block either by each Gaussian's thread or over
  * per-view lists of the Gaussians with a gradient, whichever takes fewer
  * warp runs (the pose partials' grouping follows that choice and is

@@ -45,7 +45,8 @@ class gs_config(ctypes.Structure):
                 ("near_z", ctypes.c_float), ("dilation", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float), ("fov_clamp", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("count_pairs", ctypes.c_int), ("accumulate_grads", ctypes.c_int),
-                ("use_tma", ctypes.c_int), ("fwd_batch", ctypes.c_int), ("bwd_batch", ctypes.c_int)]
+                ("use_tma", ctypes.c_int), ("fwd_batch", ctypes.c_int), ("bwd_batch", ctypes.c_int),
+                ("overlap_prev", ctypes.c_int)]
 
 
 class gs_gaussians(ctypes.Structure):
@@ -148,7 +149,7 @@ def _stream(stream):
 
 def config(tile=(16, 16), pixel_gate=True, bg=(0.0, 0.0, 0.0), near=0.2, dilation=0.3,
            alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, fov_clamp=1.3, count_pairs=False,
-           accumulate_grads=False, use_tma=True, batch=(2, 1)) -> gs_config:
+           accumulate_grads=False, use_tma=True, batch=(2, 1), overlap_prev=False) -> gs_config:
     c = gs_config()
     load().gs_config_default(ctypes.byref(c))
     c.tile_w, c.tile_h = int(tile[0]), int(tile[1])
@@ -160,6 +161,7 @@ def config(tile=(16, 16), pixel_gate=True, bg=(0.0, 0.0, 0.0), near=0.2, dilatio
     c.accumulate_grads = int(bool(accumulate_grads))
     c.use_tma = int(bool(use_tma))
     c.fwd_batch, c.bwd_batch = int(batch[0]), int(batch[1])
+    c.overlap_prev = int(bool(overlap_prev))
     return c
 
 

@@ -28,6 +28,7 @@ int launch_bin_sort(const Launch &L, const float *proj, const gs_bins *b, int32_
 int launch_render_fwd(const Launch &L, const float *proj, const gs_bins *b, float *image, cudaStream_t st);
 int launch_render_bwd(const Launch &L, const float *proj, const gs_bins *b, const float *image,
                       const float *dL_dimage, const L1Loss &l1, float *grad2d, cudaStream_t st);
+int launch_zero_accumulators(float *grad2d, long long n_floats, float *loss, cudaStream_t st);
 int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const float *viewmats, const float *intr,
                        const float *proj, const float *grad2d, const gs_grads *out, int want_gauss, int nblk,
                        int32_t *status, cudaStream_t st);
@@ -130,6 +131,7 @@ static int build_launch(const gs_views *vw, const gs_config *cfg, Launch &L) {
     L.use_tma = cfg->use_tma != 0;
     L.fwd_batch = cfg->fwd_batch;
     L.bwd_batch = cfg->bwd_batch;
+    L.overlap_prev = cfg->overlap_prev != 0;
     if (!(L.fwd_batch == 1 || L.fwd_batch == 2 || L.fwd_batch == 4) || !(L.bwd_batch == 1 || L.bwd_batch == 2))
         return GS_ERR_UNSUPPORTED;
     if (!(L.alpha_max > 0.f && L.alpha_max < 1.f) || !(L.t_min > 0.f)) return GS_ERR_ARG;
@@ -210,6 +212,7 @@ void gs_config_default(gs_config *cfg) {
     cfg->use_tma = 1;
     cfg->fwd_batch = 2;
     cfg->bwd_batch = 1;
+    cfg->overlap_prev = 0;
 }
 
 int64_t gs_num_slots(const gs_views *vw) {
@@ -366,8 +369,11 @@ int gs_rasterize_bwd(const gs_views *vw, const gs_config *cfg, const float *proj
     if (!aligned16(grad2d)) return GS_ERR_ARG;
     (void)status;   // the raster backward reports nothing on the device
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_FLOATS * (size_t)L.n_slots, st) != cudaSuccess)
+    if (L.overlap_prev) {
+        if ((rc = launch_zero_accumulators(grad2d, (long long)GS_GRAD2D_FLOATS * L.n_slots, nullptr, st))) return rc;
+    } else if (cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_FLOATS * (size_t)L.n_slots, st) != cudaSuccess) {
         return GS_ERR_CUDA;
+    }
     return launch_render_bwd(L, proj, b, image, dL_dimage, L1Loss{}, grad2d, st);
 }
 
@@ -386,9 +392,12 @@ int gs_rasterize_bwd_l1(const gs_views *vw, const gs_config *cfg, const float *p
     const int64_t count = gs_num_image_floats(vw);
     if (count < 1) return GS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_FLOATS * (size_t)L.n_slots, st) != cudaSuccess ||
-        cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess)
+    if (L.overlap_prev) {
+        if ((rc = launch_zero_accumulators(grad2d, (long long)GS_GRAD2D_FLOATS * L.n_slots, loss, st))) return rc;
+    } else if (cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_FLOATS * (size_t)L.n_slots, st) != cudaSuccess ||
+               cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess) {
         return GS_ERR_CUDA;
+    }
     L1Loss l1;
     l1.target = target;
     l1.loss = loss;

@@ -40,6 +40,7 @@ struct Launch {
     int accumulate;         // the projection backward adds to the parameter gradients
     int use_tma;            // the projection kernels may stage through tensor copies
     int fwd_batch, bwd_batch;   // Gaussians staged per thread per shared-memory batch
+    int overlap_prev;           // zero the backward's accumulators in the tail of the kernel ahead
     float near_z, dilation, alpha_min, alpha_max, t_min, fov_clamp;
     float bg[3];
     ViewDesc v[GS_MAX_VIEWS];

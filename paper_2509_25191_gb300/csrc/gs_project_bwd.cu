@@ -405,9 +405,10 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_project_bwd(
         c_end = min((long long)L.n_threads, c_next + per);
         if (GAUSS && !L.accumulate && c_next < c_end) {
             // this block's rows, zero (one view: its Gaussians are contiguous);
-            // they depend on nothing the raster backward writes, so this runs
-            // before the wait below, on SMs the raster backward has left. The
-            // listed Gaussians' rows are written again after later barriers.
+            // the kernel ahead does not touch them, so this runs before the
+            // wait below (launched with overlap_prev: on SMs the raster
+            // backward has left). The listed Gaussians' rows are written again
+            // after later barriers.
             const int sc = scene_of_thread(L, c_next);
             zero_rows<K>(L.s[sc].g_begin + (c_next - L.s[sc].thread_base), c_end - c_next, g_means, g_log_scales,
                          g_quats, g_logits, g_sh);
@@ -833,9 +834,9 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
     k_project_bwd<D, G, Z><<<nblk, PB_THREADS, dyn, st>>>(                                                         \
         L, g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, viewmats, intr, p, g2, out->means,        \
         out->log_scales, out->quats, out->opacity_logits, out->sh, out->pose_partials)
-    // one-view calls with parameter gradients: a programmatic dependent of the
-    // kernel ahead (the raster backward in a step), so that each block zeroes
-    // its rows while that kernel's tail still runs
+    // one-view calls with parameter gradients and overlap_prev: a programmatic
+    // dependent of the kernel ahead (the raster backward in a step), so that
+    // each block zeroes its rows while that kernel's tail still runs
 #define GS_PB_EARLY(D)                                                                                             \
     do {                                                                                                           \
         cudaLaunchConfig_t lc = {};                                                                                \
@@ -876,12 +877,20 @@ int launch_project_bwd(const Launch &L, int deg, const gs_gaussians *g, const fl
         case 3: GS_PBV(3); break;
         default: return GS_ERR_UNSUPPORTED;
         }
-    } else if (want_gauss) {
+    } else if (want_gauss && L.overlap_prev) {
         switch (deg) {
         case 0: GS_PB_EARLY(0); break;
         case 1: GS_PB_EARLY(1); break;
         case 2: GS_PB_EARLY(2); break;
         case 3: GS_PB_EARLY(3); break;
+        default: return GS_ERR_UNSUPPORTED;
+        }
+    } else if (want_gauss) {
+        switch (deg) {
+        case 0: GS_PB(0, true, true); break;
+        case 1: GS_PB(1, true, true); break;
+        case 2: GS_PB(2, true, true); break;
+        case 3: GS_PB(3, true, true); break;
         default: return GS_ERR_UNSUPPORTED;
         }
     } else {

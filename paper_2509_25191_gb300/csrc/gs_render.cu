@@ -214,6 +214,9 @@ __global__ void __launch_bounds__(TW * TH / 2) k_render_fwd(const Launch L, cons
     float4 *s_xy = s_dyn, *s_con = s_xy + NB, *s_rgb = s_con + NB;
     unsigned int *s_mask = reinterpret_cast<unsigned int *>(s_rgb + NB);
     __shared__ int s_item, s_end;
+    // the backward's accumulators that follow (zeroed by a programmatic
+    // dependent) may be cleared on SMs this kernel leaves in its tail
+    launch_dependents();
     const bool abort = counters[CNT_ABORT] != 0;
     const unsigned int wbit = 1u << (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -586,6 +589,36 @@ __global__ void __launch_bounds__(TW * TH / 2, 1024 / (TW * TH / 2)) k_render_bw
             atomicAdd(l1_loss, t * l1_inv_n);
         }
     }
+}
+
+// Zero the raster backward's accumulators (the 2D gradients, and the L1 loss
+// when given) as a programmatic dependent of the kernel ahead on the stream
+// (in a step, the raster forward): nothing here touches what that kernel
+// reads or writes, so the stores run on the SMs it leaves in its tail; the
+// wait at the end keeps the stream's order for the kernels after this one.
+__global__ void __launch_bounds__(256) k_zero_accumulators(float4 *__restrict__ p, long long n4,
+                                                           float *__restrict__ loss) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n4; i += (long long)gridDim.x * 256) p[i] = z;
+    if (loss && blockIdx.x == 0 && threadIdx.x == 0) *loss = 0.f;
+    grid_dependency_wait();
+}
+
+int launch_zero_accumulators(float *grad2d, long long n_floats, float *loss, cudaStream_t st) {
+    // (n_floats: 12 per slot, a whole number of float4; grad2d 16-byte aligned)
+    const long long n4 = n_floats / 4;
+    cudaLaunchConfig_t lc = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.gridDim = dim3((unsigned)max(1LL, min((long long)num_sms() * 8, (n4 + 255) / 256)));
+    lc.blockDim = dim3(256);
+    lc.stream = st;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    if (cudaLaunchKernelEx(&lc, k_zero_accumulators, reinterpret_cast<float4 *>(grad2d), n4, loss) != cudaSuccess)
+        return GS_ERR_CUDA;
+    return GS_OK;
 }
 
 // Resident blocks per SM of a raster kernel at the launch's block and

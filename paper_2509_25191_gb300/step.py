@@ -84,7 +84,9 @@ class GraphStep:
             raise ValueError(f"unknown loss {loss!r}")
         self.loss_kind, self.lam = loss, float(lam)
         dev = g.means.device
-        self.rast = Rasterizer(tile=tile, batch=batch)
+        # the step's calls run in a fixed order, so the backward's zeroing may
+        # overlap the tail of the kernel ahead (gs_config.overlap_prev)
+        self.rast = Rasterizer(tile=tile, batch=batch, overlap_prev=True)
         if capacity is None:
             # size the instance capacity from one uncaptured forward
             _, _ = self.rast.forward(g, views)
@@ -192,7 +194,7 @@ class PlainStep:
             vv = Views(views.viewmats[v:v + 1], views.intrinsics[v:v + 1], views.width[v:v + 1],
                        views.height[v:v + 1], views.gauss_begin[v:v + 1], views.gauss_count[v:v + 1])
             n = vv.num_image_floats()
-            self.one.append((vv, target[off:off + n], Rasterizer(tile=tile, batch=batch)))
+            self.one.append((vv, target[off:off + n], Rasterizer(tile=tile, batch=batch, overlap_prev=True)))
             off += n
         dev = g.means.device
         self.loss = torch.empty(1, device=dev)

@@ -207,6 +207,40 @@ def test_tile_work_record_orders_without_changing_results(case):
     assert np.array_equal(work, expect)
 
 
+@pytest.mark.parametrize("case", ["clustered_sh3", "orbit_4views"])
+def test_overlapped_backward_equals_the_plain_order(case):
+    """With gs_config.overlap_prev the raster backward's accumulators and the
+    one-view projection backward's gradient rows are zeroed in the tail of
+    the kernel ahead (programmatic dependent launches); the backward gives
+    the loss, parameter and pose gradients of the plain order, where every
+    kernel waits for the work ahead (up to the order of float atomics), on
+    a first call and on a second into the same buffers."""
+    sc, vw = CASES[case]()
+    g = _lib.Gaussians.from_scene(sc)
+    views = _lib.Views.from_synth(vw)
+    target = torch.rand(views.num_image_floats(), device="cuda", generator=torch.Generator("cuda").manual_seed(12))
+    res = []
+    for overlap in (False, True):
+        rast = Rasterizer(tile=(16, 16), overlap_prev=overlap)
+        image, proj = rast.forward(g, views)
+        loss = torch.empty(1, device="cuda")
+        out = []
+        grads = None
+        for _ in range(2):
+            grads, dvm, dtw = rast.backward_l1(g, views, proj, image, target, loss, grads=grads)
+            torch.cuda.synchronize()
+            out.append([loss.cpu().numpy().copy(), dvm.cpu().numpy().copy(), dtw.cpu().numpy().copy()] +
+                       _grads_of(grads))
+        rast.check_status()
+        res.append(out)
+    for call in range(2):
+        for a, b in zip(res[0][call], res[1][call]):
+            assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(a) + 1e-30
+        # the second call repeats the first
+        for a, b in zip(res[1][0], res[1][call]):
+            assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(a) + 1e-30
+
+
 def test_workspace_step_equals_the_rasterizer():
     """A forward and backward whose tile lists, 2D gradients and pose
     partials are carved from one caller buffer give the Rasterizer's image
