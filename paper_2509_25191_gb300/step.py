@@ -40,10 +40,11 @@ from .autograd import Rasterizer
 
 
 class GraphStep:
-    # project 1, bin/sort 5 (count, scan, scatter, split, sort), render 1,
+    # project 1, bin/sort 5 (count, scan, scatter, split, sort), render 1, the
+    # zeroing of the backward's accumulators 1 (a kernel with overlap_prev),
     # raster bwd 1, projection bwd 1, pose 1; the L1 loss is part of the raster
     # backward, the L1 + D-SSIM loss adds 2 kernels
-    KERNELS_FIXED = 10
+    KERNELS_FIXED = 11
     # the calls of a step, in order (the stages of run()'s events)
     STAGES = {"l1": ("gs_project", "gs_bin_sort", "gs_render_fwd", "gs_rasterize_bwd_l1", "gs_project_bwd",
                      "gs_pose_grad"),
@@ -55,7 +56,7 @@ class GraphStep:
         return self.STAGES[self.loss_kind]
 
     def kernels_per_step(self) -> int:
-        """Kernels of this library that one step launches: the fixed ten, the
+        """Kernels of this library that one step launches: the fixed eleven, the
         D-SSIM loss kernels, and, when the image has fewer than 16 tiles per
         SM, the tile orderings by replay length that the raster forward (from
         the previous forward's record) and the raster backward run first."""
