@@ -40,6 +40,13 @@ def test_host_layout_queries_without_gpu():
     lib.gs_config_default(ctypes.byref(cfg))
     assert (cfg.tile_w, cfg.tile_h, cfg.pixel_gate) == (16, 16, 1)
     assert abs(cfg.alpha_min - 1 / 255) < 1e-9 and abs(cfg.alpha_max - 0.99) < 1e-7
+    # every field the C default fills, in the binding's layout (the last one
+    # tells a shifted layout apart: the C side writes all of them)
+    cfg.overlap_prev = 7
+    lib.gs_config_default(ctypes.byref(cfg))
+    assert (cfg.count_pairs, cfg.accumulate_grads, cfg.use_tma) == (0, 0, 1)
+    assert (cfg.fwd_batch, cfg.bwd_batch, cfg.overlap_prev) == (2, 1, 0)
+    assert _lib.config(overlap_prev=True).overlap_prev == 1
     views = _lib.Views(None, None, vw.width, vw.height, vw.gauss_begin, vw.gauss_count)
     c = views.c()
     assert lib.gs_num_slots(ctypes.byref(c)) == 60
