@@ -605,7 +605,9 @@ def batched_vs_plain(dev, tile, steps=20, plain_steps=5):
                                      "frac": round(bbytes / (tb * 1e-3) / (peaks["hbm_gbs"] * 1e9), 4)},
             "plain_stages_ms": pst,
             "plain_definition": "the same library called view by view, uncaptured, each call with the instance-count "
-                                "readback an uncaptured call needs (bin_sort includes it)"}
+                                "readback an uncaptured call needs (bin_sort includes it); the same calls as the "
+                                "batched step (L1 loss folded into the raster backward, zeroing overlapped with "
+                                "the kernel ahead)"}
 
 
 def _time_replays(step, steps):
